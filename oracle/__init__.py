@@ -1,0 +1,90 @@
+"""ctypes access to the C oracle (oracle/_build/liboracle.so).
+
+Test infrastructure: only tests/, the smoke check (__graft_entry__.smoke) and
+the CPU-baseline leg of bench.py may import this package.  The library it
+wraps is the plain scalar implementation of the method that the CUDA path is
+checked against, bit for bit.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+K_U64, K_B64, K_SC64, K_U32, K_B32, K_SC32 = 1, 2, 3, 11, 12, 13
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = ctypes.CDLL(path)
+        _lib.oracle_apply.restype = ctypes.c_int
+        _lib.oracle_apply.argtypes = [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        _lib.oracle_kind.restype = ctypes.c_int
+        _lib.oracle_kind.argtypes = [ctypes.c_char_p]
+        _lib.oracle_count.restype = ctypes.c_int
+        _lib.oracle_name.restype = ctypes.c_char_p
+        _lib.oracle_name.argtypes = [ctypes.c_int]
+        _lib.oracle_ph_reduce.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        _lib.oracle_ph_table_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    return _lib
+
+
+def names():
+    L = lib()
+    return [L.oracle_name(i).decode() for i in range(L.oracle_count())]
+
+
+def kind(name):
+    return lib().oracle_kind(name.encode())
+
+
+def default_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def apply(name, x, y=None, nthreads=None):
+    """Evaluate oracle function `name` elementwise.  Returns out, or
+    (sin, cos) for sincos."""
+    k = kind(name)
+    if k == 0:
+        raise KeyError(f"oracle has no function {name!r}")
+    dt = np.float64 if k < 10 else np.float32
+    x = np.ascontiguousarray(x, dtype=dt)
+    n = x.size
+    out = np.empty_like(x)
+    out2 = np.empty_like(x) if k in (K_SC64, K_SC32) else None
+    yp = None
+    if k in (K_B64, K_B32):
+        y = np.ascontiguousarray(y, dtype=dt)
+        assert y.size == n
+        yp = y.ctypes.data
+    rc = lib().oracle_apply(name.encode(), x.ctypes.data, yp, out.ctypes.data,
+                            out2.ctypes.data if out2 is not None else None, n,
+                            nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"oracle_apply({name}) failed: {rc}")
+    return (out, out2) if out2 is not None else out
+
+
+def ph_reduce(x):
+    q = ctypes.c_int()
+    hi = ctypes.c_double()
+    lo = ctypes.c_double()
+    lib().oracle_ph_reduce(float(x), ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo))
+    return q.value, hi.value, lo.value
+
+
+def ph_table():
+    tab = np.empty(4096, dtype=np.float64)
+    ib = np.empty(1024, dtype=np.uint8)
+    lib().oracle_ph_table_copy(tab.ctypes.data, ib.ctypes.data)
+    return tab, ib

@@ -1,0 +1,25 @@
+/*
+ * Scalar C oracle of the vectorized libm method (Shibata & Petrogalli,
+ * "SLEEF", IEEE TPDS 2020).  Test infrastructure: only tests/, the smoke
+ * check and the CPU-baseline leg of the benchmark may use anything under
+ * oracle/.  Compiled with -ffp-contract=off -fno-fast-math; fma() only where
+ * written; round-to-nearest only (Section 5.10).
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+#include "common.h"
+
+double oracle_sin_u10_f64(double);
+double oracle_sin_u35_f64(double);
+double oracle_cos_u10_f64(double);
+double oracle_cos_u35_f64(double);
+double oracle_tan_u10_f64(double);
+double oracle_tan_u35_f64(double);
+void oracle_sincos_u10_f64(double, double *, double *);
+void oracle_sincos_u35_f64(double, double *, double *);
+
+int oracle_apply(const char *name, const void *x, const void *y, void *out, void *out2,
+                 size_t n, int nthreads);
+#endif

@@ -1,0 +1,159 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+Holds no arithmetic of the method: only random bit generation and the
+mapping of random bits onto each function's argument domain.  Every array is
+a pure function of (key, n, domain) and is built from integer operations and
+exact power-of-two scalings, so the same bytes come out on x86-64 and Arm.
+
+Recipe (the paper's workloads are uniform random arguments over stated
+domains, Section 7, Table 3):
+  uniform(a, b)       a + (b - a) * u,  u = (r >> 11) * 2^-53, r from PCG64
+  loguniform(lo, hi)  binade chosen uniformly among those covering [lo, hi],
+                      mantissa uniform within it, random sign if asked,
+                      clamped into [lo, hi]
+  mix                 per element: 89% main domain, 10% tail (log-uniform huge
+                      arguments for the trig functions), 1% from SPECIALS_F64
+"""
+import hashlib
+import math
+
+import numpy as np
+
+_MASK53 = (1 << 53) - 1
+
+
+def seed_of(key):
+    return int.from_bytes(hashlib.sha256(str(key).encode()).digest()[:8], "little")
+
+
+def raw(key, n):
+    """n uint64 values of the PCG64 stream seeded by key (stream stable
+    across numpy versions: only the bit generator is used)."""
+    bg = np.random.PCG64(seed_of(key))
+    return bg.random_raw(n).astype(np.uint64)
+
+
+def unit(key, n):
+    """n doubles uniform in [0, 1) with 53 random bits."""
+    return (raw(key, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform(key, n, a, b, dtype=np.float64):
+    u = unit(key, n)
+    x = a + (b - a) * u
+    return x.astype(dtype)
+
+
+def loguniform(key, n, lo, hi, signed=True, dtype=np.float64):
+    r = raw(key, n)
+    elo = math.frexp(lo)[1] - 1
+    ehi = math.frexp(hi)[1] - 1
+    nb = ehi - elo + 1
+    e = elo + (r % np.uint64(nb)).astype(np.int64)
+    mant = 1.0 + ((r >> np.uint64(11)) & np.uint64(_MASK53 >> 1)).astype(np.float64) * 2.0 ** -52
+    x = np.ldexp(mant, e.astype(np.int32))
+    x = np.clip(x, lo, hi)
+    if signed:
+        s = (raw(str(key) + "/sign", n) >> np.uint64(63)).astype(bool)
+        x = np.where(s, -x, x)
+    return x.astype(dtype)
+
+
+def _pi_half_int(bits):
+    """floor(pi/2 * 2^bits) from Machin's formula in integers (input
+    generation only: used to place arguments next to multiples of pi/2)."""
+    guard = bits + 16
+    one = 1 << guard
+
+    def atan_inv(k):
+        s, t, n, k2 = 0, one // k, 0, k * k
+        while t:
+            s += t // (2 * n + 1) if n % 2 == 0 else -(t // (2 * n + 1))
+            t //= k2
+            n += 1
+        return s
+    pi = 16 * atan_inv(5) - 4 * atan_inv(239)
+    return (pi >> 1) >> 16
+
+
+def near_pi_half(ks):
+    """RN(k pi/2) for integers k, as doubles."""
+    P = _pi_half_int(1200)
+    out = []
+    for k in ks:
+        v = k * P                      # k pi/2 * 2^1200
+        e = v.bit_length() - 53        # keep 53 bits
+        m = v >> e
+        rem = v - (m << e)
+        half = 1 << (e - 1)
+        if rem > half or (rem == half and (m & 1)):
+            m += 1
+        out.append(math.ldexp(float(m), e - 1200))
+    return np.array(out, dtype=np.float64)
+
+
+def _specials():
+    d = np.float64
+    tiny = np.nextafter(d(0), d(1))
+    maxsub = d(2.0 ** -1022) - tiny
+    base = [0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan, tiny, -tiny, maxsub, -maxsub,
+            2.0 ** -1022, -(2.0 ** -1022), np.finfo(d).max, -np.finfo(d).max,
+            1.0, -1.0, 0.5, -0.5, 2.0, -2.0, 15.0, -15.0,
+            float(np.nextafter(d(15), d(0))), float(np.nextafter(d(15), d(20))),
+            1e14, -1e14, float(np.nextafter(d(1e14), d(0))), float(np.nextafter(d(1e14), d(1e15))),
+            2.0 ** 1023, 3 * 2.0 ** -1022, 0.75, 1.5, 3.0, 0.1,
+            1e-300, -1e-300, 700.0, -700.0, 710.0, -745.5, 1e300, -1e300,
+            math.pi, -math.pi, math.pi / 2, -math.pi / 2, 6.283185307179586, 1e22, -1e22, 100.0]
+    k0 = int(1e22 * 2 / math.pi)
+    near = list(near_pi_half(range(k0, k0 + 14)))
+    vals = np.array(base + near, dtype=np.float64)
+    assert vals.size == 64
+    return vals
+
+
+SPECIALS_F64 = _specials()
+
+
+def specials_f32():
+    v = SPECIALS_F64.astype(np.float32)
+    return v
+
+
+# argument domains (main part) per function; trig tail = log-uniform huge
+# arguments through the Payne-Hanek path.  Trig main domain [-100, 100]; the
+# others follow Table 3 of the paper where it gives one.
+DOMAINS_F64 = {
+    "sin": (-100.0, 100.0), "cos": (-100.0, 100.0), "tan": (-100.0, 100.0),
+    "sincos": (-100.0, 100.0),
+    "asin": (-1.0, 1.0), "acos": (-1.0, 1.0), "atan": (-700.0, 700.0),
+    "atan2": (-100.0, 100.0),
+    "exp": (-700.0, 700.0), "exp2": (-1075.0, 1024.0), "exp10": (-324.0, 308.0),
+    "expm1": (-700.0, 709.0),
+    "log": (0.0, 1e300), "log2": (0.0, 1e300), "log10": (0.0, 1e300), "log1p": (-1.0, 1e300),
+    "pow": (-30.0, 30.0), "cbrt": (-1e300, 1e300),
+    "sinh": (-709.0, 709.0), "cosh": (-709.0, 709.0), "tanh": (-20.0, 20.0),
+    "asinh": (-1e300, 1e300), "acosh": (1.0, 1e300), "atanh": (-1.0, 1.0),
+    "erf": (-6.0, 6.0), "erfc": (-6.0, 27.3), "tgamma": (-170.0, 171.6),
+    "lgamma": (-1e3, 2.5e305), "fmod": (-1e25, 1e25), "remainder": (-1e25, 1e25),
+}
+TRIG = ("sin", "cos", "tan", "sincos")
+
+
+def workload(fn, n, key="c2", dtype=np.float64, operand=0):
+    """The mixed workload of one function: 89% uniform over the main domain,
+    10% log-uniform tail, 1% specials, interleaved by a seeded choice."""
+    a, b = DOMAINS_F64[fn]
+    k = f"{key}/{fn}/{operand}"
+    main = uniform(k + "/main", n, a, b)
+    if fn in TRIG:
+        tail = loguniform(k + "/tail", n, 1e5, 1e300)
+    else:
+        lo = max(1e-300, 0.0 if a <= 0 <= b else min(abs(a), abs(b)))
+        hi = max(abs(a), abs(b))
+        tail = loguniform(k + "/tail", n, max(lo, 1e-300), hi, signed=a < 0)
+    spec = SPECIALS_F64[(raw(k + "/spec", n) % np.uint64(64)).astype(np.int64)]
+    c = raw(k + "/cat", n) % np.uint64(100)
+    x = np.where(c < 89, main, np.where(c < 99, tail, spec))
+    if dtype == np.float32:
+        x = x.astype(np.float32)
+    return x
