@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the elementwise math hot path on GB300.
+
+One step = one pass of every FP64 entry point of the library over its own
+2^26-element synthetic array of the full-FP64-set workload (89% uniform over
+the function's main domain, 10% log-uniform tail -- Payne-Hanek arguments
+for the trig functions -- and 1% special values; inputs resident in HBM,
+each array larger than L2).  Metric: Gelem/s (all elements of the step /
+step time) with the per-function Gelem/s and the roofline fraction of the
+dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank on its own arrays
+(weak scaling, no collective on the data path).  --impl reference times the
+scalar C oracle on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=1 << 26, help="elements per function")
+    p.add_argument("--fns", default="", help="comma list of entry points (default: every FP64 one)")
+    p.add_argument("--cpu-sample", type=int, default=1 << 18, help="oracle sample per function")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v, device):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def default_fns(sleefcu):
+    return [e for e in sleefcu.entry_points() if e.endswith("_f64")]
+
+
+def build_inputs(sleefcu, names, n, rank, torch, device):
+    from paper_2001_09258_gb300 import inputs as I
+    host, dev = {}, {}
+    for name in names:
+        fn = name.split("_")[0]
+        if fn in host:
+            continue
+        xs = [I.workload(fn, n, key=f"c2/rank{rank}", operand=0)]
+        if sleefcu.FUNCS[fn] == "b":
+            xs.append(I.workload(fn, n, key=f"c2/rank{rank}", operand=1))
+        host[fn] = xs
+        dev[fn] = [torch.from_numpy(a).to(device) for a in xs]
+    return host, dev
+
+
+def launch(sleefcu, name, ins, outs, stream_ptr):
+    f = sleefcu.raw(name)
+    kind = sleefcu.FUNCS[name.split("_")[0]]
+    n = ins[0].numel()
+    if kind == "u":
+        rc = f(ins[0].data_ptr(), outs[0].data_ptr(), n, stream_ptr)
+    elif kind == "b":
+        rc = f(ins[0].data_ptr(), ins[1].data_ptr(), outs[0].data_ptr(), n, stream_ptr)
+    else:
+        rc = f(ins[0].data_ptr(), outs[0].data_ptr(), outs[1].data_ptr(), n, stream_ptr)
+    if rc != 0:
+        raise RuntimeError(f"{name}: {sleefcu.last_error()}")
+
+
+def fp64_pipe_peak(sleefcu, torch, device):
+    """Measured FP64 FMA-pipe throughput (ops/s) with the library's probe."""
+    props = torch.cuda.get_device_properties(device)
+    blocks = props.multi_processor_count * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    st = torch.cuda.current_stream(device)
+    sp = ctypes.c_void_p(st.cuda_stream)
+    iters = 2048
+    for _ in range(2):
+        sleefcu.lib().sleefcu_probe_dfma(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
+    best = None
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sleefcu.lib().sleefcu_probe_dfma(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
+        b.record(st)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return blocks * 256.0 * iters * 8 / (best * 1e-3)
+
+
+def cpu_baseline(names, n_sample, rank):
+    """The oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle
+    from paper_2001_09258_gb300 import inputs as I
+    threads = oracle.default_threads()
+    total_el, total_s = 0, 0.0
+    for name in names:
+        fn = name.split("_")[0]
+        x = I.workload(fn, n_sample, key=f"c2/rank{rank}", operand=0)
+        y = I.workload(fn, n_sample, key=f"c2/rank{rank}", operand=1) if oracle.kind(name) in (2, 12) else None
+        oracle.apply(name, x[:1024], None if y is None else y[:1024], nthreads=threads)
+        t = time.perf_counter()
+        oracle.apply(name, x, y, nthreads=threads)
+        total_s += time.perf_counter() - t
+        total_el += n_sample
+    return total_el, total_s, threads
+
+
+def run_reference(args, ws, rank):
+    names = args.fns.split(",") if args.fns else None
+    import paper_2001_09258_gb300 as sleefcu
+    names = names or default_fns(sleefcu)
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(names, max(1024, args.cpu_sample // 16), 0)
+    times = []
+    el = 0
+    thr = 1
+    for _ in range(args.steps):
+        e, s, thr = cpu_baseline(names, args.cpu_sample, 0)
+        times.append(s)
+        el = e
+    t = sum(times)
+    val = el * args.steps / t / 1e9
+    line = {
+        "impl": "reference", "metric": "Gelem/s (full FP64 C99 set, u10+u35) at max-ULP <=1.0/3.5",
+        "value": round(val, 6), "unit": "Gelem/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"full FP64 set mixed workload, oracle sample of {args.cpu_sample} "
+                               f"elements per entry point", "entry_points": names},
+        "cpu_baseline": {"value": round(val, 6), "unit": "Gelem/s", "cores": thr, "kind": "oracle",
+                         "sample": f"{args.cpu_sample} elements per entry point of the same workload"},
+        "e2e": {"value": round(val, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import paper_2001_09258_gb300 as sleefcu
+    from paper_2001_09258_gb300 import opcounts
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    names = args.fns.split(",") if args.fns else default_fns(sleefcu)
+    n = args.n
+    host, dev = build_inputs(sleefcu, names, n, rank, torch, device)
+    outs = {}
+    for name in names:
+        fn = name.split("_")[0]
+        k = 2 if sleefcu.FUNCS[fn] == "sc" else 1
+        outs[name] = [torch.empty(n, dtype=torch.float64, device=device) for _ in range(k)]
+    st = torch.cuda.current_stream(device)
+    sp = ctypes.c_void_p(st.cuda_stream)
+
+    def step(evs=None):
+        for i, name in enumerate(names):
+            if evs is not None:
+                evs[i].record(st)
+            launch(sleefcu, name, dev[name.split("_")[0]], outs[name], sp)
+        if evs is not None:
+            evs[len(names)].record(st)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else 3):
+        step()
+    torch.cuda.synchronize()
+    peak_fp64 = fp64_pipe_peak(sleefcu, torch, device) if rank == 0 else None
+
+    per_fn_ms = {name: [] for name in names}
+    with Clocks(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        allev = []
+        t0.record(st)
+        for _ in range(args.steps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+            step(evs)
+            allev.append(evs)
+        t1.record(st)
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms = t0.elapsed_time(t1)
+    for evs in allev:
+        for i, name in enumerate(names):
+            per_fn_ms[name].append(evs[i].elapsed_time(evs[i + 1]))
+    ms_max = allmax(ws, ms, device)
+    total_el = n * len(names) * args.steps * ws
+    value = total_el / (ms_max * 1e-3) / 1e9
+
+    # e2e: the public API from pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hin = {fn: [torch.from_numpy(a).pin_memory() for a in xs] for fn, xs in host.items()}
+        hout = {name: [torch.empty(n, dtype=torch.float64).pin_memory() for _ in outs[name]] for name in names}
+        h2d = sum(sum(a.numel() * 8 for a in hin[nm.split("_")[0]]) for nm in names)
+        d2h = sum(sum(a.numel() * 8 for a in hout[nm]) for nm in names)
+
+        def e2e_step():
+            for name in names:
+                fn = name.split("_")[0]
+                for d, h in zip(dev[fn], hin[fn]):
+                    d.copy_(h, non_blocking=True)
+                launch(sleefcu, name, dev[fn], outs[name], sp)
+                for h, d in zip(hout[name], outs[name]):
+                    h.copy_(d, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(st)
+        torch.cuda.synchronize()
+        barrier(ws)
+        e_ms = allmax(ws, a.elapsed_time(b), device)
+        e2e = {"value": round(total_el / (e_ms * 1e-3) / 1e9, 4), "unit": "Gelem/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+    avg = {name: statistics.mean(v) for name, v in per_fn_ms.items()}
+    per_fn = {name: round(n / (avg[name] * 1e-3) / 1e9, 3) for name in names}
+    dom = max(names, key=lambda nm: avg[nm])
+    ops = opcounts.ops_per_launch(dom, host[dom.split("_")[0]][0])
+    achieved = ops / (avg[dom] * 1e-3)
+    roof = {"kernel": dom, "bound": "alu", "pipe": "fp64",
+            "achieved": round(achieved / 1e12, 5), "peak": round(peak_fp64 / 1e12, 5),
+            "unit": "Tops/s (FP64 pipe: add, mul, fma, rint, div, sqrt each one op)",
+            "frac": round(achieved / peak_fp64, 4),
+            "peak_source": "measured in this run with sleefcu_probe_dfma (8 independent FMA chains "
+                           "per thread, all SMs)",
+            "ops_per_element": round(ops / n, 3), "traffic": None}
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tr = json.load(open(prof)).get(dom)
+            if tr:
+                import hashlib
+                src = open(os.path.join(ROOT, "paper_2001_09258_gb300", "csrc", tr["source"]), "rb").read()
+                if hashlib.sha256(src).hexdigest()[:16] == tr["source_sha"]:
+                    roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
+        except (OSError, ValueError, KeyError):
+            pass
+    cpu = None
+    if not args.no_cpu_baseline:
+        el, s, thr = cpu_baseline(names, args.cpu_sample, rank)
+        cpu = {"value": round(el / s / 1e9, 6), "unit": "Gelem/s", "cores": thr, "kind": "oracle",
+               "sample": f"{args.cpu_sample} elements of each entry point's workload array "
+                         f"({len(names)} entry points)"}
+    line = {
+        "metric": "Gelem/s (full FP64 C99 set, u10+u35) at max-ULP <=1.0/3.5",
+        "value": round(value, 4), "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "full FP64 C99 set, mixed 89% main domain / 10% log-uniform tail "
+                               "(trig: Payne-Hanek arguments 1e5..1e300) / 1% specials",
+                   "n_per_function": n, "entry_points": names, "l2": "inputs larger than L2 (no flush)"},
+        "per_function_gelem_s": per_fn,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": len(names) * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

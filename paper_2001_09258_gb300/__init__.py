@@ -1,0 +1,134 @@
+"""sleefcu: GB300-native elementwise C99 math functions (SLEEF's method).
+
+Thin Python binding over the C ABI in include/sleefcu.h (libsleefcu.so, built
+in-tree by _build.py).  This module only marshals arguments: every step of
+the computation runs in the CUDA kernels.  There is no CPU fallback: if the
+library is missing or fails to load, every call raises.
+
+    import paper_2001_09258_gb300 as sleefcu
+    y = sleefcu.sin(x)                # x: CUDA float64 tensor, 1-ULP variant
+    y = sleefcu.sin(x, ulp=35)        # 3.5-ULP variant
+    s, c = sleefcu.sincos(x)
+    sleefcu.call("pow_u10_f64", x, y, out=z)   # any entry point by name
+"""
+import ctypes
+import os
+
+from . import inputs  # noqa: F401  (seeded synthetic inputs; no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsleefcu.so")
+
+# (function, kind) for every entry point; kind: "u" unary, "b" binary (x, y),
+# "sc" one input two outputs.  Each is exported for the listed accuracies and
+# precisions as sleefcu_<fn>_<acc>_<prec>.
+FUNCS = {
+    "sin": "u", "cos": "u", "tan": "u", "sincos": "sc",
+}
+PRECS = {"sin": ("f64",), "cos": ("f64",), "tan": ("f64",), "sincos": ("f64",)}
+ACCS = ("u10", "u35")
+
+_lib = None
+
+
+class SleefcuError(RuntimeError):
+    pass
+
+
+def entry_points():
+    """All C-ABI entry point names this binding knows (without the prefix)."""
+    out = []
+    for fn, kind in FUNCS.items():
+        for prec in PRECS[fn]:
+            for acc in ACCS:
+                out.append(f"{fn}_{acc}_{prec}")
+    return out
+
+
+def lib():
+    """Load libsleefcu.so (building it first if it does not exist)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import _build
+            _build.build()
+        try:
+            L = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise SleefcuError(f"cannot load {LIB_PATH}: {e}") from e
+        L.sleefcu_last_error.restype = ctypes.c_char_p
+        L.sleefcu_version.restype = ctypes.c_char_p
+        for probe in ("sleefcu_probe_dfma", "sleefcu_probe_ffma"):
+            getattr(L, probe).restype = ctypes.c_int
+            getattr(L, probe).argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        for name in entry_points():
+            fn = name.split("_")[0]
+            f = getattr(L, "sleefcu_" + name)
+            f.restype = ctypes.c_int
+            nptr = {"u": 2, "b": 3, "sc": 3}[FUNCS[fn]]
+            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def last_error():
+    return lib().sleefcu_last_error().decode()
+
+
+def raw(name):
+    """The ctypes function of entry point sleefcu_<name>."""
+    return getattr(lib(), "sleefcu_" + name)
+
+
+def _check(rc, name):
+    if rc != 0:
+        raise SleefcuError(f"sleefcu_{name} returned {rc}: {last_error()}")
+
+
+def call(name, x, y=None, out=None, out2=None, stream=None):
+    """Call entry point `name` on CUDA tensors; allocates outputs with
+    empty_like when not given.  Returns out, or (out, out2) for sincos."""
+    import torch
+    fn = name.split("_")[0]
+    kind = FUNCS[fn]
+    if not x.is_cuda:
+        raise SleefcuError("sleefcu works on CUDA tensors only")
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    if kind == "sc" and out2 is None:
+        out2 = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    sp = ctypes.c_void_p(st.cuda_stream)
+    f = raw(name)
+    if kind == "u":
+        rc = f(x.data_ptr(), out.data_ptr(), x.numel(), sp)
+    elif kind == "b":
+        y = y.contiguous()
+        rc = f(x.data_ptr(), y.data_ptr(), out.data_ptr(), x.numel(), sp)
+    else:
+        rc = f(x.data_ptr(), out.data_ptr(), out2.data_ptr(), x.numel(), sp)
+    _check(rc, name)
+    return (out, out2) if kind == "sc" else out
+
+
+def _prec_of(x):
+    import torch
+    return {torch.float64: "f64", torch.float32: "f32"}[x.dtype]
+
+
+def _mk(fn):
+    def f(x, y=None, ulp=10, out=None, out2=None):
+        name = f"{fn}_u{ulp}_{_prec_of(x)}"
+        if FUNCS[fn] == "b":
+            return call(name, x, y, out=out)
+        if FUNCS[fn] == "sc":
+            return call(name, x, out=out, out2=out2)
+        return call(name, x, out=out)
+    f.__name__ = fn
+    f.__doc__ = f"Elementwise {fn} via sleefcu_{fn}_u<ulp>_<prec>."
+    return f
+
+
+for _fn in FUNCS:
+    globals()[_fn] = _mk(_fn)

@@ -1,0 +1,220 @@
+// Shared device helpers and the elementwise launch machinery of libsleefcu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/sleefcu.h"
+#include "sleefcu_dd.cuh"
+
+namespace sleefcu {
+
+// ---------------- bit helpers (integer pipe) ----------------
+__device__ __forceinline__ uint64_t bits(double d) { return (uint64_t)__double_as_longlong(d); }
+__device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ uint32_t fbits(float f) { return (uint32_t)__float_as_uint(f); }
+__device__ __forceinline__ float from_fbits(uint32_t b) { return __uint_as_float(b); }
+__device__ __forceinline__ double neg_if(double v, bool c) { return from_bits(bits(v) ^ ((uint64_t)c << 63)); }
+__device__ __forceinline__ float negf_if(float v, bool c) { return from_fbits(fbits(v) ^ ((uint32_t)c << 31)); }
+constexpr uint64_t ABS64 = 0x7FFFFFFFFFFFFFFFull;
+constexpr uint64_t EXP64 = 0x7FF0000000000000ull;
+constexpr uint64_t QNAN64 = 0x7FF8000000000000ull;
+constexpr uint32_t ABS32 = 0x7FFFFFFFu;
+constexpr uint32_t EXP32 = 0x7F800000u;
+constexpr uint32_t QNAN32 = 0x7FC00000u;
+__device__ __forceinline__ bool is_nan_b(uint64_t b) { return (b & ABS64) > EXP64; }
+__device__ __forceinline__ bool is_finite_b(uint64_t b) { return (b & EXP64) != EXP64; }
+// canonical quiet NaN for any NaN result
+__device__ __forceinline__ double canon(double y) { return is_nan_b(bits(y)) ? from_bits(QNAN64) : y; }
+__device__ __forceinline__ float canonf(float y) {
+  return (fbits(y) & ABS32) > EXP32 ? from_fbits(QNAN32) : y;
+}
+
+// For an integer-valued double k (|k| < 2^63 or a multiple of 4 above),
+// k mod 4 in two's complement, computed on the integer pipe.
+__device__ __forceinline__ int low2_of_int(double k) {
+  uint64_t b = bits(k);
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  uint64_t m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  uint64_t iv = e < 0 ? 0 : (e <= 52 ? (m >> (52 - e)) : (e < 64 ? (m << (e - 52)) : 0));
+  int v = (int)(iv & 3);
+  return (b >> 63) ? ((-v) & 3) : v;
+}
+__device__ __forceinline__ int low2_of_intf(float k) {
+  uint32_t b = fbits(k);
+  int e = (int)((b >> 23) & 0xFF) - 127;
+  uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+  uint32_t iv = e < 0 ? 0 : (e <= 23 ? (m >> (23 - e)) : (e < 32 ? (m << (e - 23)) : 0));
+  int v = (int)(iv & 3);
+  return (b >> 31) ? ((-v) & 3) : v;
+}
+
+// ---------------- Estrin's scheme ----------------
+// E(c, n) = c[0] for n = 1, else fma(t^m, E(c+m, n-m), E(c, m)) with m the
+// largest power of two below n (Section 5's polynomial evaluation).  pw[k]
+// holds t^(2^k).
+template <int N>
+struct Estrin {
+  static constexpr int M = (N <= 2) ? 1 : (N <= 4) ? 2 : (N <= 8) ? 4 : (N <= 16) ? 8 : 16;
+  static constexpr int K = (M == 1) ? 0 : (M == 2) ? 1 : (M == 4) ? 2 : (M == 8) ? 3 : 4;
+  __device__ __forceinline__ static double d(const double *c, const double *pw) {
+    return __fma_rn(pw[K], Estrin<N - M>::d(c + M, pw), Estrin<M>::d(c, pw));
+  }
+  __device__ __forceinline__ static float f(const float *c, const float *pw) {
+    return __fmaf_rn(pw[K], Estrin<N - M>::f(c + M, pw), Estrin<M>::f(c, pw));
+  }
+};
+template <>
+struct Estrin<1> {
+  __device__ __forceinline__ static double d(const double *c, const double *) { return c[0]; }
+  __device__ __forceinline__ static float f(const float *c, const float *) { return c[0]; }
+};
+template <int N>
+__device__ __forceinline__ double poly(double t, const double (&c)[N]) {
+  double pw[5];
+  pw[0] = t;
+  if (N > 2) pw[1] = __dmul_rn(t, t);
+  if (N > 4) pw[2] = __dmul_rn(pw[1], pw[1]);
+  if (N > 8) pw[3] = __dmul_rn(pw[2], pw[2]);
+  if (N > 16) pw[4] = __dmul_rn(pw[3], pw[3]);
+  return Estrin<N>::d(c, pw);
+}
+template <int N>
+__device__ __forceinline__ float polyf(float t, const float (&c)[N]) {
+  float pw[5];
+  pw[0] = t;
+  if (N > 2) pw[1] = __fmul_rn(t, t);
+  if (N > 4) pw[2] = __fmul_rn(pw[1], pw[1]);
+  if (N > 8) pw[3] = __fmul_rn(pw[2], pw[2]);
+  if (N > 16) pw[4] = __fmul_rn(pw[3], pw[3]);
+  return Estrin<N>::f(c, pw);
+}
+
+// ---------------- elementwise kernels ----------------
+constexpr int kBlock = 256;
+
+// unary: out[i] = F(x[i]); VEC processes pairs with 16-byte accesses
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_unary64(const double *x, double *out, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t np = n >> 1;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    double2 *o2 = reinterpret_cast<double2 *>(out);
+    for (size_t i = tid; i < np; i += stride) {
+      double2 v = __ldcs(x2 + i);
+      double2 r;
+      r.x = f(v.x);
+      r.y = f(v.y);
+      __stcs(o2 + i, r);
+    }
+    if ((n & 1) && tid == 0) out[n - 1] = f(x[n - 1]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) out[i] = f(x[i]);
+  }
+}
+
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_binary64(const double *x, const double *y, double *out, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t np = n >> 1;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    const double2 *y2 = reinterpret_cast<const double2 *>(y);
+    double2 *o2 = reinterpret_cast<double2 *>(out);
+    for (size_t i = tid; i < np; i += stride) {
+      double2 a = __ldcs(x2 + i), b = __ldcs(y2 + i);
+      double2 r;
+      r.x = f(a.x, b.x);
+      r.y = f(a.y, b.y);
+      __stcs(o2 + i, r);
+    }
+    if ((n & 1) && tid == 0) out[n - 1] = f(x[n - 1], y[n - 1]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) out[i] = f(x[i], y[i]);
+  }
+}
+
+// two outputs (sincos): F::operator()(x, &a, &b)
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_dual64(const double *x, double *o1, double *o2, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t np = n >> 1;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    double2 *a2 = reinterpret_cast<double2 *>(o1);
+    double2 *b2 = reinterpret_cast<double2 *>(o2);
+    for (size_t i = tid; i < np; i += stride) {
+      double2 v = __ldcs(x2 + i);
+      double2 a, b;
+      f(v.x, a.x, b.x);
+      f(v.y, a.y, b.y);
+      __stcs(a2 + i, a);
+      __stcs(b2 + i, b);
+    }
+    if ((n & 1) && tid == 0) f(x[n - 1], o1[n - 1], o2[n - 1]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) f(x[i], o1[i], o2[i]);
+  }
+}
+
+// ---------------- host side ----------------
+void set_error(const char *fmt, ...);
+sleefcu_status check_launch(const char *what);
+int grid_for(const void *kernel, size_t work_items);
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+template <class F>
+sleefcu_status launch_unary64(const char *name, const double *x, double *out, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(out)) {
+    auto k = k_unary64<F, true>;
+    k<<<grid_for((const void *)k, (n + 1) / 2), kBlock, 0, st>>>(x, out, n);
+  } else {
+    auto k = k_unary64<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, out, n);
+  }
+  return check_launch(name);
+}
+
+template <class F>
+sleefcu_status launch_binary64(const char *name, const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(y) && aligned16(out)) {
+    auto k = k_binary64<F, true>;
+    k<<<grid_for((const void *)k, (n + 1) / 2), kBlock, 0, st>>>(x, y, out, n);
+  } else {
+    auto k = k_binary64<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, y, out, n);
+  }
+  return check_launch(name);
+}
+
+template <class F>
+sleefcu_status launch_dual64(const char *name, const double *x, double *o1, double *o2, size_t n,
+                             sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(o1) && aligned16(o2)) {
+    auto k = k_dual64<F, true>;
+    k<<<grid_for((const void *)k, (n + 1) / 2), kBlock, 0, st>>>(x, o1, o2, n);
+  } else {
+    auto k = k_dual64<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, o1, o2, n);
+  }
+  return check_launch(name);
+}
+
+}  // namespace sleefcu
