@@ -318,7 +318,8 @@ def main():
     avg = {name: statistics.mean(v) for name, v in per_fn_ms.items()}
     per_fn = {name: round(n / (avg[name] * 1e-3) / 1e9, 3) for name in names}
     dom = max(names, key=lambda nm: avg[nm])
-    ops = opcounts.ops_per_launch(dom, host[dom.split("_")[0]][0])
+    hx = host[dom.split("_")[0]]
+    ops = opcounts.ops_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None)
     achieved = ops / (avg[dom] * 1e-3)
     roof = {"kernel": dom, "bound": "alu", "pipe": "fp64",
             "achieved": round(achieved / 1e12, 5), "peak": round(peak_fp64 / 1e12, 5),

@@ -73,6 +73,69 @@ sleefcu_status sleefcu_sincos_u10_f64(const double *x, double *out_sin, double *
 sleefcu_status sleefcu_sincos_u35_f64(const double *x, double *out_sin, double *out_cos, size_t n,
                                       sleefcu_stream stream);
 
+/* ---------------- exponential and logarithm, FP64 ----------------
+ * exp (Section 5.6): x = k ln2 + r, |r| <= ln2/2, one polynomial for e^r
+ * (13 terms u10, 11 terms u35), 2^k added to the exponent; exp(-inf) = +0,
+ * exp(+inf) = +inf, overflow to +inf, underflow to 0 with subnormals rounded
+ * once.
+ * log (Section 5.5): subnormals rescaled by 2^64, e = floor(log2(4a/3)),
+ * m = a 2^-e in [0.75, 1.5), log m = z + z^3 P(z^2) with z = 2(m-1)/(m+1);
+ * log(+-0) = -inf, log(1) = +0, log(x < 0) = NaN, log(+inf) = +inf.
+ * pow (Section 5.7): exp(y log|x|) with the logarithm and the product in
+ * double-double; out[i] = pow(x[i], y[i]); every C99 Annex F special pair
+ * (pow(x, +-0) = 1 even for NaN x, pow(+1, y) = 1, pow(x < 0, non-integer)
+ * = NaN, zero and infinite bases and exponents).  The u35 entry point runs
+ * the u10 algorithm. */
+sleefcu_status sleefcu_exp_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u10_f64(const double *x, const double *y, double *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u35_f64(const double *x, const double *y, double *out, size_t n,
+                                   sleefcu_stream stream);
+
+/* ---------------- inverse trigonometric functions, FP64 ----------------
+ * asin / acos (Section 5.3): |x| <= 0.5 directly, otherwise
+ * asin x = pi/2 - 2 asin(sqrt((1-x)/2)), acos x = 2 asin(sqrt((1-x)/2))
+ * (pi - that for x < -0.5); |x| > 1 gives NaN; asin(+-0) = +-0, acos(1) = +0.
+ * atan (Section 5.4): 1/a for |a| >= 1 and pi/2 - atan(1/a);
+ * atan(+-inf) = +-pi/2 (rounded), atan(+-0) = +-0.
+ * atan2: out[i] = atan2(x[i], y[i]) with x the ordinate (C argument order);
+ * all C99 Annex F special pairs (signed zeros select 0 or pi, infinities
+ * select pi/4, 3pi/4, pi/2, 0 or pi). */
+sleefcu_status sleefcu_asin_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asin_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u10_f64(const double *x, const double *y, double *out, size_t n,
+                                     sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u35_f64(const double *x, const double *y, double *out, size_t n,
+                                     sleefcu_stream stream);
+
+/* ---------------- floating-point remainder, FP64 ----------------
+ * fmod (Section 5.9, Algorithm 1 and the Appendix B listing): exact
+ * x - trunc(x/y) y by long division with floating-point digits, the partial
+ * remainder held exactly in double-double, one division in total; extended
+ * to every pair of doubles (quotients up to 2^2098, at most 48 steps) by
+ * dividing by power-of-two multiples of y while the quotient exceeds 2^1000.
+ * out[i] = fmod(x[i], y[i]); sign of x; fmod(x, +-0) = NaN,
+ * fmod(+-inf, y) = NaN, fmod(x, +-inf) = x for finite x.
+ * remainder: x - n y with n the integer nearest x/y (ties to even), exact;
+ * a zero result has the sign of x (IEEE 754 5.3.1); remainder(x, 0) and
+ * remainder(inf, y) are NaN; remainder(x, +-inf) = x.
+ * Results are exact, so u10 and u35 are the same operation. */
+sleefcu_status sleefcu_fmod_u10_f64(const double *x, const double *y, double *out, size_t n,
+                                    sleefcu_stream stream);
+sleefcu_status sleefcu_fmod_u35_f64(const double *x, const double *y, double *out, size_t n,
+                                    sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u10_f64(const double *x, const double *y, double *out, size_t n,
+                                         sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u35_f64(const double *x, const double *y, double *out, size_t n,
+                                         sleefcu_stream stream);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

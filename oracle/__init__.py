@@ -32,6 +32,11 @@ def lib():
         _lib.oracle_ph_reduce.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib.oracle_ph_table_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.oracle_fmod_iters.restype = ctypes.c_int
+        _lib.oracle_fmod_iters.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib.oracle_fmod_trace.restype = ctypes.c_int
+        _lib.oracle_fmod_trace.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int]
     return _lib
 
 
@@ -73,6 +78,17 @@ def apply(name, x, y=None, nthreads=None):
     if rc != 0:
         raise RuntimeError(f"oracle_apply({name}) failed: {rc}")
     return (out, out2) if out2 is not None else out
+
+
+def fmod_trace(x, y, maxk=64):
+    qs = np.zeros(maxk)
+    rs = np.zeros(maxk)
+    k = lib().oracle_fmod_trace(float(x), float(y), qs.ctypes.data, rs.ctypes.data, maxk)
+    return qs[:k], rs[:k]
+
+
+def fmod_iters(x, y):
+    return lib().oracle_fmod_iters(float(x), float(y))
 
 
 def ph_reduce(x):

@@ -7,18 +7,22 @@ Shapes (the term counts are the paper's where it gives them):
   exp_u10   Section 5.6: e^r = 1 + r + r^2 (c2 + c3 r + ... + c12 r^10), 13 terms,
             |r| <= ln2/2 (+slack), no DD
   exp_u35   the same with 11 terms
-  log_u10   Section 5.5: log m = z + z^3 P(z^2), z = 2(m-1)/(m+1), 7 terms
-            (log m = 2 atanh(z/2) is odd in z), |z| <= 0.4
-  log_u35   6 terms
+  log_u10   Section 5.5: log m = z + z^3 P(z^2), z = 2(m-1)/(m+1)
+            (log m = 2 atanh(z/2) is odd in z), |z| <= 0.4; 9 terms: the
+            paper's 7 terms reach only 2^-49 relative error on this domain
+  log_u35   8 terms
   powlog    Section 5.7: the internal log of pow, 11 terms, first correction
             coefficient as a DD pair
   powexp    Section 5.7: the internal exp of pow, e^r = 1 + r + r^2/2 +
             r^3 (c3 + ... + c12 r^9), 13 terms
-  asin_u10  Section 5.3: asin u = u + u^3 P(u^2) on [0, 0.5], 12 terms
-  asin_u35  10 terms
-  atan_u10  Section 5.4: atan s = s + s^3 P(s^2) on [0, 1], 20 terms, the
-            first correction coefficient as a DD pair
-  atan_u35  18 terms
+  asin_u10  Section 5.3: asin u = u + u^3 P(u^2) on [0, 0.5]; 14 terms: the
+            paper's 12 terms reach 2^-52 relative error, too much for 1 ULP
+  asin_u35  12 terms
+  atan_u10  Section 5.4: atan s = s + s^3 P(s^2) on [0, 1], the first
+            correction coefficient as a DD pair; 22 terms: the paper's 20
+            terms reach 2^-55 relative error, which with the final rounding
+            leaves no margin under 1 ULP
+  atan_u35  20 terms, all in double
 """
 import os
 import sys
@@ -97,16 +101,16 @@ def atan_w(t):
 
 
 JOBS = {
-    "exp_u10": lambda: fit_rounded(exp_u, exp_w, range(11), ["d"] * 11, -LN2H, LN2H),
-    "exp_u35": lambda: fit_rounded(exp_u, exp_w, range(9), ["d"] * 9, -LN2H, LN2H),
-    "log_u10": lambda: fit_rounded(log_g, log_w, range(6), ["d"] * 6, 0, mp.mpf("0.4001") ** 2),
-    "log_u35": lambda: fit_rounded(log_g, log_w, range(5), ["d"] * 5, 0, mp.mpf("0.4001") ** 2),
+    "exp_u10": lambda: fit_rounded(exp_u, exp_w, range(11), ["d"] * 11, -LN2H, LN2H, n_grid=4000),
+    "exp_u35": lambda: fit_rounded(exp_u, exp_w, range(9), ["d"] * 9, -LN2H, LN2H, n_grid=4000),
+    "log_u10": lambda: fit_rounded(log_g, log_w, range(8), ["d"] * 8, 0, mp.mpf("0.4001") ** 2),
+    "log_u35": lambda: fit_rounded(log_g, log_w, range(7), ["d"] * 7, 0, mp.mpf("0.4001") ** 2),
     "powlog": lambda: fit_rounded(log_g, log_w, range(10), ["dd"] + ["d"] * 9, 0, mp.mpf("0.4001") ** 2),
     "powexp": lambda: fit_rounded(exp_v, exp_wv, range(10), ["d"] * 10, -LN2H, LN2H),
-    "asin_u10": lambda: fit_rounded(asin_g, asin_w, range(11), ["d"] * 11, 0, mp.mpf("0.25")),
-    "asin_u35": lambda: fit_rounded(asin_g, asin_w, range(9), ["d"] * 9, 0, mp.mpf("0.25")),
-    "atan_u10": lambda: fit_rounded(atan_g, atan_w, range(19), ["dd"] + ["d"] * 18, 0, 1, n_grid=4000),
-    "atan_u35": lambda: fit_rounded(atan_g, atan_w, range(17), ["d"] * 17, 0, 1, n_grid=4000),
+    "asin_u10": lambda: fit_rounded(asin_g, asin_w, range(13), ["d"] * 13, 0, mp.mpf("0.25"), n_grid=4000),
+    "asin_u35": lambda: fit_rounded(asin_g, asin_w, range(11), ["d"] * 11, 0, mp.mpf("0.25"), n_grid=4000),
+    "atan_u10": lambda: fit_rounded(atan_g, atan_w, range(21), ["dd"] + ["d"] * 20, 0, 1, n_grid=4000),
+    "atan_u35": lambda: fit_rounded(atan_g, atan_w, range(19), ["d"] * 19, 0, 1, n_grid=4000),
 }
 
 if __name__ == "__main__":

@@ -171,11 +171,43 @@ def max_error(f, w, terms, a, b, n=20000, dps=50):
         return m
 
 
+def _store(c, fmt):
+    """(stored value(s), exact value of what is stored) for one coefficient"""
+    if fmt == "d":
+        v = to_double(c)
+        return v, mp.mpf(v)
+    if fmt == "f":
+        v = to_float(c)
+        return v, mp.mpf(v)
+    if fmt == "dd":
+        hi, lo = split_dd(c)
+        return (hi, lo), mp.mpf(hi) + mp.mpf(lo)
+    if fmt == "ff":
+        hi, lo = split_ff(c)
+        return (hi, lo), mp.mpf(hi) + mp.mpf(lo)
+    v = float(_round_to_bits(c, fmt[1]))
+    return v, mp.mpf(v)
+
+
 def fit_rounded(f, w, exps, formats, a, b, fixed=(), **kw):
-    """Fit, then round coefficient j (in the order given) to formats[j]:
-    'd' double, 'dd' double-double (hi, lo), 'f' float, 'ff' float-float,
-    ('bits', k) k-bit mantissa; after each rounding refit the rest.
-    Returns (list of (exponent, stored value(s)), max weighted error)."""
+    """Fit, then store the coefficients in formats[j]: 'd' double, 'dd'
+    double-double (hi, lo), 'f' float, 'ff' float-float, ('bits', k) k-bit
+    mantissa.  Two candidates: (1) round coefficient j (lowest degree first)
+    and refit the rest after each rounding; (2) round the free minimax fit
+    directly.  Returns the one with the smaller max weighted error as
+    (list of (exponent, stored value(s)), max weighted error)."""
+    seq = _fit_sequential(f, w, exps, formats, a, b, fixed, **kw)
+    cs, _ = remez(f, w, list(exps), a, b, fixed=list(fixed), **kw)
+    stored, terms = [], list(fixed)
+    for e, c, fmt in zip(exps, cs, formats):
+        v, exact = _store(c, fmt)
+        stored.append((e, v))
+        terms.append((e, exact))
+    naive = (stored, max_error(f, w, terms, a, b))
+    return seq if seq[1] <= naive[1] else naive
+
+
+def _fit_sequential(f, w, exps, formats, a, b, fixed=(), **kw):
     fixed = list(fixed)
     stored = []
     exps = list(exps)

@@ -20,6 +20,28 @@ double oracle_tan_u35_f64(double);
 void oracle_sincos_u10_f64(double, double *, double *);
 void oracle_sincos_u35_f64(double, double *, double *);
 
+double oracle_exp_u10_f64(double);
+double oracle_exp_u35_f64(double);
+double oracle_log_u10_f64(double);
+double oracle_log_u35_f64(double);
+double oracle_pow_u10_f64(double, double);
+double oracle_pow_u35_f64(double, double);
+double oracle_asin_u10_f64(double);
+double oracle_asin_u35_f64(double);
+double oracle_acos_u10_f64(double);
+double oracle_acos_u35_f64(double);
+double oracle_atan_u10_f64(double);
+double oracle_atan_u35_f64(double);
+double oracle_atan2_u10_f64(double, double);
+double oracle_atan2_u35_f64(double, double);
+
+double oracle_fmod_u10_f64(double, double);
+double oracle_fmod_u35_f64(double, double);
+double oracle_remainder_u10_f64(double, double);
+double oracle_remainder_u35_f64(double, double);
+int oracle_fmod_iters(double, double);
+int oracle_fmod_trace(double, double, double *, double *, int);
+
 int oracle_apply(const char *name, const void *x, const void *y, void *out, void *out2,
                  size_t n, int nthreads);
 #endif

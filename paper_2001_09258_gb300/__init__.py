@@ -24,8 +24,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsleefcu.so")
 # precisions as sleefcu_<fn>_<acc>_<prec>.
 FUNCS = {
     "sin": "u", "cos": "u", "tan": "u", "sincos": "sc",
+    "asin": "u", "acos": "u", "atan": "u", "atan2": "b",
+    "exp": "u", "log": "u", "pow": "b",
+    "fmod": "b", "remainder": "b",
 }
-PRECS = {"sin": ("f64",), "cos": ("f64",), "tan": ("f64",), "sincos": ("f64",)}
+PRECS = {fn: ("f64",) for fn in FUNCS}
 ACCS = ("u10", "u35")
 
 _lib = None

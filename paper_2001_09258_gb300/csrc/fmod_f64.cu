@@ -1,0 +1,132 @@
+// FP64 fmod and remainder for sm_103a (exact results; the u35 entry points
+// are the same kernels).
+//
+// Section 5.9 (Algorithm 1) and the Appendix B listing: the remainder is
+// found by long division with floating-point digits, r_{k+1} = r_k - q_k d,
+// q_k = trunc(nextafter(r_k, 0) * nextafter(1/d, 0)) with the fix-ups for
+// 1 < r/d < 3 and r == d, r held exactly as a double-double, one division in
+// total.  Extension for quotients beyond DBL_MAX (the listing's stated
+// limit): each step divides by D = d 2^j, j = max(kmin, ilogb(r) - ilogb(d) -
+// 1000), which is the listing itself whenever n/d < 2^1000; a subnormal d
+// (kmin = 54) is rescaled by 2^54 once r < d 2^54, as in the listing.
+// Elements are grouped in divergence-sorted tiles by their expected trip
+// count ceil((ilogb n - ilogb d) / 52), so the lanes of a warp leave the loop
+// together (the listing's "terminate once every element of the vector is
+// done").  Comparisons of the non-negative operands run on the integer pipe.
+//
+// remainder: fmod(|x|, 2|y|), then |y| subtracted once or twice by comparing
+// 2 r with |y| (ties to the even quotient), every subtraction exact.
+#include "sleefcu_common.cuh"
+
+namespace sleefcu {
+namespace fmod64 {
+
+constexpr int MAXIT = 48;
+constexpr uint64_t DMIN = 0x0010000000000000ull;   // bits of DBL_MIN
+constexpr uint64_t INF = 0x7FF0000000000000ull;
+constexpr uint64_t DMAX = 0x7FEFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ double rdown(double v) {   // nextafter(v, 0) for v > 0 finite
+  return from_bits(bits(v) - 1);
+}
+__device__ __forceinline__ int ilogb_n(uint64_t b) { return (int)((b >> 52) & 0x7FF) - 1023; }
+__device__ __forceinline__ double scale_n(double v, int j) {   // v normal, v 2^j normal
+  return from_bits(bits(v) + ((uint64_t)(int64_t)j << 52));
+}
+
+// one step of Algorithm 1 (listing's fix-ups), r >= 0
+__device__ __forceinline__ d2 step(d2 r, double D, double rD) {
+  double q = trunc(__dmul_rn(rdown(r.x), rD));
+  uint64_t brx = bits(r.x), bD = bits(D);
+  bool gt = brx > bD;                                    // r.x > D
+  if (bits(__dmul_rn(3.0, D)) > brx && gt) q = 2.0;
+  if (bits(__dmul_rn(2.0, D)) > brx && gt) q = 1.0;
+  if (brx == bD) q = ((bits(r.y) >> 63) == 0 || (bits(r.y) & ABS64) == 0) ? 1.0 : 0.0;
+  return norm_d2(add_d2d2(r, mul_dd(q, -D)));
+}
+
+// |x| mod |y| for finite n >= 0 and finite d > 0
+__device__ __forceinline__ double fmod_abs(double n, double d) {
+  uint64_t bd = bits(d);
+  bool sub = bd < DMIN;
+  int kmin = sub ? 54 : 0;
+  double dmin = sub ? __dmul_rn(d, 0x1p54) : d;          // exact
+  double rd0 = rdown(__ddiv_rn(1.0, dmin));
+  int edm = ilogb_n(bits(dmin));                           // ilogb(d) + kmin
+  d2 r = D2(n, 0.0);
+  uint64_t bdmin = bits(dmin);
+  for (int it = 0; it < MAXIT && (int64_t)bits(r.x) >= (int64_t)bdmin; it++) {
+    int j = ilogb_n(bits(r.x)) - edm - 1000;             // j - kmin
+    if (j < 0) j = 0;
+    r = step(r, j ? scale_n(dmin, j) : dmin, j ? scale_n(rd0, -j) : rd0);
+  }
+  double ret;
+  if (sub) {
+    r = D2(__dmul_rn(r.x, 0x1p54), __dmul_rn(r.y, 0x1p54));
+    for (int k = 0; k < 4 && (int64_t)bits(r.x) >= (int64_t)bdmin; k++) r = step(r, dmin, rd0);
+    ret = __dmul_rn(r.x, 0x1p-54);
+    if (__dadd_rn(r.x, r.y) == dmin) ret = 0.0;
+  } else {
+    ret = r.x;
+    if (__dadd_rn(r.x, r.y) == d) ret = 0.0;
+  }
+  return ret;
+}
+
+// expected trip-count class of |x| mod |y| (for the tile sort)
+__device__ __forceinline__ int trip_class(double x, double y) {
+  int en = ilogb_n(bits(x) & ABS64), ed = ilogb_n(bits(y) & ABS64);
+  int t = (en - ed + 51) / 52;
+  return t < 0 ? 0 : (t > 15 ? 15 : t);
+}
+
+struct FmodF {
+  static constexpr int NCLS = 16;
+  __device__ static int cls(double x, double y) { return trip_class(x, y); }
+  __device__ double operator()(double x, double y) const {
+    uint64_t bx = bits(x), by = bits(y);
+    uint64_t an = bx & ABS64, ad = by & ABS64;
+    bool ok = an < INF && ad != 0 && ad < INF;
+    double ret = fmod_abs(ok ? from_bits(an) : 0.0, ok ? from_bits(ad) : 1.0);
+    ret = from_bits((bits(ret) & ABS64) | (bx & ~ABS64));          // copysign(ret, x)
+    if (an < ad) ret = x;
+    if (ad == 0 || an >= INF || ad > INF) ret = from_bits(QNAN64);
+    return canon(ret);
+  }
+};
+
+struct RemainderF {
+  static constexpr int NCLS = 16;
+  __device__ static int cls(double x, double y) { return trip_class(x, y); }
+  __device__ double operator()(double x, double y) const {
+    uint64_t bx = bits(x), by = bits(y);
+    uint64_t an = bx & ABS64, ad = by & ABS64;
+    bool ok = an < INF && ad != 0 && ad < INF;
+    double nn = ok ? from_bits(an) : 0.0, d = ok ? from_bits(ad) : 1.0;
+    double r2 = nn;
+    if (bits(d) <= 0x7FDFFFFFFFFFFFFFull) r2 = fmod_abs(nn, __dmul_rn(2.0, d));   // 2|y| finite
+    if (__dadd_rn(r2, r2) > d) {   // quotient 1, or 2 when r2 >= 3|y|/2
+      r2 = __dsub_rn(r2, d);
+      if (__dadd_rn(r2, r2) >= d) r2 = __dsub_rn(r2, d);
+    }
+    double ret = neg_if(r2, (bx >> 63) != 0);
+    if (ad == INF && an < INF) ret = x;
+    if (ad == 0 || an >= INF || ad > INF) ret = from_bits(QNAN64);
+    return canon(ret);
+  }
+};
+
+}  // namespace fmod64
+}  // namespace sleefcu
+
+using namespace sleefcu;
+
+#define BIN64(NAME, F)                                                                      \
+  extern "C" sleefcu_status sleefcu_##NAME(const double *x, const double *y, double *out,   \
+                                           size_t n, sleefcu_stream s) {                    \
+    return launch_sorted64b<fmod64::F>("sleefcu_" #NAME, x, y, out, n, s);                  \
+  }
+BIN64(fmod_u10_f64, FmodF)
+BIN64(fmod_u35_f64, FmodF)
+BIN64(remainder_u10_f64, RemainderF)
+BIN64(remainder_u35_f64, RemainderF)

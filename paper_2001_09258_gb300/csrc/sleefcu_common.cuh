@@ -163,6 +163,166 @@ __global__ void __launch_bounds__(kBlock) k_dual64(const double *x, double *o1, 
   }
 }
 
+// ---------------- divergence-sorted tiles ----------------
+// For functions whose lanes take different paths (Cody-Waite level 1 or 2,
+// Payne-Hanek, ...), a CTA loads a tile, classifies every element with
+// F::cls, scatters the elements into shared memory grouped by class and
+// evaluates them in that order, so that each warp runs one path; results are
+// gathered back and stored coalesced.  The arithmetic per element is
+// unchanged, so the output bits do not depend on the grouping.
+constexpr int kSortEPT = 4;
+constexpr int kSortTile = kBlock * kSortEPT;
+
+template <int NC>
+__device__ __forceinline__ void sort_scatter(const int (&cl)[kSortEPT], int *cnt, int *cur,
+                                             unsigned short *sidx, int tid) {
+  const unsigned lane = tid & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int j = 0; j < kSortEPT; j++) {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
+      if (m) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(&cur[c], __popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (cl[j] == c) sidx[b + __popc(m & lt)] = (unsigned short)(j * kBlock + tid);
+      }
+    }
+  }
+  (void)cnt;
+}
+
+template <int NC>
+__device__ __forceinline__ void sort_count(const int (&cl)[kSortEPT], int *cnt, int tid) {
+  const unsigned lane = tid & 31;
+  for (int j = 0; j < kSortEPT; j++) {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
+      if (lane == 0 && m) atomicAdd(&cnt[c], __popc(m));
+    }
+  }
+}
+
+// unary (NOUT = 1) or one-input-two-output (NOUT = 2) sorted kernel
+template <class F, int NOUT>
+__global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1, double *o2, size_t n) {
+  constexpr int NC = F::NCLS;
+  __shared__ double sx[kSortTile];
+  __shared__ double so[NOUT][kSortTile];
+  __shared__ unsigned short sidx[kSortTile];
+  __shared__ int cnt[NC], cur[NC];
+  F f;
+  const int tid = threadIdx.x;
+  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kSortTile;
+    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    if (tid < NC) cnt[tid] = 0;
+    __syncthreads();
+    double xv[kSortEPT];
+    int cl[kSortEPT];
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      if (e < valid) {
+        xv[j] = __ldcs(x + base + e);
+        cl[j] = F::cls(xv[j]);
+      } else {
+        xv[j] = 0.0;
+        cl[j] = -1;
+      }
+      sx[e] = xv[j];
+    }
+    sort_count<NC>(cl, cnt, tid);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
+    }
+    __syncthreads();
+    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    __syncthreads();
+    for (int k = tid; k < valid; k += kBlock) {
+      int e = sidx[k];
+      if constexpr (NOUT == 1) {
+        so[0][e] = f(sx[e]);
+      } else {
+        double a, b;
+        f.dual(sx[e], a, b);
+        so[0][e] = a;
+        so[NOUT - 1][e] = b;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      if (e < valid) {
+        __stcs(o1 + base + e, so[0][e]);
+        if constexpr (NOUT == 2) __stcs(o2 + base + e, so[NOUT - 1][e]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// binary sorted kernel: class from (x, y)
+template <class F>
+__global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const double *y, double *o, size_t n) {
+  constexpr int NC = F::NCLS;
+  __shared__ double sx[kSortTile];
+  __shared__ double sy[kSortTile];
+  __shared__ unsigned short sidx[kSortTile];
+  __shared__ int cnt[NC], cur[NC];
+  F f;
+  const int tid = threadIdx.x;
+  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kSortTile;
+    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    if (tid < NC) cnt[tid] = 0;
+    __syncthreads();
+    int cl[kSortEPT];
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      double a = 0.0, b = 0.0;
+      if (e < valid) {
+        a = __ldcs(x + base + e);
+        b = __ldcs(y + base + e);
+        cl[j] = F::cls(a, b);
+      } else {
+        cl[j] = -1;
+      }
+      sx[e] = a;
+      sy[e] = b;
+    }
+    sort_count<NC>(cl, cnt, tid);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
+    }
+    __syncthreads();
+    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    __syncthreads();
+    for (int k = tid; k < valid; k += kBlock) {
+      int e = sidx[k];
+      double r = f(sx[e], sy[e]);
+      sx[e] = r;   // each e is owned by exactly one k
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      if (e < valid) __stcs(o + base + e, sx[e]);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------- host side ----------------
 void set_error(const char *fmt, ...);
 sleefcu_status check_launch(const char *what);
@@ -214,6 +374,33 @@ sleefcu_status launch_dual64(const char *name, const double *x, double *o1, doub
     auto k = k_dual64<F, false>;
     k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, o1, o2, n);
   }
+  return check_launch(name);
+}
+
+template <class F>
+sleefcu_status launch_sorted64(const char *name, const double *x, double *out, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  auto k = k_sorted64<F, 1>;
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n);
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_sorted64_dual(const char *name, const double *x, double *o1, double *o2, size_t n,
+                                    sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  auto k = k_sorted64<F, 2>;
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n);
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_sorted64b(const char *name, const double *x, const double *y, double *out, size_t n,
+                                sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  auto k = k_sorted64b<F>;
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n);
   return check_launch(name);
 }
 

@@ -185,6 +185,16 @@ __device__ __forceinline__ double reduce_quarter_d(double x, uint64_t ab, int &q
   return __dadd_rn(r.x, r.y);
 }
 
+// reduction path of an argument: 0 level-1 Cody-Waite, 1 level-2, 2 Payne-Hanek
+// (|x| >= 1e14, infinities and NaN)
+__device__ __forceinline__ int path_of(double x) {
+  uint64_t ab = bits(x) & ABS64;
+  return ab < B15 ? 0 : (ab < B1E14 ? 1 : 2);
+}
+#define TRIG_PATHS                       \
+  static constexpr int NCLS = 3;         \
+  __device__ static int cls(double x) { return path_of(x); }
+
 // ---------------- polynomials ----------------
 // sin s = s + s t (c1 + t P(t)), t = s^2, the leading products in DD
 __device__ __forceinline__ double sin_poly_u10(d2 s) {
@@ -202,6 +212,7 @@ __device__ __forceinline__ double sin_poly_u35(double s) {
 }
 
 struct SinU10 {
+  TRIG_PATHS
   __device__ double operator()(double x) const {
     uint64_t ab = bits(x) & ABS64;
     int q;
@@ -212,6 +223,7 @@ struct SinU10 {
   }
 };
 struct CosU10 {
+  TRIG_PATHS
   __device__ double operator()(double x) const {
     uint64_t ab = bits(x) & ABS64;
     int q;
@@ -220,6 +232,7 @@ struct CosU10 {
   }
 };
 struct SinU35 {
+  TRIG_PATHS
   __device__ double operator()(double x) const {
     uint64_t ab = bits(x) & ABS64;
     int q;
@@ -230,6 +243,7 @@ struct SinU35 {
   }
 };
 struct CosU35 {
+  TRIG_PATHS
   __device__ double operator()(double x) const {
     uint64_t ab = bits(x) & ABS64;
     int q;
@@ -240,6 +254,7 @@ struct CosU35 {
 
 // tan: Appendix A listing with the level-2 Cody-Waite added
 struct TanU10 {
+  TRIG_PATHS
   __device__ double operator()(double d) const {
     uint64_t ab = bits(d) & ABS64;
     int q;
@@ -263,6 +278,7 @@ struct TanU10 {
   }
 };
 struct TanU35 {
+  TRIG_PATHS
   __device__ double operator()(double d) const {
     uint64_t ab = bits(d) & ABS64;
     int q;
@@ -290,7 +306,9 @@ __device__ __forceinline__ void sc_quadrant(int q, double &sn, double &cs) {
 }
 
 struct SinCosU10 {
-  __device__ void operator()(double d, double &os, double &oc) const {
+  TRIG_PATHS
+  __device__ void operator()(double d, double &os, double &oc) const { dual(d, os, oc); }
+  __device__ void dual(double d, double &os, double &oc) const {
     uint64_t ab = bits(d) & ABS64;
     int q;
     d2 s = reduce_quarter(d, ab, q);
@@ -312,7 +330,9 @@ struct SinCosU10 {
   }
 };
 struct SinCosU35 {
-  __device__ void operator()(double d, double &os, double &oc) const {
+  TRIG_PATHS
+  __device__ void operator()(double d, double &os, double &oc) const { dual(d, os, oc); }
+  __device__ void dual(double d, double &os, double &oc) const {
     uint64_t ab = bits(d) & ABS64;
     int q;
     double s = reduce_quarter_d(d, ab, q);
@@ -334,7 +354,7 @@ using namespace sleefcu;
 #define UNARY64(NAME, F)                                                                    \
   extern "C" sleefcu_status sleefcu_##NAME(const double *x, double *out, size_t n,          \
                                            sleefcu_stream s) {                              \
-    return launch_unary64<trig64::F>("sleefcu_" #NAME, x, out, n, s);                       \
+    return launch_sorted64<trig64::F>("sleefcu_" #NAME, x, out, n, s);                       \
   }
 UNARY64(sin_u10_f64, SinU10)
 UNARY64(sin_u35_f64, SinU35)
@@ -345,9 +365,9 @@ UNARY64(tan_u35_f64, TanU35)
 
 extern "C" sleefcu_status sleefcu_sincos_u10_f64(const double *x, double *os, double *oc, size_t n,
                                                  sleefcu_stream s) {
-  return launch_dual64<trig64::SinCosU10>("sleefcu_sincos_u10_f64", x, os, oc, n, s);
+  return launch_sorted64_dual<trig64::SinCosU10>("sleefcu_sincos_u10_f64", x, os, oc, n, s);
 }
 extern "C" sleefcu_status sleefcu_sincos_u35_f64(const double *x, double *os, double *oc, size_t n,
                                                  sleefcu_stream s) {
-  return launch_dual64<trig64::SinCosU35>("sleefcu_sincos_u35_f64", x, os, oc, n, s);
+  return launch_sorted64_dual<trig64::SinCosU35>("sleefcu_sincos_u35_f64", x, os, oc, n, s);
 }

@@ -23,20 +23,67 @@ OPS = {
     "tan_u35_f64": {"cw1": 21, "cw2": 22, "ph": 78},
     "sincos_u10_f64": {"cw1": 54, "cw2": 60, "ph": 107},
     "sincos_u35_f64": {"cw1": 21, "cw2": 22, "ph": 78},
+    "exp_u10_f64": {"all": 26},
+    "exp_u35_f64": {"all": 18},
+    "log_u10_f64": {"all": 36},
+    "log_u35_f64": {"all": 17},
+    "pow_u10_f64": {"all": 107},
+    "pow_u35_f64": {"all": 107},
+    # asin/acos: "small" |x| <= 0.5, "big" otherwise ("bigneg" x < -0.5 for acos)
+    "asin_u10_f64": {"small": 23, "big": 36},
+    "asin_u35_f64": {"small": 18, "big": 22},
+    "acos_u10_f64": {"small": 28, "big": 31, "bigneg": 36},
+    "acos_u35_f64": {"small": 20, "big": 21, "bigneg": 22},
+    # atan: "small" |x| < 1, "big" otherwise
+    "atan_u10_f64": {"small": 46, "big": 54},
+    "atan_u35_f64": {"small": 25, "big": 27},
+    # atan2: base + 5 (u35: 1) when |x| > |y| and again when y < 0
+    "atan2_u10_f64": {"base": 52, "swap": 5, "yneg": 5},
+    "atan2_u35_f64": {"base": 26, "swap": 1, "yneg": 1},
+    # fmod / remainder: 4 setup ops (division, nextafter-free scaling) plus
+    # 17 per step of the long division (trunc product 2, 3D and 2D 2, exact
+    # q*D 2, DD add 8, renormalization 3), steps counted by the oracle
+    "fmod_u10_f64": {"setup": 4, "step": 17},
+    "fmod_u35_f64": {"setup": 4, "step": 17},
+    "remainder_u10_f64": {"setup": 9, "step": 17},
+    "remainder_u35_f64": {"setup": 9, "step": 17},
 }
 
 
-def path_mix(name, x):
+def path_mix(name, x, y=None):
     """Number of elements of x on each path of entry point `name`."""
-    ax = np.abs(np.asarray(x, dtype=np.float64))
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
     fn = name.split("_")[0]
     if fn in ("sin", "cos", "tan", "sincos"):
         small = ax < 15
         mid = (ax >= 15) & (ax < 1e14)
         return {"cw1": int(small.sum()), "cw2": int(mid.sum()), "ph": int(ax.size - small.sum() - mid.sum())}
+    if fn == "asin":
+        big = int((~(ax <= 0.5)).sum())
+        return {"small": ax.size - big, "big": big}
+    if fn == "acos":
+        big = ~(ax <= 0.5)
+        bn = int((big & (x < 0)).sum())
+        return {"small": int(ax.size - big.sum()), "big": int(big.sum()) - bn, "bigneg": bn}
+    if fn == "atan":
+        big = int((~(ax < 1)).sum())
+        return {"small": ax.size - big, "big": big}
+    if fn in ("fmod", "remainder"):
+        import oracle
+        yy = np.abs(np.asarray(y, dtype=np.float64))
+        if fn == "remainder":
+            yy = np.where(yy <= 0x1.fffffffffffffp1022, 2 * yy, yy)
+        f = oracle.lib().oracle_fmod_iters
+        m = min(ax.size, 1 << 16)          # step count from a prefix sample, scaled
+        steps = sum(f(float(a), float(b)) for a, b in zip(ax[:m], yy[:m])) * (ax.size / max(m, 1))
+        return {"setup": ax.size, "step": int(steps)}
+    if fn == "atan2":
+        ay = np.abs(np.asarray(y, dtype=np.float64))
+        return {"base": ax.size, "swap": int((ax > ay).sum()), "yneg": int((np.asarray(y) < 0).sum())}
     return {"all": int(ax.size)}
 
 
-def ops_per_launch(name, x):
+def ops_per_launch(name, x, y=None):
     tbl = OPS[name]
-    return float(sum(tbl[k] * v for k, v in path_mix(name, x).items()))
+    return float(sum(tbl[k] * v for k, v in path_mix(name, x, y).items()))

@@ -1,0 +1,154 @@
+"""Pins of the FP64 exp/log/pow/asin/acos/atan/atan2 oracle: ULP bounds
+against __float128, C99 Annex F special values against the host C library
+(glibc, called through ctypes), and identities."""
+import ctypes
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import quadref
+from paper_2001_09258_gb300 import inputs as I
+
+needs_quad = pytest.mark.skipif(not quadref.available(), reason="__float128 needs x86-64")
+BOUND = {"u10": 1.0, "u35": 3.5}
+N = 60000
+
+UNARY_SETS = {
+    "exp": lambda: np.concatenate([I.uniform("e1", N, -745.2, 709.79), I.uniform("e2", N, -1, 1),
+                                   I.loguniform("e3", N // 4, 1e-300, 1e-3), I.uniform("e4", N // 4, 700, 709.8),
+                                   I.uniform("e5", N // 4, -745.2, -700)]),
+    "log": lambda: np.concatenate([I.loguniform("l1", N, 5e-324, 1.7e308, signed=False),
+                                   I.uniform("l2", N, 0.5, 2), I.uniform("l3", N, 0.999, 1.001),
+                                   I.uniform("l4", N // 4, 0.74, 0.76), I.uniform("l5", N // 4, 1.49, 1.51)]),
+    "asin": lambda: np.concatenate([I.uniform("a1", N, -1, 1), I.uniform("a2", N // 2, 0.49, 0.51),
+                                    I.uniform("a3", N // 2, 0.999, 1), I.loguniform("a4", N // 4, 1e-300, 1e-3)]),
+    "acos": lambda: np.concatenate([I.uniform("a1", N, -1, 1), I.uniform("a2", N // 2, -0.51, -0.49),
+                                    I.uniform("a3", N // 2, 0.999, 1), I.uniform("a5", N // 2, -1, -0.999)]),
+    "atan": lambda: np.concatenate([I.uniform("t1", N, -700, 700), I.uniform("t2", N, -2, 2),
+                                    I.uniform("t4", N, 0.95, 1.05), I.loguniform("t3", N, 1e-300, 1e300)]),
+}
+
+
+@needs_quad
+@pytest.mark.parametrize("fn", list(UNARY_SETS))
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_unary_ulp_bound(fn, acc):
+    x = np.concatenate([UNARY_SETS[fn](), I.SPECIALS_F64])
+    y = oracle.apply(f"{fn}_{acc}_f64", x)
+    err = quadref.ulp_err(fn, x, y)
+    i = int(np.argmax(err))
+    assert err.max() <= BOUND[acc], (fn, acc, x[i], y[i], err.max())
+
+
+def _pow_pairs():
+    return [
+        (I.uniform("p1", N, -30, 30), I.uniform("p2", N, -30, 30)),
+        (I.uniform("p3", N, 0, 2), I.uniform("p4", N, -700, 700)),
+        (I.loguniform("p5", N, 1e-300, 1e300, signed=False), I.uniform("p6", N, -2, 2)),
+        (-I.uniform("p7", N, 0.5, 3), np.round(I.uniform("p8", N, -60, 60))),
+        (I.uniform("p9", N, 0.99, 1.01), I.loguniform("p10", N, 1e3, 1e5)),
+    ]
+
+
+@needs_quad
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_pow_ulp_bound(acc):
+    for k, (x, y) in enumerate(_pow_pairs()):
+        r = oracle.apply(f"pow_{acc}_f64", x, y)
+        err = quadref.ulp_err("pow", x, r, y)
+        i = int(np.argmax(err))
+        assert err.max() <= BOUND[acc], (k, x[i], y[i], r[i], err.max())
+
+
+@needs_quad
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_atan2_ulp_bound(acc):
+    for k, (a, b) in enumerate([(I.uniform("q1", N, -100, 100), I.uniform("q2", N, -100, 100)),
+                                (I.loguniform("q3", N, 1e-300, 1e300), I.loguniform("q4", N, 1e-300, 1e300)),
+                                (I.uniform("q5", N, -1, 1), I.uniform("q6", N, 0.99, 1.01))]):
+        r = oracle.apply(f"atan2_{acc}_f64", a, b)
+        err = quadref.ulp_err("atan2", a, r, b)
+        i = int(np.argmax(err))
+        assert err.max() <= BOUND[acc], (k, a[i], b[i], err.max())
+
+
+# ---------------- special values (C99 Annex F, Section 5.10) ----------------
+_libm = ctypes.CDLL("libm.so.6")
+for _f in ("exp", "log", "asin", "acos", "atan"):
+    getattr(_libm, _f).restype = ctypes.c_double
+    getattr(_libm, _f).argtypes = [ctypes.c_double]
+for _f in ("pow", "atan2"):
+    getattr(_libm, _f).restype = ctypes.c_double
+    getattr(_libm, _f).argtypes = [ctypes.c_double, ctypes.c_double]
+
+SPEC = [0.0, -0.0, 1.0, -1.0, 0.5, -0.5, 2.0, -2.0, 3.0, -3.0, 0.25, math.inf, -math.inf, math.nan,
+        1e-310, -1e-310, 1e300, -1e300, 7.5, -7.5, 2.0 ** 53, -(2.0 ** 53), 2.0 ** 53 + 2]
+
+
+def _same(a, b):
+    if math.isnan(b):
+        return math.isnan(a) and np.array([a]).view(np.uint64)[0] == 0x7FF8000000000000
+    if b == 0 or math.isinf(b):
+        return a == b and math.copysign(1, a) == math.copysign(1, b)
+    return True   # finite non-zero values are covered by the ULP tests
+
+
+@pytest.mark.parametrize("fn", ["exp", "log", "asin", "acos", "atan"])
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_unary_special_values(fn, acc):
+    x = np.array(SPEC)
+    y = oracle.apply(f"{fn}_{acc}_f64", x)
+    for xi, yi in zip(x, y):
+        ref = getattr(_libm, fn)(float(xi))
+        assert _same(float(yi), ref), (fn, xi, yi, ref)
+        if ref in (1.0, -1.0) or (abs(ref) == math.pi / 2 and abs(xi) in (1.0, math.inf)):
+            assert yi == ref, (fn, xi, yi, ref)
+
+
+@pytest.mark.parametrize("fn", ["pow", "atan2"])
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_binary_special_pairs(fn, acc):
+    """Section 6.1: all combinations of the special arguments of the binary
+    functions."""
+    pairs = list(itertools.product(SPEC, SPEC))
+    a = np.array([p[0] for p in pairs])
+    b = np.array([p[1] for p in pairs])
+    y = oracle.apply(f"{fn}_{acc}_f64", a, b)
+    for ai, bi, yi in zip(a, b, y):
+        ref = getattr(_libm, fn)(float(ai), float(bi))
+        assert _same(float(yi), ref), (fn, ai, bi, yi, ref)
+        if ref in (1.0, -1.0, math.pi, -math.pi) or abs(ref) in (math.pi / 2, math.pi / 4, 3 * math.pi / 4):
+            if not (fn == "pow" and ref in (1.0, -1.0) and abs(ai) not in (1.0, 0.0, math.inf)
+                    and bi != 0):
+                assert yi == ref, (fn, ai, bi, yi, ref)
+
+
+def test_closed_forms_and_identities():
+    assert oracle.apply("exp_u10_f64", np.array([0.0]))[0] == 1.0
+    assert oracle.apply("log_u10_f64", np.array([1.0])).view(np.uint64)[0] == 0
+    x = I.uniform("id1", 20000, -700, 700)
+    back = oracle.apply("log_u10_f64", oracle.apply("exp_u10_f64", x))
+    assert np.max(np.abs(back - x) / np.maximum(np.abs(x), 1)) < 2 ** -50
+    u = I.uniform("id2", 20000, -1, 1)
+    s = oracle.apply("asin_u10_f64", u) + oracle.apply("acos_u10_f64", u)
+    assert np.max(np.abs(s - math.pi / 2)) < 4 * 2 ** -52
+    t = I.loguniform("id3", 20000, 1e-3, 1e3, signed=False)
+    s = oracle.apply("atan_u10_f64", t) + oracle.apply("atan_u10_f64", 1 / t)
+    assert np.max(np.abs(s - math.pi / 2)) < 4 * 2 ** -52
+    a = I.uniform("id4", 20000, -100, 100)
+    b = I.uniform("id5", 20000, 1e-3, 100)
+    assert np.max(np.abs(oracle.apply("atan2_u10_f64", a, b) - oracle.apply("atan_u10_f64", a / b))) < 1e-15
+    sq = oracle.apply("pow_u10_f64", t, np.full(t.size, 2.0))
+    assert np.max(np.abs(sq - t * t) / (t * t)) <= 2 ** -52
+
+
+def test_exp_subnormal_and_overflow_edges():
+    x = np.array([709.782712893384, 709.7827128933841, -745.1332191019411, -745.1332191019412,
+                  -744.44007192138122, -708.39641853226408])
+    y = oracle.apply("exp_u10_f64", x)
+    ref = np.array([_libm.exp(float(v)) for v in x])
+    assert np.isinf(y[1]) and np.isfinite(y[0])
+    assert y[2] == ref[2] and y[3] == ref[3]
