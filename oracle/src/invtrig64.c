@@ -25,7 +25,7 @@
 
 static const double ASIN_U10[13] = { ASIN_U10_COEFFS };
 static const double AT_C1H = ATAN_U10_C1H, AT_C1L = ATAN_U10_C1L;
-static const double ATAN_U10[18] = { ATAN_U10_COEFFS };
+static const double ATAN_U10[20] = { ATAN_U10_COEFFS };
 static const double ATAN_U35[19] = { ATAN_U35_COEFFS };
 
 /* sqrt of a non-negative double as DD; the tail is 0 for a zero argument */
@@ -95,7 +95,7 @@ double oracle_acos_u35_f64(double x) {
 /* atan(s) as DD for s in [0, 1] given as DD: s + s t (c1 + t P(t)) */
 static dd_t atan_core_u10(dd_t s) {
   dd_t t = ddsqu_d2_d2(s);
-  double p = poly_d(t.x, ATAN_U10, 18);
+  double p = poly_d(t.x, ATAN_U10, 20);
   dd_t w = ddadd_d2_d2_d(dd(AT_C1H, AT_C1L), t.x * p);
   w = ddmul_d2_d2_d2(t, w);
   w = ddmul_d2_d2_d2(s, w);
@@ -142,6 +142,8 @@ double oracle_atan2_u10_f64(double a, double b) {
   int swap = aa > ab;
   double num = swap ? ab : aa, den = swap ? aa : ab;
   if (!(den > 0 && den <= 0x1.fffffffffffffp1023) || !(num <= den)) { num = 0.0; den = 1.0; }
+  if (den < 0x1p-1000) { num *= 0x1p600; den *= 0x1p600; }      /* keep 1/den finite */
+  if (den > 0x1p1000) { num *= 0x1p-600; den *= 0x1p-600; }     /* keep 1/den normal */
   dd_t s = dddiv_d2_d2_d2(dd(num, 0), dd(den, 0));
   dd_t r = atan_core_u10(s);
   if (swap) r = ddadd_d2_d2_d2(dd(PIO2H, PIO2L), dd(-r.x, -r.y));
@@ -156,6 +158,8 @@ double oracle_atan2_u35_f64(double a, double b) {
   int swap = aa > ab;
   double num = swap ? ab : aa, den = swap ? aa : ab;
   if (!(den > 0 && den <= 0x1.fffffffffffffp1023) || !(num <= den)) { num = 0.0; den = 1.0; }
+  if (den < 0x1p-1000) { num *= 0x1p600; den *= 0x1p600; }      /* keep 1/den finite */
+  if (den > 0x1p1000) { num *= 0x1p-600; den *= 0x1p-600; }     /* keep 1/den normal */
   double r = atan_core_u35(num / den);
   if (swap) r = PIO2H - r;
   if (b < 0) r = PIH - r;

@@ -25,13 +25,13 @@ __constant__ double kAsinU10[13] = {
   0x1.6e8bdee04467bp-6, 0x1.1c49f05c614d5p-6, 0x1.ca1f8d8013edbp-7, 0x1.75858907d1626p-7,
   0x1.613c905725fb1p-7, 0x1.e5f54ce7fcfd8p-9, 0x1.639c82c0224b6p-6, -0x1.57fd8f93ea512p-6,
   0x1.0b46c1e48a247p-5};
-constexpr double AT_C1H = -0x1.555555555544cp-2, AT_C1L = 0x1.2adf401684e89p-56;
-__constant__ double kAtanU10[18] = {
-  0x1.99999999840d2p-3, -0x1.2492491fa1746p-3, 0x1.c71c709dfe90dp-4, -0x1.745d022f8d4dfp-4,
-  0x1.3b12b2db49ea7p-4, -0x1.11089ca960b50p-4, 0x1.e17813d31d297p-5, -0x1.ad32adf6464acp-5,
-  0x1.7ee3d3c4fd336p-5, -0x1.4f44d7d0468bap-5, 0x1.17155ffcf37d4p-5, -0x1.a7256d9c48f4ep-6,
-  0x1.162b08b2a723dp-6, -0x1.2cf5a6d0a88e4p-7, 0x1.f96903869082dp-9, -0x1.312781dbf63a5p-10,
-  0x1.d3b6306811c8ap-13, -0x1.53e1c6fbab687p-16};
+constexpr double AT_C1H = -0x1.555555555554dp-2, AT_C1L = 0x1.f6f1c78b4061fp-57;
+__constant__ double kAtanU10[20] = {
+  0x1.9999999998c27p-3, -0x1.2492492456a9cp-3, 0x1.c71c71b628925p-4, -0x1.745d15d02799cp-4,
+  0x1.3b139bce356edp-4, -0x1.1110326711fe3p-4, 0x1.e1d487be7157ap-5, -0x1.aeda6036339c0p-5,
+  0x1.84b4dcab75621p-5, -0x1.5f276ea2a952dp-5, 0x1.3911a513777bbp-5, -0x1.0cba41b2fdaedp-5,
+  0x1.ad1808a727ccep-6, -0x1.31f10ec96d5a7p-6, 0x1.75115934da341p-7, -0x1.73826f657b4aap-8,
+  0x1.1e67b2bdce61dp-9, -0x1.3de0d575d18fdp-11, 0x1.c1459ac17e788p-14, -0x1.2e664c7ca4205p-17};
 __constant__ double kAtanU35[19] = {
   -0x1.555555555544cp-2, 0x1.999999998410ep-3, -0x1.2492491fa20b6p-3, 0x1.c71c709e18536p-4,
   -0x1.745d0230ed218p-4, 0x1.3b12b2e80c939p-4, -0x1.11089cfe49ae0p-4, 0x1.e1781718de794p-5,
@@ -204,7 +204,10 @@ struct Atan2U10 {
     bool swap = aa > ab;
     uint64_t num = swap ? ab : aa, den = swap ? aa : ab;
     if (!((den - 1) < DMAX) || !(num <= den)) { num = 0; den = ONE; }
-    d2 s = div_d2d2(D2(from_bits(num), 0.0), D2(from_bits(den), 0.0));
+    double fn = from_bits(num), fd = from_bits(den);
+    if (den < 0x0170000000000000ull) { fn = __dmul_rn(fn, 0x1p600); fd = __dmul_rn(fd, 0x1p600); }
+    if (den > 0x7E70000000000000ull) { fn = __dmul_rn(fn, 0x1p-600); fd = __dmul_rn(fd, 0x1p-600); }
+    d2 s = div_d2d2(D2(fn, 0.0), D2(fd, 0.0));
     d2 r = atan_core_u10(s);
     if (swap) r = add_d2d2_fast(D2(PIO2H, PIO2L), D2(-r.x, -r.y));
     bool bneg = (bb >> 63) && ab != 0 && ab <= INF;   // b < 0
@@ -222,7 +225,10 @@ struct Atan2U35 {
     bool swap = aa > ab;
     uint64_t num = swap ? ab : aa, den = swap ? aa : ab;
     if (!((den - 1) < DMAX) || !(num <= den)) { num = 0; den = ONE; }
-    double r = atan_core_u35(__ddiv_rn(from_bits(num), from_bits(den)));
+    double fn = from_bits(num), fd = from_bits(den);
+    if (den < 0x0170000000000000ull) { fn = __dmul_rn(fn, 0x1p600); fd = __dmul_rn(fd, 0x1p600); }
+    if (den > 0x7E70000000000000ull) { fn = __dmul_rn(fn, 0x1p-600); fd = __dmul_rn(fd, 0x1p-600); }
+    double r = atan_core_u35(__ddiv_rn(fn, fd));
     if (swap) r = __dsub_rn(PIO2H, r);
     bool bneg = (bb >> 63) && ab != 0 && ab <= INF;
     if (bneg) r = __dsub_rn(PIH, r);

@@ -35,7 +35,7 @@ OPS = {
     "acos_u10_f64": {"small": 28, "big": 31, "bigneg": 36},
     "acos_u35_f64": {"small": 20, "big": 21, "bigneg": 22},
     # atan: "small" |x| < 1, "big" otherwise
-    "atan_u10_f64": {"small": 46, "big": 54},
+    "atan_u10_f64": {"small": 46, "big": 54},  # 22-term polynomial
     "atan_u35_f64": {"small": 25, "big": 27},
     # atan2: base + 5 (u35: 1) when |x| > |y| and again when y < 0
     "atan2_u10_f64": {"base": 52, "swap": 5, "yneg": 5},
