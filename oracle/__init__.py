@@ -32,6 +32,7 @@ def lib():
         _lib.oracle_ph_reduce.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib.oracle_ph_table_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.oracle_ph_tablef_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib.oracle_fmod_iters.restype = ctypes.c_int
         _lib.oracle_fmod_iters.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib.oracle_fmod_trace.restype = ctypes.c_int
@@ -97,6 +98,13 @@ def ph_reduce(x):
     lo = ctypes.c_double()
     lib().oracle_ph_reduce(float(x), ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo))
     return q.value, hi.value, lo.value
+
+
+def ph_tablef():
+    tab = np.empty(512, dtype=np.float32)
+    ib = np.empty(128, dtype=np.uint8)
+    lib().oracle_ph_tablef_copy(tab.ctypes.data, ib.ctypes.data)
+    return tab, ib
 
 
 def ph_table():

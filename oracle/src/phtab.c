@@ -80,23 +80,28 @@ static void b_atan_inv(big *r, uint32_t k) {
 
 static double tab[4096];
 static uint8_t ibit[1024];
+static float tabf[512];
+static uint8_t ibitf[128];
 static int ready;
 
-/* round the (non-negative) fixed-point value v * 2^scale to a double, RN-even,
- * with subnormal handling; returns 0 for v == 0 */
-static double b_to_double(const big *v, int scale) {
+/* round the (non-negative) fixed-point value v * 2^scale to a binary
+ * floating-point number with p-bit significands and smallest exponent
+ * emin_sub of its subnormals (53/-1074 double, 24/-149 float), RN-even;
+ * returns 0 for v == 0 */
+static double b_round(const big *v, int scale, int p, int emin_sub) {
   int tb = b_topbit(v);
   if (tb < 0) return 0.0;
   int e = tb - FRAC_BITS + scale;                 /* ilogb of the value */
-  int ulpe = e - 52 < -1074 ? -1074 : e - 52;     /* exponent of the last kept bit */
-  int p = ulpe - scale + FRAC_BITS;               /* bit index of the last kept bit */
+  int ulpe = e - (p - 1) < emin_sub ? emin_sub : e - (p - 1);   /* exponent of the last kept bit */
+  int lo = ulpe - scale + FRAC_BITS;              /* bit index of the last kept bit */
   uint64_t m = 0;
-  for (int k = tb; k >= p; k--) m = (m << 1) | (uint64_t)b_bit(v, k);
-  int half = b_bit(v, p - 1), sticky = 0;
-  for (int k = p - 2; k >= 0 && !sticky; k--) sticky = b_bit(v, k);
+  for (int k = tb; k >= lo; k--) m = (m << 1) | (uint64_t)b_bit(v, k);
+  int half = b_bit(v, lo - 1), sticky = 0;
+  for (int k = lo - 2; k >= 0 && !sticky; k--) sticky = b_bit(v, k);
   if (half && (sticky || (m & 1))) m++;
   return ldexp((double)m, ulpe);
 }
+static double b_to_double(const big *v, int scale) { return b_round(v, scale, 53, -1074); }
 
 /* the exact fixed-point value of |t| * 2^-scale (t a double) */
 static void b_from_double(big *r, double t, int scale) {
@@ -136,6 +141,24 @@ static void build(void) {
       else { b_sub(&fr, &tv, &fr); neg = !neg; }
     }
   }
+  /* FP32 table: the same definition with 24-bit words, E = 0..127,
+   * M = (E > 64 ? -64 : 0), m = frac(2/pi 2^(E-24)) 2^-(E-24+M) */
+  for (int E = 0; E < 128; E++) {
+    int sh = E - 24, M = E > 64 ? -64 : 0;
+    big fr; b_zero(&fr);
+    for (int k = 0; k < FRAC_BITS; k++) if (b_bit(&two_over_pi, k - sh)) b_setbit(&fr, k);
+    ibitf[E] = (uint8_t)(sh >= 0 ? b_bit(&two_over_pi, FRAC_BITS - sh) : 0);
+    int scale = -(E - 24 + M);
+    int neg = 0;
+    for (int i = 0; i < 4; i++) {
+      float t = (float)b_round(&fr, scale, 24, -149);     /* exact: already 24 bits */
+      uint32_t bits; memcpy(&bits, &t, 4); bits &= ~(uint32_t)1; memcpy(&t, &bits, 4);
+      tabf[4 * E + i] = neg ? -t : t;
+      big tv; b_from_double(&tv, (double)t, scale);
+      if (b_cmp(&fr, &tv) >= 0) b_sub(&fr, &fr, &tv);
+      else { b_sub(&fr, &tv, &fr); neg = !neg; }
+    }
+  }
   ready = 1;
 }
 
@@ -143,6 +166,15 @@ __attribute__((constructor)) static void init_tables(void) { if (!ready) build()
 
 const double *oracle_ph_tab(void) { if (!ready) build(); return tab; }
 const uint8_t *oracle_ph_ibit(void) { if (!ready) build(); return ibit; }
+
+const float *oracle_ph_tabf(void) { if (!ready) build(); return tabf; }
+const uint8_t *oracle_ph_ibitf(void) { if (!ready) build(); return ibitf; }
+
+void oracle_ph_tablef_copy(float *out512, uint8_t *ibit128) {
+  if (!ready) build();
+  memcpy(out512, tabf, sizeof tabf);
+  memcpy(ibit128, ibitf, sizeof ibitf);
+}
 
 void oracle_ph_table_copy(double *out4096, uint8_t *ibit1024) {
   if (!ready) build();
