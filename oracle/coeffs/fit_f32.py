@@ -10,7 +10,8 @@ float-float (FF) arithmetic with binary32 coefficients:
   logf     log m = z + z^3 P(z^2), z = 2(m-1)/(m+1), |z| <= 0.4
   expm1f   e^r - 1 = r + r^2/2 + r^3 v(r), |r| <= ln2/2 (tanh core)
   erff_a   erf x = x P(x^2) on [0, 1], the constant term as FF
-  erff_b   erfc x = e^(-x^2) R(x) on [1, 3.95], R smooth (relative error)
+  erff_b   erfc x = exp(-x^2 + L(x)) on [1, 3.95], L = log(erfc(x) e^(x^2))
+           smooth and O(1) (absolute error), a polynomial in u = x - 2.475
 """
 import os
 import sys
@@ -50,6 +51,21 @@ def inv(f):
     return lambda x: 1 / f(x)
 
 
+ERF_C = mp.mpf("2.475")
+
+
+def erfc_r_u(u):
+    return erfc_r(u + ERF_C)
+
+
+def log_r_u(u):
+    return mp.log(erfc_r(u + ERF_C))
+
+
+def one(u):
+    return mp.mpf(1)
+
+
 # |s| bound: pi/2 plus the slack of q = rint(x * RN(1/pi)) for |x| < 2^20
 TS = mp.mpf("1.7") ** 2
 JOBS = {
@@ -61,7 +77,8 @@ JOBS = {
     "logf_u35": lambda: fit_rounded(log_g, log_w, range(3), ["f"] * 3, 0, mp.mpf("0.4001") ** 2),
     "expm1f": lambda: fit_rounded(exp_v, exp_wv, range(5), ["f"] * 5, -LN2H, LN2H),
     "erff_a": lambda: fit_rounded(erf_g, erf_w, range(8), ["ff"] + ["f"] * 7, 0, 1),
-    "erff_b": lambda: fit_rounded(erfc_r, inv(erfc_r), range(10), ["f"] * 10, 1, mp.mpf("3.95")),
+    "erff_b": lambda: fit_rounded(log_r_u, one, range(12), ["ff"] + ["f"] * 11, 1 - ERF_C,
+                                  mp.mpf("3.95") - ERF_C),
 }
 
 if __name__ == "__main__":

@@ -196,7 +196,10 @@ def fit_rounded(f, w, exps, formats, a, b, fixed=(), **kw):
     and refit the rest after each rounding; (2) round the free minimax fit
     directly.  Returns the one with the smaller max weighted error as
     (list of (exponent, stored value(s)), max weighted error)."""
-    seq = _fit_sequential(f, w, exps, formats, a, b, fixed, **kw)
+    try:
+        seq = _fit_sequential(f, w, exps, formats, a, b, fixed, **kw)
+    except ZeroDivisionError:          # a degenerate reference late in the refits
+        seq = None
     cs, _ = remez(f, w, list(exps), a, b, fixed=list(fixed), **kw)
     stored, terms = [], list(fixed)
     for e, c, fmt in zip(exps, cs, formats):
@@ -204,7 +207,7 @@ def fit_rounded(f, w, exps, formats, a, b, fixed=(), **kw):
         stored.append((e, v))
         terms.append((e, exact))
     naive = (stored, max_error(f, w, terms, a, b))
-    return seq if seq[1] <= naive[1] else naive
+    return seq if seq is not None and seq[1] <= naive[1] else naive
 
 
 def _fit_sequential(f, w, exps, formats, a, b, fixed=(), **kw):

@@ -42,6 +42,22 @@ double oracle_remainder_u35_f64(double, double);
 int oracle_fmod_iters(double, double);
 int oracle_fmod_trace(double, double, double *, double *, int);
 
+float oracle_sin_u10_f32(float);
+float oracle_sin_u35_f32(float);
+float oracle_cos_u10_f32(float);
+float oracle_cos_u35_f32(float);
+float oracle_exp_u10_f32(float);
+float oracle_exp_u35_f32(float);
+float oracle_log_u10_f32(float);
+float oracle_log_u35_f32(float);
+float oracle_log1p_u10_f32(float);
+float oracle_log1p_u35_f32(float);
+float oracle_tanh_u10_f32(float);
+float oracle_tanh_u35_f32(float);
+float oracle_erf_u10_f32(float);
+float oracle_erf_u35_f32(float);
+void oracle_ph_reduce_f32(float, int *, float *, float *);
+
 int oracle_apply(const char *name, const void *x, const void *y, void *out, void *out2,
                  size_t n, int nthreads);
 #endif

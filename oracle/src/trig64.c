@@ -63,6 +63,13 @@ static dd_t cw1(double x, double qd) {
   double u = fma(qd, -PIO2_A, x);
   return ddadd_d2_d_d(u, qd * -PIO2_B);
 }
+/* level-1 form for cos at |x| < 1 (q = +-1): there x is finer-grained than
+ * x - q A, so the fma head is not exact; q A is taken as an exact DD product
+ * and added with TwoSum instead */
+static dd_t cw1_exact(double x, double qd) {
+  dd_t s = ddadd2_d2_d_d2(x, ddmul_d2_d_d(qd, -PIO2_A));
+  return ddadd_d2_d2_d(s, qd * -PIO2_B);
+}
 /* level-2 Cody-Waite for |x| < 1e14: x - qd*A is exact, qd*B is an exact
  * DD product, qd*C goes into the tail */
 static dd_t cw2(double x, double qd) {
@@ -114,6 +121,7 @@ static dd_t reduce_half(double x, int parity, int *q) {
   if (ax < 1e14) {
     double qd = parity ? 2.0 * rint(fma(x, R_1_PI, -0.5)) + 1.0 : 2.0 * rint(x * R_1_PI);
     *q = q_of(qd);
+    if (parity && ax < 1) return cw1_exact(x, qd);
     return ax < 15 ? cw1(x, qd) : cw2(x, qd);
   }
   dd_t r = oracle_ph_reduce_dd(x, q);

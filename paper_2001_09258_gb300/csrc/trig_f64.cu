@@ -28,6 +28,7 @@ constexpr double TWOPI_L = 0x1.1a62633145c07p-52;
 constexpr double R_1_PI = 0x1.45f306dc9c883p-2;
 constexpr double R_2_PI = 0x1.45f306dc9c883p-1;
 constexpr uint64_t B15 = 0x402e000000000000ull;   // bits of 15.0
+constexpr uint64_t B1 = 0x3ff0000000000000ull;    // bits of 1.0
 constexpr uint64_t B1E14 = 0x42d6bcc41e900000ull; // bits of 1e14
 
 __constant__ double kSinU10[7] = {
@@ -60,6 +61,12 @@ __constant__ double kScSU35[6] = {
 __device__ __forceinline__ d2 cw1(double x, double qd) {
   double u = __fma_rn(qd, -PIO2_A, x);
   return add_dd_fast(u, __dmul_rn(qd, -PIO2_B));
+}
+// cos at |x| < 1 (q = +-1): the fma head is not exact there, so q A is an
+// exact DD product added with TwoSum
+__device__ __forceinline__ d2 cw1_exact(double x, double qd) {
+  d2 s = add_d_d2(x, mul_dd(qd, -PIO2_A));
+  return add_d2_d_fast(s, __dmul_rn(qd, -PIO2_B));
 }
 __device__ __forceinline__ d2 cw2(double x, double qd) {
   double u = __fma_rn(qd, -PIO2_A, x);
@@ -138,6 +145,7 @@ __device__ __forceinline__ d2 reduce_half(double x, uint64_t ab, int &q) {
       k = rint(__fma_rn(x, R_1_PI, -0.5));
       qd = __fma_rn(2.0, k, 1.0);
       q = ((low2_of_int(k) << 1) + 1) & 3;
+      if (ab < B1) return cw1_exact(x, qd);
     }
     if (ab < B15) return cw1(x, qd);
     return cw2(x, qd);
@@ -194,6 +202,11 @@ __device__ __forceinline__ int path_of(double x) {
 #define TRIG_PATHS                       \
   static constexpr int NCLS = 3;         \
   __device__ static int cls(double x) { return path_of(x); }
+// cos u10 has a fourth path: the exact head for |x| < 1
+#define COS_PATHS                        \
+  static constexpr int NCLS = 4;         \
+  __device__ static int cls(double x) {  \
+    return (bits(x) & ABS64) < B1 ? 3 : path_of(x); }
 
 // ---------------- polynomials ----------------
 // sin s = s + s t (c1 + t P(t)), t = s^2, the leading products in DD
@@ -223,7 +236,7 @@ struct SinU10 {
   }
 };
 struct CosU10 {
-  TRIG_PATHS
+  COS_PATHS
   __device__ double operator()(double x) const {
     uint64_t ab = bits(x) & ABS64;
     int q;

@@ -115,8 +115,10 @@ SPECIALS_F64 = _specials()
 
 
 def specials_f32():
-    v = SPECIALS_F64.astype(np.float32)
-    return v
+    """The FP64 specials rounded to binary32 (out-of-range values become
+    infinities, tiny ones zeros or subnormals)."""
+    with np.errstate(over="ignore", under="ignore"):
+        return SPECIALS_F64.astype(np.float32)
 
 
 # argument domains (main part) per function; trig tail = log-uniform huge
