@@ -136,6 +136,29 @@ sleefcu_status sleefcu_remainder_u10_f64(const double *x, const double *y, doubl
 sleefcu_status sleefcu_remainder_u35_f64(const double *x, const double *y, double *out, size_t n,
                                          sleefcu_stream stream);
 
+/* ---------------- FP32 family (float-float forms) ----------------
+ * The same methods in binary32 arithmetic only, with float-float pairs where
+ * the 1-ULP bound needs them (the paper describes the FP64 functions; "all
+ * C99 real floating-point math functions" in both precisions, Section 1):
+ * sin/cos (Cody-Waite for |x| < 2^20, the FF Payne-Hanek reduction with the
+ * FP32 table above), exp, log, log1p (1 + x as an FF pair), tanh (via an FF
+ * expm1) and erf (x P(x^2) below 1, 1 - exp(-x^2 + L(x)) above, +-1 from
+ * 3.95).  Special values as for FP64; NaN results are 0x7FC00000. */
+sleefcu_status sleefcu_sin_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sin_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cos_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cos_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

@@ -27,8 +27,13 @@ FUNCS = {
     "asin": "u", "acos": "u", "atan": "u", "atan2": "b",
     "exp": "u", "log": "u", "pow": "b",
     "fmod": "b", "remainder": "b",
+    "log1p": "u", "tanh": "u", "erf": "u",
 }
 PRECS = {fn: ("f64",) for fn in FUNCS}
+for _fn in ("sin", "cos", "exp", "log"):
+    PRECS[_fn] = ("f64", "f32")
+for _fn in ("log1p", "tanh", "erf"):
+    PRECS[_fn] = ("f32",)
 ACCS = ("u10", "u35")
 
 _lib = None

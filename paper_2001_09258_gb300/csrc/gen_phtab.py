@@ -128,15 +128,15 @@ def main(out):
     tab64, ib64, tab32, ib32 = tables()
     with open(out, "w") as f:
         f.write("// generated by gen_phtab.py: Payne-Hanek tables (Section 5.8)\n")
-        f.write("__device__ __align__(32) const double k_phtab64[4096] = {\n")
+        f.write("static __device__ __align__(32) const double k_phtab64[4096] = {\n")
         for i in range(0, 4096, 4):
             f.write("  " + ", ".join(float(t).hex() for t in tab64[i:i + 4]) + ",\n")
-        f.write("};\n__device__ const unsigned k_phbit64[32] = {\n")
+        f.write("};\nstatic __device__ const unsigned k_phbit64[32] = {\n")
         f.write("  " + ", ".join(f"0x{w:08x}u" for w in words(ib64)) + "};\n")
-        f.write("__device__ __align__(16) const float k_phtab32[512] = {\n")
+        f.write("static __device__ __align__(16) const float k_phtab32[512] = {\n")
         for i in range(0, 512, 4):
             f.write("  " + ", ".join(float(t).hex() + "f" for t in tab32[i:i + 4]) + ",\n")
-        f.write("};\n__device__ const unsigned k_phbit32[4] = {\n")
+        f.write("};\nstatic __device__ const unsigned k_phbit32[4] = {\n")
         f.write("  " + ", ".join(f"0x{w:08x}u" for w in words(ib32)) + "};\n")
 
 

@@ -405,3 +405,109 @@ sleefcu_status launch_sorted64b(const char *name, const double *x, const double 
 }
 
 }  // namespace sleefcu
+
+// ---------------- FP32 kernels ----------------
+namespace sleefcu {
+
+// unary FP32: out[i] = F(x[i]); VEC processes 4 elements per 16-byte access
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_unary32(const float *x, float *out, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t nq = n >> 2;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float4 *o4 = reinterpret_cast<float4 *>(out);
+    for (size_t i = tid; i < nq; i += stride) {
+      float4 v = __ldcs(x4 + i);
+      float4 r;
+      r.x = f(v.x);
+      r.y = f(v.y);
+      r.z = f(v.z);
+      r.w = f(v.w);
+      __stcs(o4 + i, r);
+    }
+    size_t rem = n & 3;
+    if (tid < rem) out[n - rem + tid] = f(x[n - rem + tid]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) out[i] = f(x[i]);
+  }
+}
+
+// FP32 divergence-sorted tiles (see k_sorted64)
+template <class F>
+__global__ void __launch_bounds__(kBlock) k_sorted32(const float *x, float *out, size_t n) {
+  constexpr int NC = F::NCLS;
+  __shared__ float sx[kSortTile];
+  __shared__ float so[kSortTile];
+  __shared__ unsigned short sidx[kSortTile];
+  __shared__ int cnt[NC], cur[NC];
+  F f;
+  const int tid = threadIdx.x;
+  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kSortTile;
+    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    if (tid < NC) cnt[tid] = 0;
+    __syncthreads();
+    int cl[kSortEPT];
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      float v = 0.0f;
+      if (e < valid) {
+        v = __ldcs(x + base + e);
+        cl[j] = F::cls(v);
+      } else {
+        cl[j] = -1;
+      }
+      sx[e] = v;
+    }
+    sort_count<NC>(cl, cnt, tid);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
+    }
+    __syncthreads();
+    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    __syncthreads();
+    for (int k = tid; k < valid; k += kBlock) {
+      int e = sidx[k];
+      so[e] = f(sx[e]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortEPT; j++) {
+      int e = j * kBlock + tid;
+      if (e < valid) __stcs(out + base + e, so[e]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class F>
+sleefcu_status launch_unary32(const char *name, const float *x, float *out, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(out)) {
+    auto k = k_unary32<F, true>;
+    k<<<grid_for((const void *)k, (n + 3) / 4), kBlock, 0, st>>>(x, out, n);
+  } else {
+    auto k = k_unary32<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, out, n);
+  }
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_sorted32(const char *name, const float *x, float *out, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  auto k = k_sorted32<F>;
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, out, n);
+  return check_launch(name);
+}
+
+}  // namespace sleefcu

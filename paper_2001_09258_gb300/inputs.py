@@ -139,23 +139,33 @@ DOMAINS_F64 = {
     "lgamma": (-1e3, 2.5e305), "fmod": (-1e25, 1e25), "remainder": (-1e25, 1e25),
 }
 TRIG = ("sin", "cos", "tan", "sincos")
+# FP32: the same mixes scaled to the binary32 range
+DOMAINS_F32 = {
+    "sin": (-100.0, 100.0), "cos": (-100.0, 100.0), "exp": (-87.0, 88.0),
+    "log": (0.0, 3.4e38), "log1p": (-1.0, 3.4e38), "tanh": (-9.0, 9.0), "erf": (-4.0, 4.0),
+}
+SPECIALS_F32_TAIL = (1e5, 3.4e38)
 
 
 def workload(fn, n, key="c2", dtype=np.float64, operand=0):
     """The mixed workload of one function: 89% uniform over the main domain,
-    10% log-uniform tail, 1% specials, interleaved by a seeded choice."""
-    a, b = DOMAINS_F64[fn]
-    k = f"{key}/{fn}/{operand}"
+    10% log-uniform tail, 1% specials, interleaved by a seeded choice.
+    dtype float32 uses the binary32 domains (trig tail up to 3.4e38)."""
+    f32 = dtype == np.float32
+    a, b = (DOMAINS_F32 if f32 else DOMAINS_F64)[fn]
+    k = f"{key}/{fn}/{operand}" + ("/f32" if f32 else "")
     main = uniform(k + "/main", n, a, b)
     if fn in TRIG:
-        tail = loguniform(k + "/tail", n, 1e5, 1e300)
+        tail = loguniform(k + "/tail", n, 1e5, 3.4e38 if f32 else 1e300)
     else:
         lo = max(1e-300, 0.0 if a <= 0 <= b else min(abs(a), abs(b)))
         hi = max(abs(a), abs(b))
         tail = loguniform(k + "/tail", n, max(lo, 1e-300), hi, signed=a < 0)
-    spec = SPECIALS_F64[(raw(k + "/spec", n) % np.uint64(64)).astype(np.int64)]
+    specials = specials_f32().astype(np.float64) if f32 else SPECIALS_F64
+    spec = specials[(raw(k + "/spec", n) % np.uint64(64)).astype(np.int64)]
     c = raw(k + "/cat", n) % np.uint64(100)
     x = np.where(c < 89, main, np.where(c < 99, tail, spec))
-    if dtype == np.float32:
-        x = x.astype(np.float32)
+    if f32:
+        with np.errstate(over="ignore", under="ignore"):
+            x = x.astype(np.float32)
     return x
