@@ -40,6 +40,9 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=1 << 18, help="oracle sample per function")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the FP32 / bf16 / f16 family measurements")
+    p.add_argument("--n32", type=int, default=1 << 28, help="elements per FP32 entry point")
     return p.parse_args()
 
 
@@ -174,6 +177,115 @@ def fp64_pipe_peak(sleefcu, torch, device):
         ms = a.elapsed_time(b)
         best = ms if best is None else min(best, ms)
     return blocks * 256.0 * iters * 8 / (best * 1e-3)
+
+
+def time_calls(torch, st, fn, reps=5):
+    """average ms of fn() over reps launches, CUDA events on stream st"""
+    fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
+    """FP32 family (2^28 floats) and bf16/f16 activation forms ([8192, 28672]),
+    each with its speedup over the plain FP64 / FP32 form of the function."""
+    from paper_2001_09258_gb300 import inputs as I
+    import numpy as np
+    hbm = peaks.get("hbm_gbs")
+    f32 = {}
+    for name in [e for e in sleefcu.entry_points() if e.endswith("_f32")]:
+        fn = name.split("_")[0]
+        x = torch.from_numpy(I.workload(fn, n32, key="c3", dtype=np.float32)).to(device)
+        o = torch.empty_like(x)
+        f = sleefcu.raw(name)
+        ms = time_calls(torch, st, lambda: f(x.data_ptr(), o.data_ptr(), n32, sp))
+        g = n32 / (ms * 1e-3) / 1e9
+        acc = name.split("_")[1]
+        base = per_fn_f64.get(f"{fn}_{acc}_f64")
+        f32[name] = {"gelem_s": round(g, 2), "hbm_gbs": round(8 * n32 / (ms * 1e-3) / 1e9, 1),
+                     "hbm_frac": round(8 * n32 / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                     "speedup_vs_f64": round(g / base, 2) if base else None}
+        del x, o
+    low = {}
+    shape = (8192, 28672)
+    n16 = shape[0] * shape[1]
+    for name in [e for e in sleefcu.entry_points() if e.endswith(("_bf16", "_f16"))]:
+        fn, acc, fmt = name.split("_")
+        h = I.activations("c3/act", shape, fmt).reshape(-1)
+        x = torch.from_numpy(h.view(np.int16)).to(device)
+        o = torch.empty_like(x)
+        f = sleefcu.raw(name)
+        ms = time_calls(torch, st, lambda: f(x.data_ptr(), o.data_ptr(), n16, sp))
+        g = n16 / (ms * 1e-3) / 1e9
+        base = f32.get(f"{fn}_{acc}_f32", {}).get("gelem_s")
+        low[name] = {"gelem_s": round(g, 2), "hbm_gbs": round(4 * n16 / (ms * 1e-3) / 1e9, 1),
+                     "hbm_frac": round(4 * n16 / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                     "speedup_vs_f32": round(g / base, 2) if base else None}
+        del x, o
+    return {"fp32_family": {"n": n32, "workload": "same mixes scaled to binary32 (trig tail to 3.4e38)",
+                            "entry_points": f32},
+            "bf16_f16_forms": {"shape": list(shape), "inputs": "N(0,3) rounded to the 16-bit format",
+                               "entry_points": low}}
+
+
+def batched(sleefcu, torch, device, st, sp, narrays=4096):
+    """4096 arrays, lengths log-uniform in [1, 2^20], each assigned an FP64 or
+    FP32 entry point uniformly at random: one autotuned persistent launch (plain
+    and graph replay) against one launch per array (plain and captured in a
+    CUDA graph)."""
+    import math
+    import numpy as np
+    from paper_2001_09258_gb300 import inputs as I
+    names_all = [e for e in sleefcu.entry_points() if e.endswith(("_f64", "_f32"))]
+    u = (I.raw("c4/len", narrays) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    lens = np.clip(np.floor(np.exp(u * math.log(2 ** 20))), 1, 2 ** 20).astype(np.int64)
+    pick = (I.raw("c4/fn", narrays) % np.uint64(len(names_all))).astype(np.int64)
+    items = []
+    for k in range(narrays):
+        name = names_all[pick[k]]
+        fn, acc, prec = name.split("_")
+        dt = np.float64 if prec == "f64" else np.float32
+        n = int(lens[k])
+        x = torch.from_numpy(I.workload(fn, n, key=f"c4/{k}", dtype=dt)).to(device)
+        y = torch.from_numpy(I.workload(fn, n, key=f"c4/{k}", operand=1, dtype=dt)).to(device) \
+            if sleefcu.FUNCS[fn] == "b" else None
+        out = torch.empty_like(x)
+        out2 = torch.empty_like(x) if sleefcu.FUNCS[fn] == "sc" else None
+        items.append((name, x, y, out, out2))
+    total = int(lens.sum())
+    b = sleefcu.Batch(items)
+    b.autotune(os.path.join(ROOT, "paper_2001_09258_gb300", "_build", "batch_tune.jsonl"))
+    cfg = b.config()
+    ms_plain = time_calls(torch, st, lambda: b.launch(st), reps=5)
+    ms_graph = time_calls(torch, st, lambda: b.launch(st, graph=True), reps=5)
+
+    def singles():
+        for name, x, y, out, out2 in items:
+            launch(sleefcu, name, [x] + ([y] if y is not None else []), [out] + ([out2] if out2 is not None else []), sp)
+    ms_single = time_calls(torch, st, singles, reps=2)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream(device)
+    with torch.cuda.stream(cs):
+        csp = ctypes.c_void_p(cs.cuda_stream)
+        with torch.cuda.graph(g, stream=cs):
+            for name, x, y, out, out2 in items:
+                launch(sleefcu, name, [x] + ([y] if y is not None else []),
+                       [out] + ([out2] if out2 is not None else []), csp)
+    ms_single_graph = time_calls(torch, st, lambda: g.replay(), reps=3)
+    b.close()
+    gel = lambda ms: round(total / (ms * 1e-3) / 1e9, 3)
+    return {"arrays": narrays, "elements": total, "entry_points": len(names_all), "config": cfg,
+            "batched_ms": round(ms_plain, 3), "batched_graph_ms": round(ms_graph, 3),
+            "single_launches_ms": round(ms_single, 3), "single_launches_graph_ms": round(ms_single_graph, 3),
+            "batched_gelem_s": gel(ms_plain), "batched_graph_gelem_s": gel(ms_graph),
+            "single_launches_gelem_s": gel(ms_single), "single_launches_graph_gelem_s": gel(ms_single_graph),
+            "speedup_vs_single_launches": round(ms_single / ms_graph, 2),
+            "speedup_vs_single_launch_graph": round(ms_single_graph / ms_graph, 2)}
 
 
 def cpu_baseline(names, n_sample, rank):
@@ -317,6 +429,13 @@ def main():
         return
     avg = {name: statistics.mean(v) for name, v in per_fn_ms.items()}
     per_fn = {name: round(n / (avg[name] * 1e-3) / 1e9, 3) for name in names}
+    ext = None
+    if not args.no_extras:
+        del dev, outs
+        torch.cuda.empty_cache()
+        ext = extras(sleefcu, torch, device, st, sp, per_fn, measured_peaks(), args.n32)
+        torch.cuda.empty_cache()
+        ext["batched"] = batched(sleefcu, torch, device, st, sp)
     dom = max(names, key=lambda nm: avg[nm])
     hx = host[dom.split("_")[0]]
     ops = opcounts.ops_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None)
@@ -359,6 +478,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": len(names) * args.steps,
+        "forms": ext,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

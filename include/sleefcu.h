@@ -159,6 +159,79 @@ sleefcu_status sleefcu_tanh_u35_f32(const float *x, float *out, size_t n, sleefc
 sleefcu_status sleefcu_erf_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
 sleefcu_status sleefcu_erf_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
 
+/* ---------------- bf16 / f16 activation forms ----------------
+ * x and out hold n 16-bit values (bf16 or IEEE binary16, as the suffix says).
+ * Each element is converted exactly to binary32, evaluated with the FP32
+ * u10 / u35 entry point of the same name, and rounded to the 16-bit format
+ * with round-to-nearest-even; NaN results are 0x7FC0 (bf16) / 0x7E00 (f16).
+ * 16-byte-aligned arrays take the 8-elements-per-access path. */
+sleefcu_status sleefcu_erf_u10_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u35_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u10_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u35_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u10_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u35_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u10_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u35_bf16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u10_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u35_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u10_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u35_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u10_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u35_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u10_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u35_f16(const void *x, void *out, size_t n, sleefcu_stream stream);
+
+/* ---------------- batched mixed launch ----------------
+ * Many arrays of uneven length, each with its own function, precision and
+ * accuracy, evaluated by one persistent kernel (the batched form of the hot
+ * path; every output equals the single-array entry point's, bit for bit).
+ * fn: a sleefcu_fn; dtype: a sleefcu_dtype; ulp: 10 or 35.  x, y (binary
+ * functions), out, out2 (sincos) are device pointers owned by the caller.
+ * sleefcu_batch_create copies the descriptors to the device (it allocates
+ * device memory and synchronizes; not capturable) and returns EUNSUPPORTED
+ * for a combination the library does not have, EINVAL for a null pointer
+ * with n > 0, ENOMEM when the descriptors do not fit.  Items with n == 0 are
+ * ignored.  The caller keeps the arrays alive while the plan is launched.
+ * sleefcu_batch_launch enqueues one memset and one kernel on the stream, no
+ * allocation and no synchronization: it may be captured in a CUDA graph.
+ * sleefcu_batch_launch_graph captures that pair once into a graph owned by
+ * the plan and replays it on each call.  sleefcu_batch_autotune times the
+ * candidate configurations (block size 128/256/512, 4/16/64 elements per
+ * thread per tile, grid multiplier 1/2/4, vector width 1/2) on the plan's own
+ * arrays (it overwrites the outputs) and keeps the fastest; with a cache file
+ * (JSON lines keyed by device name and batch shape) a stored choice is reused
+ * without timing.  Launches on one plan must not overlap (they share the
+ * plan's tile counter). */
+typedef enum {
+  SLEEFCU_FN_SIN = 0, SLEEFCU_FN_COS, SLEEFCU_FN_TAN, SLEEFCU_FN_SINCOS, SLEEFCU_FN_ASIN,
+  SLEEFCU_FN_ACOS, SLEEFCU_FN_ATAN, SLEEFCU_FN_ATAN2, SLEEFCU_FN_EXP, SLEEFCU_FN_LOG, SLEEFCU_FN_POW,
+  SLEEFCU_FN_FMOD, SLEEFCU_FN_REMAINDER, SLEEFCU_FN_LOG1P, SLEEFCU_FN_TANH, SLEEFCU_FN_ERF,
+  SLEEFCU_FN_COUNT
+} sleefcu_fn;
+typedef enum { SLEEFCU_F64 = 0, SLEEFCU_F32 = 1, SLEEFCU_BF16 = 2, SLEEFCU_F16 = 3 } sleefcu_dtype;
+typedef struct {
+  uint16_t fn;
+  uint8_t dtype;
+  uint8_t ulp;
+  uint32_t reserved;
+  const void *x;
+  const void *y;
+  void *out;
+  void *out2;
+  size_t n;
+} sleefcu_batch_item;
+typedef struct sleefcu_batch sleefcu_batch;
+
+sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count, sleefcu_batch **plan);
+sleefcu_status sleefcu_batch_launch(sleefcu_batch *plan, sleefcu_stream stream);
+sleefcu_status sleefcu_batch_launch_graph(sleefcu_batch *plan, sleefcu_stream stream);
+sleefcu_status sleefcu_batch_autotune(sleefcu_batch *plan, const char *cache_file_or_null, sleefcu_stream stream);
+sleefcu_status sleefcu_batch_set_config(sleefcu_batch *plan, int block, int tile, int grid_mult, int vec);
+sleefcu_status sleefcu_batch_get_config(const sleefcu_batch *plan, int *block, int *tile, int *grid_mult,
+                                        int *vec);
+void sleefcu_batch_destroy(sleefcu_batch *plan);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

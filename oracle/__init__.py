@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 _lib = None
-K_U64, K_B64, K_SC64, K_U32, K_B32, K_SC32 = 1, 2, 3, 11, 12, 13
+K_U64, K_B64, K_SC64, K_U32, K_B32, K_SC32, K_U16 = 1, 2, 3, 11, 12, 13, 21
 
 
 def lib():
@@ -63,7 +63,7 @@ def apply(name, x, y=None, nthreads=None):
     k = kind(name)
     if k == 0:
         raise KeyError(f"oracle has no function {name!r}")
-    dt = np.float64 if k < 10 else np.float32
+    dt = np.float64 if k < 10 else (np.float32 if k < 20 else np.uint16)
     x = np.ascontiguousarray(x, dtype=dt)
     n = x.size
     out = np.empty_like(x)

@@ -14,7 +14,7 @@
 #include <stddef.h>
 #include "oracle.h"
 
-enum { K_U64 = 1, K_B64 = 2, K_SC64 = 3, K_U32 = 11, K_B32 = 12, K_SC32 = 13 };
+enum { K_U64 = 1, K_B64 = 2, K_SC64 = 3, K_U32 = 11, K_B32 = 12, K_SC32 = 13, K_U16 = 21 };
 
 typedef struct {
   const char *name;
@@ -26,6 +26,7 @@ typedef struct {
     float (*u32)(float);
     float (*b32)(float, float);
     void (*sc32)(float, float *, float *);
+    uint16_t (*u16)(uint16_t);
     void *any;
   } f;
 } entry;
@@ -36,6 +37,7 @@ typedef struct {
 #define U32(n) { #n, K_U32, { .u32 = oracle_##n } }
 #define B32(n) { #n, K_B32, { .b32 = oracle_##n } }
 #define SC32(n) { #n, K_SC32, { .sc32 = oracle_##n } }
+#define U16(n) { #n, K_U16, { .u16 = oracle_##n } }
 
 static const entry REG[] = {
 #include "registry.inc"
@@ -70,6 +72,7 @@ static void run(const job *j) {
       case K_U32: ((float *)j->o)[i] = e->f.u32(((const float *)j->x)[i]); break;
       case K_B32: ((float *)j->o)[i] = e->f.b32(((const float *)j->x)[i], ((const float *)j->y)[i]); break;
       case K_SC32: e->f.sc32(((const float *)j->x)[i], (float *)j->o + i, (float *)j->o2 + i); break;
+      case K_U16: ((uint16_t *)j->o)[i] = e->f.u16(((const uint16_t *)j->x)[i]); break;
     }
   }
 }

@@ -58,6 +58,27 @@ float oracle_erf_u10_f32(float);
 float oracle_erf_u35_f32(float);
 void oracle_ph_reduce_f32(float, int *, float *, float *);
 
+uint16_t oracle_erf_u10_bf16(uint16_t);
+uint16_t oracle_erf_u10_f16(uint16_t);
+uint16_t oracle_erf_u35_bf16(uint16_t);
+uint16_t oracle_erf_u35_f16(uint16_t);
+uint16_t oracle_tanh_u10_bf16(uint16_t);
+uint16_t oracle_tanh_u10_f16(uint16_t);
+uint16_t oracle_tanh_u35_bf16(uint16_t);
+uint16_t oracle_tanh_u35_f16(uint16_t);
+uint16_t oracle_exp_u10_bf16(uint16_t);
+uint16_t oracle_exp_u10_f16(uint16_t);
+uint16_t oracle_exp_u35_bf16(uint16_t);
+uint16_t oracle_exp_u35_f16(uint16_t);
+uint16_t oracle_log1p_u10_bf16(uint16_t);
+uint16_t oracle_log1p_u10_f16(uint16_t);
+uint16_t oracle_log1p_u35_bf16(uint16_t);
+uint16_t oracle_log1p_u35_f16(uint16_t);
+float oracle_bf16_to_f32(uint16_t);
+uint16_t oracle_f32_to_bf16(float);
+float oracle_f16_to_f32(uint16_t);
+uint16_t oracle_f32_to_f16(float);
+
 int oracle_apply(const char *name, const void *x, const void *y, void *out, void *out2,
                  size_t n, int nthreads);
 #endif

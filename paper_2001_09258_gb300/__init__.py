@@ -34,6 +34,8 @@ for _fn in ("sin", "cos", "exp", "log"):
     PRECS[_fn] = ("f64", "f32")
 for _fn in ("log1p", "tanh", "erf"):
     PRECS[_fn] = ("f32",)
+for _fn in ("erf", "tanh", "exp", "log1p"):
+    PRECS[_fn] = PRECS[_fn] + ("bf16", "f16")
 ACCS = ("u10", "u35")
 
 _lib = None
@@ -122,7 +124,8 @@ def call(name, x, y=None, out=None, out2=None, stream=None):
 
 def _prec_of(x):
     import torch
-    return {torch.float64: "f64", torch.float32: "f32"}[x.dtype]
+    return {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16",
+            torch.float16: "f16"}[x.dtype]
 
 
 def _mk(fn):
@@ -140,3 +143,82 @@ def _mk(fn):
 
 for _fn in FUNCS:
     globals()[_fn] = _mk(_fn)
+
+
+# ---------------- batched mixed launch ----------------
+FN_IDS = {name: i for i, name in enumerate(
+    ["sin", "cos", "tan", "sincos", "asin", "acos", "atan", "atan2", "exp", "log", "pow", "fmod",
+     "remainder", "log1p", "tanh", "erf"])}
+DTYPE_IDS = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_uint16), ("dtype", ctypes.c_uint8), ("ulp", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint32), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("out2", ctypes.c_void_p), ("n", ctypes.c_size_t)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.sleefcu_batch_create.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_void_p)]
+        for f in ("sleefcu_batch_launch", "sleefcu_batch_launch_graph"):
+            getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.sleefcu_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
+        L.sleefcu_batch_set_config.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+        L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
+        L.sleefcu_batch_destroy.restype = None
+        L._batch_ready = True
+    return L
+
+
+class Batch:
+    """A plan for sleefcu_batch_*: items are (entry point name, x, y, out, out2)
+    with CUDA tensors (y / out2 None where unused)."""
+
+    def __init__(self, items):
+        L = _batch_lib()
+        arr = (BatchItem * len(items))()
+        self._keep = items
+        for i, (name, x, y, out, out2) in enumerate(items):
+            fn, acc, prec = name.split("_")
+            arr[i] = BatchItem(FN_IDS[fn], DTYPE_IDS[prec], int(acc[1:]), 0,
+                               x.data_ptr(), y.data_ptr() if y is not None else None,
+                               out.data_ptr(), out2.data_ptr() if out2 is not None else None, x.numel())
+        h = ctypes.c_void_p()
+        _check(L.sleefcu_batch_create(arr, len(items), ctypes.byref(h)), "batch_create")
+        self.handle = h
+
+    def _stream(self, stream):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(st.cuda_stream)
+
+    def launch(self, stream=None, graph=False):
+        f = _batch_lib().sleefcu_batch_launch_graph if graph else _batch_lib().sleefcu_batch_launch
+        _check(f(self.handle, self._stream(stream)), "batch_launch")
+
+    def autotune(self, cache_file=None, stream=None):
+        c = cache_file.encode() if cache_file else None
+        _check(_batch_lib().sleefcu_batch_autotune(self.handle, c, self._stream(stream)), "batch_autotune")
+
+    def config(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(_batch_lib().sleefcu_batch_get_config(self.handle, *[ctypes.byref(a) for a in v]), "batch_get_config")
+        return dict(zip(("block", "tile", "grid_mult", "vec"), (a.value for a in v)))
+
+    def set_config(self, block, tile, grid_mult, vec):
+        _check(_batch_lib().sleefcu_batch_set_config(self.handle, block, tile, grid_mult, vec), "batch_set_config")
+
+    def close(self):
+        if self.handle:
+            _batch_lib().sleefcu_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

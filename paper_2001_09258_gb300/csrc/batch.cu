@@ -1,0 +1,448 @@
+// Batched mixed launch: many arrays of uneven length and mixed functions in
+// one persistent kernel.
+//
+// A plan holds one descriptor per array (entry point code, pointers, n) and
+// the prefix sums of each array's tile count.  The kernel runs one CTA per
+// resident slot; CTAs claim tiles from a device counter, find the array of a
+// tile by binary search over the prefix sums, and evaluate its elements with
+// the same device functors as the individual entry points (so every output is
+// bit-identical to the single-array call).  The switch over entry points is
+// uniform within a CTA.  Block size, tile size (elements per thread x block
+// size), vector width and grid multiplier are runtime parameters chosen by
+// sleefcu_batch_autotune, which times candidate configurations on the plan
+// itself and can cache the choice in a JSON file keyed by device name.
+#define SLEEFCU_FUNCTORS_ONLY
+#include "trig_f64.cu"
+#include "explog_f64.cu"
+#include "invtrig_f64.cu"
+#include "fmod_f64.cu"
+#include "trig_f32.cu"
+#include "explog_f32.cu"
+#undef SLEEFCU_FUNCTORS_ONLY
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace sleefcu {
+namespace batch {
+
+enum Kind { U64, B64, SC64, U32, BF, HF };
+
+// entry point table: (code order) name, kind, functor
+// entry point codes: the index in this list
+static const char *kNames[] = {
+    "sin_u10_f64", "sin_u35_f64", "cos_u10_f64", "cos_u35_f64",
+    "tan_u10_f64", "tan_u35_f64", "sincos_u10_f64", "sincos_u35_f64",
+    "asin_u10_f64", "asin_u35_f64", "acos_u10_f64", "acos_u35_f64",
+    "atan_u10_f64", "atan_u35_f64", "atan2_u10_f64", "atan2_u35_f64",
+    "exp_u10_f64", "exp_u35_f64", "log_u10_f64", "log_u35_f64",
+    "pow_u10_f64", "pow_u35_f64", "fmod_u10_f64", "fmod_u35_f64",
+    "remainder_u10_f64", "remainder_u35_f64", "sin_u10_f32", "sin_u35_f32",
+    "cos_u10_f32", "cos_u35_f32", "exp_u10_f32", "exp_u35_f32",
+    "log_u10_f32", "log_u35_f32", "log1p_u10_f32", "log1p_u35_f32",
+    "tanh_u10_f32", "tanh_u35_f32", "erf_u10_f32", "erf_u35_f32",
+    "erf_u10_bf16", "erf_u35_bf16", "tanh_u10_bf16", "tanh_u35_bf16",
+    "exp_u10_bf16", "exp_u35_bf16", "log1p_u10_bf16", "log1p_u35_bf16",
+    "erf_u10_f16", "erf_u35_f16", "tanh_u10_f16", "tanh_u35_f16",
+    "exp_u10_f16", "exp_u35_f16", "log1p_u10_f16", "log1p_u35_f16"};
+constexpr int kCodes = sizeof(kNames) / sizeof(kNames[0]);
+
+struct Desc {
+  const void *x, *y;
+  void *out, *out2;
+  long long n;
+  int code, pad;
+};
+
+// evaluate elements [b, e) of one array; threads of the CTA stride over them,
+// vec > 1 uses 16-byte accesses when the tile start is aligned
+template <Kind K, class F>
+__device__ __forceinline__ void run(const Desc &D, long long b, long long e, int vec) {
+  F f;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if constexpr (K == U64) {
+    const double *x = (const double *)D.x;
+    double *o = (double *)D.out;
+    if (vec > 1 && ((((uintptr_t)(x + b)) | ((uintptr_t)(o + b))) & 15) == 0) {
+      long long np = (e - b) >> 1;
+      for (long long i = tid; i < np; i += nt) {
+        double2 v = __ldcs(reinterpret_cast<const double2 *>(x + b) + i), r;
+        r.x = f(v.x);
+        r.y = f(v.y);
+        __stcs(reinterpret_cast<double2 *>(o + b) + i, r);
+      }
+      if (((e - b) & 1) && tid == 0) o[e - 1] = f(x[e - 1]);
+    } else {
+      for (long long i = b + tid; i < e; i += nt) o[i] = f(x[i]);
+    }
+  } else if constexpr (K == B64) {
+    const double *x = (const double *)D.x, *y = (const double *)D.y;
+    double *o = (double *)D.out;
+    for (long long i = b + tid; i < e; i += nt) o[i] = f(x[i], y[i]);
+  } else if constexpr (K == SC64) {
+    const double *x = (const double *)D.x;
+    double *o = (double *)D.out, *o2 = (double *)D.out2;
+    for (long long i = b + tid; i < e; i += nt) f.dual(x[i], o[i], o2[i]);
+  } else if constexpr (K == U32) {
+    const float *x = (const float *)D.x;
+    float *o = (float *)D.out;
+    if (vec > 1 && ((((uintptr_t)(x + b)) | ((uintptr_t)(o + b))) & 15) == 0) {
+      long long nq = (e - b) >> 2;
+      for (long long i = tid; i < nq; i += nt) {
+        float4 v = __ldcs(reinterpret_cast<const float4 *>(x + b) + i), r;
+        r.x = f(v.x);
+        r.y = f(v.y);
+        r.z = f(v.z);
+        r.w = f(v.w);
+        __stcs(reinterpret_cast<float4 *>(o + b) + i, r);
+      }
+      for (long long i = b + 4 * nq + tid; i < e; i += nt) o[i] = f(x[i]);
+    } else {
+      for (long long i = b + tid; i < e; i += nt) o[i] = f(x[i]);
+    }
+  } else {
+    const uint16_t *x = (const uint16_t *)D.x;
+    uint16_t *o = (uint16_t *)D.out;
+    for (long long i = b + tid; i < e; i += nt) o[i] = lowp::ev<F, K == BF>(f, x[i]);
+  }
+}
+
+__global__ void __launch_bounds__(512) k_batch(const Desc *__restrict__ d, const long long *__restrict__ pre,
+                                               int nitems, long long ntiles, int tile, int vec,
+                                               unsigned long long *ctr) {
+  __shared__ long long s_t;
+  __shared__ int s_i;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long t = (long long)atomicAdd(ctr, 1ull);
+      int lo = 0, hi = nitems - 1;          // last item with pre[item] <= t
+      if (t < ntiles) {
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+      }
+      s_t = t;
+      s_i = lo;
+    }
+    __syncthreads();
+    long long t = s_t;
+    int item = s_i;
+    __syncthreads();
+    if (t >= ntiles) break;
+    Desc D = d[item];
+    long long b = (t - pre[item]) * (long long)tile;
+    long long e = b + tile < D.n ? b + tile : D.n;
+    switch (D.code) {
+      case 0: run<U64, trig64::SinU10>(D, b, e, vec); break;
+      case 1: run<U64, trig64::SinU35>(D, b, e, vec); break;
+      case 2: run<U64, trig64::CosU10>(D, b, e, vec); break;
+      case 3: run<U64, trig64::CosU35>(D, b, e, vec); break;
+      case 4: run<U64, trig64::TanU10>(D, b, e, vec); break;
+      case 5: run<U64, trig64::TanU35>(D, b, e, vec); break;
+      case 6: run<SC64, trig64::SinCosU10>(D, b, e, vec); break;
+      case 7: run<SC64, trig64::SinCosU35>(D, b, e, vec); break;
+      case 8: run<U64, invtrig64::AsinU10>(D, b, e, vec); break;
+      case 9: run<U64, invtrig64::AsinU35>(D, b, e, vec); break;
+      case 10: run<U64, invtrig64::AcosU10>(D, b, e, vec); break;
+      case 11: run<U64, invtrig64::AcosU35>(D, b, e, vec); break;
+      case 12: run<U64, invtrig64::AtanU10>(D, b, e, vec); break;
+      case 13: run<U64, invtrig64::AtanU35>(D, b, e, vec); break;
+      case 14: run<B64, invtrig64::Atan2U10>(D, b, e, vec); break;
+      case 15: run<B64, invtrig64::Atan2U35>(D, b, e, vec); break;
+      case 16: run<U64, explog64::ExpU10>(D, b, e, vec); break;
+      case 17: run<U64, explog64::ExpU35>(D, b, e, vec); break;
+      case 18: run<U64, explog64::LogU10>(D, b, e, vec); break;
+      case 19: run<U64, explog64::LogU35>(D, b, e, vec); break;
+      case 20: run<B64, explog64::PowU10>(D, b, e, vec); break;
+      case 21: run<B64, explog64::PowU10>(D, b, e, vec); break;
+      case 22: run<B64, fmod64::FmodF>(D, b, e, vec); break;
+      case 23: run<B64, fmod64::FmodF>(D, b, e, vec); break;
+      case 24: run<B64, fmod64::RemainderF>(D, b, e, vec); break;
+      case 25: run<B64, fmod64::RemainderF>(D, b, e, vec); break;
+      case 26: run<U32, trig32::SinU10>(D, b, e, vec); break;
+      case 27: run<U32, trig32::SinU35>(D, b, e, vec); break;
+      case 28: run<U32, trig32::CosU10>(D, b, e, vec); break;
+      case 29: run<U32, trig32::CosU35>(D, b, e, vec); break;
+      case 30: run<U32, explog32::ExpU10>(D, b, e, vec); break;
+      case 31: run<U32, explog32::ExpU35>(D, b, e, vec); break;
+      case 32: run<U32, explog32::LogU10>(D, b, e, vec); break;
+      case 33: run<U32, explog32::LogU35>(D, b, e, vec); break;
+      case 34: run<U32, explog32::Log1pU10>(D, b, e, vec); break;
+      case 35: run<U32, explog32::Log1pU35>(D, b, e, vec); break;
+      case 36: run<U32, explog32::TanhU10>(D, b, e, vec); break;
+      case 37: run<U32, explog32::TanhU35>(D, b, e, vec); break;
+      case 38: run<U32, explog32::ErfU10>(D, b, e, vec); break;
+      case 39: run<U32, explog32::ErfU35>(D, b, e, vec); break;
+      case 40: run<BF, explog32::ErfU10>(D, b, e, vec); break;
+      case 41: run<BF, explog32::ErfU35>(D, b, e, vec); break;
+      case 42: run<BF, explog32::TanhU10>(D, b, e, vec); break;
+      case 43: run<BF, explog32::TanhU35>(D, b, e, vec); break;
+      case 44: run<BF, explog32::ExpU10>(D, b, e, vec); break;
+      case 45: run<BF, explog32::ExpU35>(D, b, e, vec); break;
+      case 46: run<BF, explog32::Log1pU10>(D, b, e, vec); break;
+      case 47: run<BF, explog32::Log1pU35>(D, b, e, vec); break;
+      case 48: run<HF, explog32::ErfU10>(D, b, e, vec); break;
+      case 49: run<HF, explog32::ErfU35>(D, b, e, vec); break;
+      case 50: run<HF, explog32::TanhU10>(D, b, e, vec); break;
+      case 51: run<HF, explog32::TanhU35>(D, b, e, vec); break;
+      case 52: run<HF, explog32::ExpU10>(D, b, e, vec); break;
+      case 53: run<HF, explog32::ExpU35>(D, b, e, vec); break;
+      case 54: run<HF, explog32::Log1pU10>(D, b, e, vec); break;
+      case 55: run<HF, explog32::Log1pU35>(D, b, e, vec); break;
+      default: break;
+    }
+  }
+}
+
+}  // namespace batch
+}  // namespace sleefcu
+
+// ---------------- host side ----------------
+namespace {
+using namespace sleefcu;
+using namespace sleefcu::batch;
+
+const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin", "cos", "tan", "sincos", "asin", "acos", "atan", "atan2",
+                                          "exp", "log", "pow", "fmod", "remainder", "log1p", "tanh", "erf"};
+const char *kTypeNames[4] = {"f64", "f32", "bf16", "f16"};
+
+int code_of(const sleefcu_batch_item &it) {
+  if (it.fn >= SLEEFCU_FN_COUNT || it.dtype > 3 || (it.ulp != 10 && it.ulp != 35)) return -1;
+  char name[64];
+  snprintf(name, sizeof name, "%s_u%d_%s", kFnNames[it.fn], it.ulp, kTypeNames[it.dtype]);
+  for (int c = 0; c < kCodes; c++)
+    if (!strcmp(kNames[c], name)) return c;
+  return -1;
+}
+bool needs_y(int code) { return strstr(kNames[code], "atan2_") || strstr(kNames[code], "pow_") ||
+                                strstr(kNames[code], "fmod_") || strstr(kNames[code], "remainder_"); }
+bool needs_out2(int code) { return strstr(kNames[code], "sincos_") != nullptr; }
+}  // namespace
+
+struct sleefcu_batch {
+  int dev = 0, sms = 0;
+  std::vector<Desc> desc;              // non-empty items only
+  Desc *d_desc = nullptr;
+  long long *d_pre = nullptr;
+  unsigned long long *d_ctr = nullptr;
+  long long ntiles = 0;
+  int block = 256, tile = 4096, grid_mult = 2, vec = 2;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static void drop_graph(sleefcu_batch *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+}
+
+// tile prefix sums for the current tile size (synchronous upload)
+static sleefcu_status upload_prefix(sleefcu_batch *p) {
+  std::vector<long long> pre(p->desc.size() + 1, 0);
+  for (size_t i = 0; i < p->desc.size(); i++) pre[i + 1] = pre[i] + (p->desc[i].n + p->tile - 1) / p->tile;
+  p->ntiles = pre.back();
+  if (p->desc.empty()) return SLEEFCU_OK;
+  cudaError_t e = cudaMemcpy(p->d_pre, pre.data(), pre.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { set_error("sleefcu_batch: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  return SLEEFCU_OK;
+}
+
+extern "C" sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count, sleefcu_batch **plan) {
+  if (!plan || (count && !items)) { set_error("sleefcu_batch_create: null argument"); return SLEEFCU_EINVAL; }
+  *plan = nullptr;
+  sleefcu_batch *p = new sleefcu_batch();
+  for (size_t i = 0; i < count; i++) {
+    const sleefcu_batch_item &it = items[i];
+    int c = code_of(it);
+    if (c < 0) {
+      set_error("sleefcu_batch_create: item %zu: unsupported (fn %u, dtype %u, ulp %u)", i, it.fn, it.dtype, it.ulp);
+      delete p;
+      return SLEEFCU_EUNSUPPORTED;
+    }
+    if (it.n == 0) continue;
+    if (!it.x || !it.out || (needs_y(c) && !it.y) || (needs_out2(c) && !it.out2)) {
+      set_error("sleefcu_batch_create: item %zu: null pointer with n = %zu", i, it.n);
+      delete p;
+      return SLEEFCU_EINVAL;
+    }
+    p->desc.push_back(Desc{it.x, it.y, it.out, it.out2, (long long)it.n, c, 0});
+  }
+  cudaGetDevice(&p->dev);
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->dev);
+  if (!p->desc.empty()) {
+    size_t nd = p->desc.size();
+    if (cudaMalloc(&p->d_desc, nd * sizeof(Desc)) != cudaSuccess ||
+        cudaMalloc(&p->d_pre, (nd + 1) * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_ctr, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("sleefcu_batch_create: out of device memory");
+      sleefcu_batch_destroy(p);
+      return SLEEFCU_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(p->d_desc, p->desc.data(), nd * sizeof(Desc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_error("sleefcu_batch_create: %s", cudaGetErrorString(e));
+      sleefcu_batch_destroy(p);
+      return SLEEFCU_ECUDA;
+    }
+  }
+  sleefcu_status st = upload_prefix(p);
+  if (st != SLEEFCU_OK) { sleefcu_batch_destroy(p); return st; }
+  *plan = p;
+  return SLEEFCU_OK;
+}
+
+extern "C" void sleefcu_batch_destroy(sleefcu_batch *p) {
+  if (!p) return;
+  drop_graph(p);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  cudaFree(p->d_desc);
+  cudaFree(p->d_pre);
+  cudaFree(p->d_ctr);
+  delete p;
+}
+
+static int batch_grid(sleefcu_batch *p) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_batch, p->block, 0);
+  if (per < 1) per = 1;
+  long long g = (long long)p->sms * per * p->grid_mult;
+  if (g > p->ntiles) g = p->ntiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+static sleefcu_status enqueue(sleefcu_batch *p, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) { set_error("sleefcu_batch_launch: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  k_batch<<<batch_grid(p), p->block, 0, st>>>(p->d_desc, p->d_pre, (int)p->desc.size(), p->ntiles, p->tile,
+                                               p->vec, p->d_ctr);
+  return check_launch("sleefcu_batch_launch");
+}
+
+extern "C" sleefcu_status sleefcu_batch_launch(sleefcu_batch *p, sleefcu_stream s) {
+  if (!p) { set_error("sleefcu_batch_launch: null plan"); return SLEEFCU_EINVAL; }
+  if (p->ntiles == 0) return SLEEFCU_OK;
+  return enqueue(p, (cudaStream_t)s);
+}
+
+extern "C" sleefcu_status sleefcu_batch_launch_graph(sleefcu_batch *p, sleefcu_stream s) {
+  if (!p) { set_error("sleefcu_batch_launch_graph: null plan"); return SLEEFCU_EINVAL; }
+  if (p->ntiles == 0) return SLEEFCU_OK;
+  if (!p->exec) {
+    if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("sleefcu_batch_launch_graph: cannot create the capture stream");
+      return SLEEFCU_ECUDA;
+    }
+    cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { set_error("sleefcu_batch_launch_graph: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+    sleefcu_status st = enqueue(p, p->cap);
+    e = cudaStreamEndCapture(p->cap, &p->graph);
+    if (st != SLEEFCU_OK) { drop_graph(p); return st; }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) {
+      drop_graph(p);
+      set_error("sleefcu_batch_launch_graph: %s", cudaGetErrorString(e));
+      return SLEEFCU_ECUDA;
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)s);
+  if (e != cudaSuccess) { set_error("sleefcu_batch_launch_graph: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  return SLEEFCU_OK;
+}
+
+extern "C" sleefcu_status sleefcu_batch_set_config(sleefcu_batch *p, int block, int tile, int grid_mult, int vec) {
+  if (!p || block < 32 || block > 512 || (block & 31) || tile < block || grid_mult < 1 || grid_mult > 16 ||
+      (vec != 1 && vec != 2)) {
+    set_error("sleefcu_batch_set_config: bad argument");
+    return SLEEFCU_EINVAL;
+  }
+  p->block = block;
+  p->tile = tile;
+  p->grid_mult = grid_mult;
+  p->vec = vec;
+  drop_graph(p);
+  return upload_prefix(p);
+}
+
+extern "C" sleefcu_status sleefcu_batch_get_config(const sleefcu_batch *p, int *block, int *tile, int *grid_mult,
+                                                   int *vec) {
+  if (!p) { set_error("sleefcu_batch_get_config: null plan"); return SLEEFCU_EINVAL; }
+  if (block) *block = p->block;
+  if (tile) *tile = p->tile;
+  if (grid_mult) *grid_mult = p->grid_mult;
+  if (vec) *vec = p->vec;
+  return SLEEFCU_OK;
+}
+
+// the plan's signature for the tuning cache: device name, array count, elements
+static std::string signature(const sleefcu_batch *p) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, p->dev);
+  long long el = 0;
+  for (const Desc &d : p->desc) el += d.n;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|items=%zu|elems=%lld", prop.name, p->desc.size(), el);
+  return buf;
+}
+
+extern "C" sleefcu_status sleefcu_batch_autotune(sleefcu_batch *p, const char *cache_file, sleefcu_stream s) {
+  if (!p) { set_error("sleefcu_batch_autotune: null plan"); return SLEEFCU_EINVAL; }
+  if (p->ntiles == 0) return SLEEFCU_OK;
+  std::string sig = signature(p);
+  if (cache_file) {                    // JSON lines: {"signature": "...", "block": b, "tile": t, ...}
+    if (FILE *f = fopen(cache_file, "r")) {
+      char line[1024];
+      int b = 0, t = 0, g = 0, v = 0, found = 0;
+      while (fgets(line, sizeof line, f)) {
+        const char *k = strstr(line, "\"signature\": \"");
+        if (!k || strncmp(k + 14, sig.c_str(), sig.size()) || k[14 + sig.size()] != '"') continue;
+        const char *c = strstr(line, "\"block\":");
+        if (c && sscanf(c, "\"block\": %d, \"tile\": %d, \"grid_mult\": %d, \"vec\": %d", &b, &t, &g, &v) == 4)
+          found = 1;
+      }
+      fclose(f);
+      if (found) return sleefcu_batch_set_config(p, b, t, g, v);
+    }
+  }
+  cudaStream_t st = (cudaStream_t)s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks[] = {128, 256, 512};
+  const int ept[] = {4, 16, 64};            // elements per thread: tile = ept x block
+  const int mults[] = {1, 2, 4};
+  const int vecs[] = {1, 2};
+  float best = 1e30f;
+  int bb = p->block, bt = p->tile, bg = p->grid_mult, bv = p->vec;
+  for (int b : blocks)
+    for (int e : ept)
+      for (int g : mults)
+        for (int v : vecs) {
+          if (sleefcu_batch_set_config(p, b, e * b, g, v) != SLEEFCU_OK) continue;
+          enqueue(p, st);                    // warm-up
+          cudaEventRecord(e0, st);
+          for (int r = 0; r < 3; r++) enqueue(p, st);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) { best = ms; bb = b; bt = e * b; bg = g; bv = v; }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  sleefcu_status rc = sleefcu_batch_set_config(p, bb, bt, bg, bv);
+  if (rc == SLEEFCU_OK && cache_file) {
+    if (FILE *f = fopen(cache_file, "a")) {
+      fprintf(f, "{\"signature\": \"%s\", \"block\": %d, \"tile\": %d, \"grid_mult\": %d, \"vec\": %d, \"ms\": %.4f}\n",
+              sig.c_str(), bb, bt, bg, bv, best / 3);
+      fclose(f);
+    }
+  }
+  return rc;
+}

@@ -24,26 +24,26 @@ constexpr uint64_t B746 = 0x4087500000000000ull;  // bits of 746.0
 constexpr uint64_t DMAX = 0x7FEFFFFFFFFFFFFFull;
 constexpr uint64_t INF = 0x7FF0000000000000ull;
 
-__constant__ double kExpU10[11] = {
+static __constant__ double kExpU10[11] = {
   0x1.0000000000000p-1, 0x1.555555555555bp-3, 0x1.5555555555503p-5, 0x1.111111110ec3fp-7,
   0x1.6c16c16c305dap-10, 0x1.a01a01b38a1ccp-13, 0x1.a01a01364ed77p-16, 0x1.71ddf0027528ep-19,
   0x1.27e5b4917ffe5p-22, 0x1.af6c1dcd03fd7p-26, 0x1.1e3d09ab8b9a5p-29};
-__constant__ double kExpU35[9] = {
+static __constant__ double kExpU35[9] = {
   0x1.ffffffffffed1p-2, 0x1.5555555550776p-3, 0x1.5555555589411p-5, 0x1.11111125c3b1dp-7,
   0x1.6c16c0c7b3762p-10, 0x1.a0198d1cfb5cfp-13, 0x1.a01b7d10e56f2p-16, 0x1.72e95f1b1c6d2p-19,
   0x1.27076dd8a5103p-22};
-__constant__ double kLogU10[8] = {
+static __constant__ double kLogU10[8] = {
   0x1.555555555554fp-4, 0x1.999999999c179p-7, 0x1.24924921e457cp-9, 0x1.c71c748fb0e5ep-12,
   0x1.745c4adfd4929p-14, 0x1.3b35c02f141cfp-16, 0x1.0dcba14fc06c7p-18, 0x1.1b8139759f314p-20};
-__constant__ double kLogU35[7] = {
+static __constant__ double kLogU35[7] = {
   0x1.5555555555775p-4, 0x1.99999998f0e71p-7, 0x1.249249b213a2dp-9, 0x1.c71c01680d46ap-12,
   0x1.7474e2e4fcac3p-14, 0x1.3852c703d6843p-16, 0x1.3abef8cc48463p-18};
 constexpr double PL_C1H = 0x1.5555555555555p-4, PL_C1L = 0x1.54855a03b34d8p-58;
-__constant__ double kPowLog[9] = {
+static __constant__ double kPowLog[9] = {
   0x1.999999999999cp-7, 0x1.2492492492062p-9, 0x1.c71c71c78a1b0p-12, 0x1.745d171399b86p-14,
   0x1.3b13bf3c5b892p-16, 0x1.110e98ef52765p-18, 0x1.e26f3be0efb86p-21, 0x1.a57c235e7b51bp-23,
   0x1.e37c78d194e20p-25};
-__constant__ double kPowExp[10] = {
+static __constant__ double kPowExp[10] = {
   0x1.555555555555ap-3, 0x1.5555555555498p-5, 0x1.111111110f0acp-7, 0x1.6c16c16c4d9f3p-10,
   0x1.a01a01b2b4f71p-13, 0x1.a01a010b94555p-16, 0x1.71ddf039a6182p-19, 0x1.27e54bd4df84bp-22,
   0x1.af6e560a2694ap-26, 0x1.1fda157dfad50p-29};
@@ -225,6 +225,7 @@ struct PowU10 {
 }  // namespace explog64
 }  // namespace sleefcu
 
+#ifndef SLEEFCU_FUNCTORS_ONLY
 using namespace sleefcu;
 
 #define UNARY64(NAME, F)                                                                    \
@@ -245,3 +246,5 @@ extern "C" sleefcu_status sleefcu_pow_u35_f64(const double *x, const double *y, 
                                               sleefcu_stream s) {
   return launch_binary64<explog64::PowU10>("sleefcu_pow_u35_f64", x, y, out, n, s);
 }
+#undef UNARY64
+#endif  // SLEEFCU_FUNCTORS_ONLY

@@ -119,6 +119,7 @@ struct RemainderF {
 }  // namespace fmod64
 }  // namespace sleefcu
 
+#ifndef SLEEFCU_FUNCTORS_ONLY
 using namespace sleefcu;
 
 #define BIN64(NAME, F)                                                                      \
@@ -130,3 +131,5 @@ BIN64(fmod_u10_f64, FmodF)
 BIN64(fmod_u35_f64, FmodF)
 BIN64(remainder_u10_f64, RemainderF)
 BIN64(remainder_u35_f64, RemainderF)
+#undef BIN64
+#endif  // SLEEFCU_FUNCTORS_ONLY

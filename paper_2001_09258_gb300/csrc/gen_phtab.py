@@ -127,7 +127,7 @@ def words(bits):
 def main(out):
     tab64, ib64, tab32, ib32 = tables()
     with open(out, "w") as f:
-        f.write("// generated by gen_phtab.py: Payne-Hanek tables (Section 5.8)\n")
+        f.write("// generated by gen_phtab.py: Payne-Hanek tables (Section 5.8)\n#pragma once\n")
         f.write("static __device__ __align__(32) const double k_phtab64[4096] = {\n")
         for i in range(0, 4096, 4):
             f.write("  " + ", ".join(float(t).hex() for t in tab64[i:i + 4]) + ",\n")

@@ -20,19 +20,19 @@ constexpr double PI4 = 0x1.921fb54442d18p-1, PI34 = 0x1.2d97c7f3321d2p1;
 constexpr uint64_t ONE = 0x3FF0000000000000ull, HALF = 0x3FE0000000000000ull;
 constexpr uint64_t INF = 0x7FF0000000000000ull, DMAX = 0x7FEFFFFFFFFFFFFFull;
 
-__constant__ double kAsinU10[13] = {
+static __constant__ double kAsinU10[13] = {
   0x1.5555555555577p-3, 0x1.333333332e131p-4, 0x1.6db6db7212680p-5, 0x1.f1c71a94f2d61p-6,
   0x1.6e8bdee04467bp-6, 0x1.1c49f05c614d5p-6, 0x1.ca1f8d8013edbp-7, 0x1.75858907d1626p-7,
   0x1.613c905725fb1p-7, 0x1.e5f54ce7fcfd8p-9, 0x1.639c82c0224b6p-6, -0x1.57fd8f93ea512p-6,
   0x1.0b46c1e48a247p-5};
 constexpr double AT_C1H = -0x1.555555555554dp-2, AT_C1L = 0x1.f6f1c78b4061fp-57;
-__constant__ double kAtanU10[20] = {
+static __constant__ double kAtanU10[20] = {
   0x1.9999999998c27p-3, -0x1.2492492456a9cp-3, 0x1.c71c71b628925p-4, -0x1.745d15d02799cp-4,
   0x1.3b139bce356edp-4, -0x1.1110326711fe3p-4, 0x1.e1d487be7157ap-5, -0x1.aeda6036339c0p-5,
   0x1.84b4dcab75621p-5, -0x1.5f276ea2a952dp-5, 0x1.3911a513777bbp-5, -0x1.0cba41b2fdaedp-5,
   0x1.ad1808a727ccep-6, -0x1.31f10ec96d5a7p-6, 0x1.75115934da341p-7, -0x1.73826f657b4aap-8,
   0x1.1e67b2bdce61dp-9, -0x1.3de0d575d18fdp-11, 0x1.c1459ac17e788p-14, -0x1.2e664c7ca4205p-17};
-__constant__ double kAtanU35[19] = {
+static __constant__ double kAtanU35[19] = {
   -0x1.555555555544cp-2, 0x1.999999998410ep-3, -0x1.2492491fa20b6p-3, 0x1.c71c709e18536p-4,
   -0x1.745d0230ed218p-4, 0x1.3b12b2e80c939p-4, -0x1.11089cfe49ae0p-4, 0x1.e1781718de794p-5,
   -0x1.ad32ba2f14c5ep-5, 0x1.7ee3f6bdf7ae1p-5, -0x1.4f4524eb17978p-5, 0x1.1715e3114eceep-5,
@@ -241,6 +241,7 @@ struct Atan2U35 {
 }  // namespace invtrig64
 }  // namespace sleefcu
 
+#ifndef SLEEFCU_FUNCTORS_ONLY
 using namespace sleefcu;
 
 #define SORTED64(NAME, F)                                                                   \
@@ -263,3 +264,5 @@ extern "C" sleefcu_status sleefcu_atan2_u35_f64(const double *x, const double *y
                                                 sleefcu_stream s) {
   return launch_sorted64b<invtrig64::Atan2U35>("sleefcu_atan2_u35_f64", x, y, out, n, s);
 }
+#undef SORTED64
+#endif  // SLEEFCU_FUNCTORS_ONLY

@@ -20,9 +20,9 @@ constexpr float TWOPIF_H = 0x1.921fb6p2f, TWOPIF_L = -0x1.777a5cp-23f;
 constexpr uint32_t B1 = 0x3f800000u, B125 = 0x42fa0000u, B2P20 = 0x49800000u;
 
 constexpr float SIN_C1H = -0x1.5555560000000p-3f, SIN_C1L = 0x1.940bfe0000000p-28f;
-__constant__ float kSinU10[4] = {
+static __constant__ float kSinU10[4] = {
   0x1.1111080000000p-7f, -0x1.a016880000000p-13f, 0x1.7147b00000000p-19f, -0x1.9704fc0000000p-26f};
-__constant__ float kSinU35[5] = {
+static __constant__ float kSinU35[5] = {
   -0x1.5555560000000p-3f, 0x1.11112e0000000p-7f, -0x1.a01faa0000000p-13f, 0x1.7228ca0000000p-19f,
   -0x1.a61f4c0000000p-26f};
 
@@ -56,7 +56,7 @@ __device__ __forceinline__ void ph_step(f2 &x, int &q) {
   x = norm_f2(x);
 }
 // Payne-Hanek in FF for |d| >= 2^20 or non-finite d
-__device__ __noinline__ f2 ph(float d, int &q) {
+static __device__ __noinline__ f2 ph(float d, int &q) {
   uint32_t b = fbits(d);
   bool fin = (b & EXP32) != EXP32;
   uint32_t bf = fin ? b : 0u;
@@ -175,6 +175,7 @@ struct CosU35 : Paths<true> {
 }  // namespace trig32
 }  // namespace sleefcu
 
+#ifndef SLEEFCU_FUNCTORS_ONLY
 using namespace sleefcu;
 
 #define SORTED32(NAME, F)                                                                   \
@@ -186,3 +187,5 @@ SORTED32(sin_u10_f32, SinU10)
 SORTED32(sin_u35_f32, SinU35)
 SORTED32(cos_u10_f32, CosU10)
 SORTED32(cos_u35_f32, CosU35)
+#undef SORTED32
+#endif  // SLEEFCU_FUNCTORS_ONLY

@@ -31,29 +31,29 @@ constexpr uint64_t B15 = 0x402e000000000000ull;   // bits of 15.0
 constexpr uint64_t B1 = 0x3ff0000000000000ull;    // bits of 1.0
 constexpr uint64_t B1E14 = 0x42d6bcc41e900000ull; // bits of 1e14
 
-__constant__ double kSinU10[7] = {
+static __constant__ double kSinU10[7] = {
   0x1.111111111109fp-7, -0x1.a01a01a0129ddp-13, 0x1.71de3a51b383dp-19,
   -0x1.ae64546a1a9ebp-26, 0x1.6123b2c07aaa7p-33, -0x1.ae3cc8078333ap-41,
   0x1.877f977ffe028p-49};
 constexpr double SIN_C1H = -0x1.5555555555555p-3, SIN_C1L = 0x1.07fb00106bcfdp-57;
-__constant__ double kSinU35[8] = {
+static __constant__ double kSinU35[8] = {
   -0x1.5555555555555p-3, 0x1.11111111110bdp-7, -0x1.a01a01a013e17p-13,
   0x1.71de3a5220856p-19, -0x1.ae645492b5795p-26, 0x1.6123bb419f3c8p-33,
   -0x1.ae3ea885fb135p-41, 0x1.87ab1397c30b7p-49};
 // Appendix A tan listing, constant term first
-__constant__ double kTanC[8] = {
+static __constant__ double kTanC[8] = {
   0x1.111111110e933p-3, 0x1.ba1ba1bdcec06p-5, 0x1.664f4729f98e5p-6,
   0x1.226e7bfa35090p-7, 0x1.d6c27c371c959p-9, 0x1.7eef631e20b93p-10,
   0x1.269be400de3afp-11, 0x1.5445f555134edp-12};
 constexpr double TAN_C3 = 0x1.5555555555568p-2;
 constexpr double SC_S1H = -0x1.5555555555543p-3, SC_S1L = 0x1.cc5eebaea7e3cp-57;
-__constant__ double kScSU10[5] = {
+static __constant__ double kScSU10[5] = {
   0x1.111111110eea5p-7, -0x1.a01a019ad6669p-13, 0x1.71de3466b0f92p-19,
   -0x1.ae5d912c0cb21p-26, 0x1.5d558cd2a4be1p-33};
-__constant__ double kScC[6] = {
+static __constant__ double kScC[6] = {
   0x1.5555555555546p-5, -0x1.6c16c16c14555p-10, 0x1.a01a019b8491fp-16,
   -0x1.27e4f73296656p-22, 0x1.1ee95b26826a1p-29, -0x1.8f6489336e5adp-37};
-__constant__ double kScSU35[6] = {
+static __constant__ double kScSU35[6] = {
   -0x1.5555555555543p-3, 0x1.111111110ef1dp-7, -0x1.a01a019ae1837p-13,
   0x1.71de346e3d979p-19, -0x1.ae5d95f8b7e3ep-26, 0x1.5d56b550f4cf7p-33};
 
@@ -94,7 +94,7 @@ __device__ __forceinline__ void ph_step(d2 &x, int &q) {
 // quarter-turn count mod 4.  Only lanes with |d| >= 1e14 or non-finite d
 // call it.  The table drops M*I(E)/2 turns: a half turn is restored through
 // q when the mantissa and I(E) are odd.
-__device__ __noinline__ d2 ph(double d, int &q) {
+static __device__ __noinline__ d2 ph(double d, int &q) {
   uint64_t b = bits(d);
   bool fin = is_finite_b(b);
   uint64_t bf = fin ? b : 0;
@@ -362,6 +362,7 @@ struct SinCosU35 {
 }  // namespace trig64
 }  // namespace sleefcu
 
+#ifndef SLEEFCU_FUNCTORS_ONLY
 using namespace sleefcu;
 
 #define UNARY64(NAME, F)                                                                    \
@@ -384,3 +385,5 @@ extern "C" sleefcu_status sleefcu_sincos_u35_f64(const double *x, double *os, do
                                                  sleefcu_stream s) {
   return launch_sorted64_dual<trig64::SinCosU35>("sleefcu_sincos_u35_f64", x, os, oc, n, s);
 }
+#undef UNARY64
+#endif  // SLEEFCU_FUNCTORS_ONLY

@@ -169,3 +169,31 @@ def workload(fn, n, key="c2", dtype=np.float64, operand=0):
         with np.errstate(over="ignore", under="ignore"):
             x = x.astype(np.float32)
     return x
+
+
+def to_bf16_bits(x32):
+    """binary32 -> bf16 bit patterns, round-to-nearest-even (input preparation)."""
+    b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return r.astype(np.uint16)
+
+
+def bits16_to_f64(h, fmt):
+    """exact double values of bf16 / binary16 bit patterns."""
+    h = np.asarray(h, dtype=np.uint16)
+    if fmt == "bf16":
+        return (h.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+    return h.view(np.float16).astype(np.float64)
+
+
+def activations(key, shape, fmt, sigma=3.0):
+    """N(0, sigma) activations of the given shape as bf16 / binary16 bit
+    patterns (Box-Muller in double, then binary32, then the 16-bit format)."""
+    n = int(np.prod(shape))
+    u1 = (raw(key + "/u1", n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 + 2.0 ** -54
+    u2 = (raw(key + "/u2", n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    z = sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    x32 = z.astype(np.float32)
+    if fmt == "bf16":
+        return to_bf16_bits(x32).reshape(shape)
+    return x32.astype(np.float16).view(np.uint16).reshape(shape)

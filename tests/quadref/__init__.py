@@ -33,6 +33,8 @@ def lib():
         for f in ("quad_ulp_f64", "quad_ulp_f32"):
             getattr(_lib, f).argtypes = [ctypes.c_char_p] + [ctypes.c_void_p] * 4 + [ctypes.c_size_t]
         _lib.quad_ref_f64.argtypes = [ctypes.c_char_p] + [ctypes.c_void_p] * 3 + [ctypes.c_size_t]
+        _lib.quad_ulp_gen.argtypes = [ctypes.c_char_p] + [ctypes.c_void_p] * 3 + [ctypes.c_size_t] + \
+            [ctypes.c_int] * 3
     return _lib
 
 
@@ -63,3 +65,18 @@ def ref(fn, x, y=None):
     if lib().quad_ref_f64(fn.encode(), x.ctypes.data, yp, out.ctypes.data, x.size) != 0:
         raise KeyError(fn)
     return out
+
+
+FORMATS = {"bf16": (8, -126, 127), "f16": (11, -14, 15)}
+
+
+def ulp_err_fmt(fn, x, out, fmt):
+    """ULP error of out (exact values given as doubles) in a 16-bit format."""
+    p, emin, emax = FORMATS[fmt]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.ascontiguousarray(out, dtype=np.float64)
+    err = np.empty(x.size)
+    if lib().quad_ulp_gen(fn.encode(), x.ctypes.data, out.ctypes.data, err.ctypes.data, x.size,
+                          p, emin, emax) != 0:
+        raise KeyError(fn)
+    return err

@@ -109,3 +109,16 @@ int quad_ref_f64(const char *fn, const double *x, const double *y, double *out, 
   }
   return 0;
 }
+
+/* err[i] = ULP error of out[i] (given as a double) in a format with p-bit
+ * significands and exponent range [emin, emax] (bf16: 8, -126, 127; binary16:
+ * 11, -14, 15), inputs given as doubles */
+int quad_ulp_gen(const char *fn, const double *x, const double *out, double *err, size_t n,
+                 int p, int emin, int emax) {
+  for (size_t i = 0; i < n; i++) {
+    Q r;
+    if (eval(fn, x[i], 0.0, &r)) return -1;
+    err[i] = ulp_err(r, out[i], p, emin, emax);
+  }
+  return 0;
+}

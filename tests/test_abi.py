@@ -30,7 +30,7 @@ def test_binding_covers_header():
     names = set(declared())
     for e in sleefcu.entry_points():
         assert "sleefcu_" + e in names, e
-    fn_decl = {n for n in names if re.match(r"sleefcu_\w+_u(10|35)_(f64|f32)$", n)}
+    fn_decl = {n for n in names if re.match(r"sleefcu_\w+_u(10|35)_(f64|f32|bf16|f16)$", n)}
     assert fn_decl == {"sleefcu_" + e for e in sleefcu.entry_points()}
 
 
