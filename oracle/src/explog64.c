@@ -18,6 +18,7 @@
  */
 #include "common.h"
 #include "coeffs64.h"
+#include "explog64.h"
 
 #define R_LN2 0x1.71547652b82fep0    /* RN(1/ln2) */
 #define L2A 0x1.62e42fefa39efp-1     /* RN(ln2) */
@@ -33,12 +34,20 @@ static double scale2(double y, int k) {
   int k1 = k / 2, k2 = k - k1;
   return (y * pow2i(k1)) * pow2i(k2);
 }
+double oracle_scale2(double y, int k) { return scale2(y, k); }
 
 /* ---------------- exp ---------------- */
 static const double EXP_U10[11] = { EXP_U10_COEFFS };
 static const double EXP_U35[9] = { EXP_U35_COEFFS };
 
 /* u35: e^r = 1 + (r + r^2 u(r)) in double, r rounded once */
+/* e^r - 1 for |r| <= ln2/2 (u35 polynomial), rounded */
+double oracle_expm1_r_u35(double r) {
+  double s = r * r;
+  double u = poly_d(r, EXP_U35, 9);
+  return fma(s, u, r);
+}
+
 static double exp_core(double x, const double *c, int nc) {
   double xc = fabs(x) <= 746 ? x : 0.0;   /* keeps k small; out-of-range is selected below */
   double k = rint(xc * R_LN2);
@@ -55,16 +64,20 @@ static double exp_core(double x, const double *c, int nc) {
 /* u10: the same reduction keeps the rounding residual rl of r = h - k L2B
  * (h = x - k L2A exact) and forms 1 + r as a DD, so that the only rounding
  * of order one ulp is the final one */
+double oracle_exp_tail_u10(double r, double rl, double k) {
+  double s = r * r;
+  double w = fma(s, poly_d(r, EXP_U10, 11), rl);
+  dd_t o = ddadd_d2_d_d(1.0, r);
+  return scale2(o.x + (o.y + w), (int)k);
+}
+
 static double exp_core_u10(double x) {
   double xc = fabs(x) <= 746 ? x : 0.0;
   double k = rint(xc * R_LN2);
   double h = fma(k, -L2A, xc);
   double r = fma(k, -L2B, h);
   double rl = fma(k, -L2B, h - r);
-  double s = r * r;
-  double w = fma(s, poly_d(r, EXP_U10, 11), rl);
-  dd_t o = ddadd_d2_d_d(1.0, r);
-  double y = scale2(o.x + (o.y + w), (int)k);
+  double y = oracle_exp_tail_u10(r, rl, k);
   if (!(fabs(x) <= 746)) y = x > 0 ? INFINITY : (x < 0 ? 0.0 : NAN);
   return canon(y);
 }
@@ -119,6 +132,40 @@ double oracle_log_u35_f64(double x) {
   return canon(log_special(x, y));
 }
 
+/* log of a DD a > 0 with a normal, finite head: a = m 2^e, m in [0.75, 1.5)
+ * (heads below DBL_MIN are scaled by 2^64 first); returns log m = z +
+ * z^3 P(z^2) as a DD, with z = 2(m-1)/(m+1) in DD and the u10 polynomial,
+ * and e through *ep (Section 5.5 applied to a DD argument). */
+dd_t oracle_logm_u10(dd_t a, int *ep) {
+  int off = 0;
+  if (a.x < 0x1p-1022) { a = ddscale_d2_d2_d(a, 0x1p64); off = 64; }
+  int ex = ilogb(a.x);
+  dd_t m = ddscale_d2_d2_d(a, ldexp(1.0, -ex));
+  if (m.x >= 1.5) { m = ddscale_d2_d2_d(m, 0.5); ex++; }
+  dd_t num = ddscale_d2_d2_d(ddadd2_d2_d_d(m.x - 1.0, m.y), 2.0);
+  dd_t den = ddadd2_d2_d_d2(1.0, m);
+  dd_t z = dddiv_d2_d2_d2(num, den);
+  double t = z.x * z.x;
+  double corr = (z.x * t) * poly_d(t, LOG_U10, 8);
+  *ep = ex - off;
+  return ddadd_d2_d2_d(z, corr);
+}
+
+/* log m in double for the u35 forms: a = m 2^e as above, z rounded once
+ * from the DD numerator */
+double oracle_logm_u35(dd_t a, int *ep) {
+  int off = 0;
+  if (a.x < 0x1p-1022) { a = ddscale_d2_d2_d(a, 0x1p64); off = 64; }
+  int ex = ilogb(a.x);
+  dd_t m = ddscale_d2_d2_d(a, ldexp(1.0, -ex));
+  if (m.x >= 1.5) { m = ddscale_d2_d2_d(m, 0.5); ex++; }
+  double num = 2.0 * ((m.x - 1.0) + m.y);
+  double z = num / (1.0 + m.x);
+  double t = z * z;
+  *ep = ex - off;
+  return fma(z * t, poly_d(t, LOG_U35, 7), z);
+}
+
 /* ---------------- pow ---------------- */
 static const double PL_C1H = POWLOG_C1H, PL_C1L = POWLOG_C1L;
 static const double POWLOG[9] = { POWLOG_COEFFS };
@@ -141,17 +188,27 @@ static dd_t logk(double a) {
 }
 
 /* e^Y for a DD argument (13-term polynomial, the leading terms in DD) */
-static double expk(dd_t Y) {
-  double yh = Y.x, yl = Y.y;
-  if (!(fabs(yh) <= 746)) { yh = 0; yl = 0; }
-  double k = rint(yh * R_LN2);
-  double u = fma(k, -L2A, yh);
-  dd_t r = ddadd2_d2_d_d(u, fma(k, -L2B, yl));
+/* For |Y.x| <= 746: k = rint(Y.x / ln2) and e^(Y - k ln2) - 1 as a DD.
+ * Y.x - k L2A is exact (k has at most 11 bits and |result| < 1/2), so the
+ * reduced argument is a DD to about 2^-100. */
+dd_t oracle_expk_s(dd_t Y, double *kp) {
+  double k = rint(Y.x * R_LN2);
+  double u = fma(k, -L2A, Y.x);
+  dd_t r = ddadd2_d2_d_d(u, fma(k, -L2B, Y.y));
   dd_t q = ddscale_d2_d2_d(ddsqu_d2_d2(r), 0.5);
   double p = poly_d(r.x, POWEXP, 10);
   double v = ((r.x * r.x) * r.x) * p;
   dd_t s = ddadd2_d2_d2_d2(r, q);
   s = ddadd2_d2_d2_d(s, v);
+  *kp = k;
+  return s;
+}
+
+static double expk(dd_t Y) {
+  double yh = Y.x, yl = Y.y;
+  if (!(fabs(yh) <= 746)) { yh = 0; yl = 0; }
+  double k;
+  dd_t s = oracle_expk_s(dd(yh, yl), &k);
   s = ddadd_d2_d_d2(1.0, s);
   double y = scale2(s.x + s.y, (int)k);
   if (!(fabs(Y.x) <= 746)) y = Y.x > 0 ? INFINITY : 0.0;

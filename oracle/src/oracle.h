@@ -24,6 +24,32 @@ double oracle_exp_u10_f64(double);
 double oracle_exp_u35_f64(double);
 double oracle_log_u10_f64(double);
 double oracle_log_u35_f64(double);
+double oracle_exp2_u10_f64(double);
+double oracle_exp2_u35_f64(double);
+double oracle_exp10_u10_f64(double);
+double oracle_exp10_u35_f64(double);
+double oracle_expm1_u10_f64(double);
+double oracle_expm1_u35_f64(double);
+double oracle_log2_u10_f64(double);
+double oracle_log2_u35_f64(double);
+double oracle_log10_u10_f64(double);
+double oracle_log10_u35_f64(double);
+double oracle_log1p_u10_f64(double);
+double oracle_log1p_u35_f64(double);
+double oracle_cbrt_u10_f64(double);
+double oracle_cbrt_u35_f64(double);
+double oracle_sinh_u10_f64(double);
+double oracle_sinh_u35_f64(double);
+double oracle_cosh_u10_f64(double);
+double oracle_cosh_u35_f64(double);
+double oracle_tanh_u10_f64(double);
+double oracle_tanh_u35_f64(double);
+double oracle_asinh_u10_f64(double);
+double oracle_asinh_u35_f64(double);
+double oracle_acosh_u10_f64(double);
+double oracle_acosh_u35_f64(double);
+double oracle_atanh_u10_f64(double);
+double oracle_atanh_u35_f64(double);
 double oracle_pow_u10_f64(double, double);
 double oracle_pow_u35_f64(double, double);
 double oracle_asin_u10_f64(double);
