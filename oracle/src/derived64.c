@@ -20,7 +20,8 @@
  * expm1  e^x - 1 = 2^k s + (2^k - 1) with s = e^r - 1 as a DD: no
  *        cancellation at k = 0 and exact 2^k - 1 elsewhere.
  * log2, log10, log1p   the log core on a DD argument (1 + x exactly for
- *        log1p), the result multiplied by DD constants.
+ *        log1p), the result multiplied by DD constants (u10) or the core
+ *        rounded to double and multiplied in double (u35).
  * cbrt   a = m 2^(3q + i) with a in [1, 8); a^(-1/3) from a polynomial and
  *        one Newton step without division; y = a z^2 and one Newton step on
  *        y whose residual y^3 - a is exact in DD (u10) or rounded (u35).
@@ -57,6 +58,10 @@ static const double EXPM1_U35[10] = { EXPM1_U35_COEFFS };
 static const double CBRT_P[8] = { CBRT_COEFFS };
 static const double CBRT_C[3] = { 1.0, 0x1.965fea53d6e3dp-1, 0x1.428a2f98d728bp-1 };  /* RN(2^(-i/3)) */
 
+/* e^t - 1 for |t| <= ln2/2 with the polynomial fitted relative to e^t - 1
+ * (12 terms), rounded once by the last fma */
+static double em1_r_u35(double t) { return fma(t * t, poly_d(t, EXPM1_U35, 10), t); }
+
 /* ---------------- exp2, exp10 ---------------- */
 double oracle_exp2_u10_f64(double x) {
   double xc = fabs(x) <= 1100 ? x : 0.0;
@@ -72,7 +77,7 @@ double oracle_exp2_u35_f64(double x) {
   double xc = fabs(x) <= 1100 ? x : 0.0;
   double k = rint(xc);
   double t = (xc - k) * L2A;
-  double y = oracle_scale2(1.0 + oracle_expm1_r_u35(t), (int)k);
+  double y = oracle_scale2(1.0 + em1_r_u35(t), (int)k);
   if (!(fabs(x) <= 1100)) y = x > 0 ? INFINITY : (x < 0 ? 0.0 : NAN);
   return canon(y);
 }
@@ -93,18 +98,19 @@ double oracle_exp10_u35_f64(double x) {
   double xc = fabs(x) <= 350 ? x : 0.0;
   double k = rint(xc * LOG2_10);
   double r = fma(k, -L10B, fma(k, -L10A, xc));
-  double y = oracle_scale2(1.0 + oracle_expm1_r_u35(r * LN10H), (int)k);
+  double y = oracle_scale2(1.0 + em1_r_u35(r * LN10H), (int)k);
   if (!(fabs(x) <= 350)) y = x > 0 ? INFINITY : (x < 0 ? 0.0 : NAN);
   return canon(y);
 }
 
 /* ---------------- expm1 ---------------- */
-/* e^a - 1 as a DD for -40 < a <= 40 (2^k - 1 is exact up to k = 53) */
+/* e^a - 1 as a DD for -40 < a <= 40: 2^k s + (2^k - 1), the second term an
+ * exact DD */
 static dd_t em1_dd(double a) {
   double k;
   dd_t s = oracle_expk_s(dd(a, 0.0), &k);
   double p = ldexp(1.0, (int)k);
-  return ddadd2_d2_d_d2(p - 1.0, ddscale_d2_d2_d(s, p));
+  return ddadd2_d2_d2_d2(ddadd2_d2_d_d(p, -1.0), ddscale_d2_d2_d(s, p));
 }
 
 double oracle_expm1_u10_f64(double x) {
@@ -117,7 +123,7 @@ double oracle_expm1_u10_f64(double x) {
     y = oracle_scale2(e.x + e.y, (int)k);
   } else {
     double p = ldexp(1.0, (int)k);
-    dd_t r = ddadd2_d2_d_d2(p - 1.0, ddscale_d2_d2_d(s, p));
+    dd_t r = ddadd2_d2_d2_d2(ddadd2_d2_d_d(p, -1.0), ddscale_d2_d2_d(s, p));
     y = r.x + r.y;
   }
   if (x == 0) y = x;
@@ -131,7 +137,7 @@ static double em1_u35(double xc, double *kp) {
   double k = rint(xc * R_LN2);
   double r = fma(k, -L2B, fma(k, -L2A, xc));
   *kp = k;
-  return fma(r * r, poly_d(r, EXPM1_U35, 10), r);
+  return em1_r_u35(r);
 }
 
 double oracle_expm1_u35_f64(double x) {
@@ -170,8 +176,8 @@ double oracle_log2_u10_f64(double x) {
 double oracle_log2_u35_f64(double x) {
   double a = (x > 0 && x <= 0x1.fffffffffffffp1023) ? x : 1.0;
   int e;
-  double lm = oracle_logm_u35(dd(a, 0.0), &e);
-  return canon(log_special(x, fma(lm, RL2H, (double)e)));
+  dd_t lm = oracle_logm_u10(dd(a, 0.0), &e);
+  return canon(log_special(x, fma(lm.x + lm.y, RL2H, (double)e)));
 }
 
 double oracle_log10_u10_f64(double x) {
@@ -187,8 +193,8 @@ double oracle_log10_u10_f64(double x) {
 double oracle_log10_u35_f64(double x) {
   double a = (x > 0 && x <= 0x1.fffffffffffffp1023) ? x : 1.0;
   int e;
-  double lm = oracle_logm_u35(dd(a, 0.0), &e);
-  return canon(log_special(x, fma((double)e, L10A, lm * RL10H)));
+  dd_t lm = oracle_logm_u10(dd(a, 0.0), &e);
+  return canon(log_special(x, fma((double)e, L10A, (lm.x + lm.y) * RL10H)));
 }
 
 /* log a as a DD for a DD a > 0 */

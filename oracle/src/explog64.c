@@ -41,13 +41,6 @@ static const double EXP_U10[11] = { EXP_U10_COEFFS };
 static const double EXP_U35[9] = { EXP_U35_COEFFS };
 
 /* u35: e^r = 1 + (r + r^2 u(r)) in double, r rounded once */
-/* e^r - 1 for |r| <= ln2/2 (u35 polynomial), rounded */
-double oracle_expm1_r_u35(double r) {
-  double s = r * r;
-  double u = poly_d(r, EXP_U35, 9);
-  return fma(s, u, r);
-}
-
 static double exp_core(double x, const double *c, int nc) {
   double xc = fabs(x) <= 746 ? x : 0.0;   /* keeps k small; out-of-range is selected below */
   double k = rint(xc * R_LN2);

@@ -14,8 +14,6 @@
 double oracle_scale2(double y, int k);
 /* 2^k (1 + r + rl) with the 1-ULP exp polynomial; |r| <= ln2/2 (Section 5.6) */
 double oracle_exp_tail_u10(double r, double rl, double k);
-/* e^r - 1 with the 3.5-ULP exp polynomial, |r| <= ln2/2 */
-double oracle_expm1_r_u35(double r);
 /* e^(Y - k ln2) - 1 as a DD and k = rint(Y.x / ln2), |Y.x| <= 746 */
 dd_t oracle_expk_s(dd_t Y, double *k);
 /* log m as a DD with a = m 2^e, m in [0.75, 1.5), for a DD a > 0 */
