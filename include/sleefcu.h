@@ -136,6 +136,58 @@ sleefcu_status sleefcu_remainder_u10_f64(const double *x, const double *y, doubl
 sleefcu_status sleefcu_remainder_u35_f64(const double *x, const double *y, double *out, size_t n,
                                          sleefcu_stream stream);
 
+/* ---------------- functions built on the exp/log cores, FP64 ----------------
+ * The paper lists these in the library without their steps; each is a fixed
+ * IEEE sequence on the exp/log cores of Sections 5.5-5.7 with DD arithmetic
+ * where the 1-ULP bound needs it (Section 3):
+ * exp2 / exp10: k = rint(x) or rint(x log2 10), the reduced argument times
+ *   ln2 or ln10 in DD, then the exp polynomial; overflow to +inf, underflow
+ *   to 0 with subnormals rounded once; exp2(k) = 2^k and (u10) exp10(k) =
+ *   10^k exactly where representable.
+ * expm1: 2^k s + (2^k - 1) with s = e^r - 1 in DD; expm1(-0) = -0,
+ *   expm1(-inf) = -1, expm1(x <= -40) = -1.
+ * log2 / log10: the log core on the argument, times 1/ln2 or 1/ln10 in DD
+ *   (u10) or rounded and one fma (u35); log2(2^k) = k, log10(10^k) = k;
+ *   special values as log.  log1p: the log core on 1 + x formed exactly as
+ *   a DD; log1p(-1) = -inf, log1p(x < -1) = NaN, log1p(+-0) = +-0.
+ * cbrt: x = a 2^(3q), a in [1, 8); a division-free Newton step on a^(-1/3),
+ *   then one Newton step on the root with the residual in DD (u10) or one
+ *   fma (u35); cbrt(-x) = -cbrt(x), cbrt(+-0) = +-0, cbrt(+-inf) = +-inf.
+ * sinh / cosh / tanh: from e^|x| - 1 (e^(2|x|) - 1 for tanh) in DD; sinh
+ *   and cosh overflow only above 710.475; tanh(x) = +-1 for |x| > 20.
+ * asinh / acosh / atanh: log of the DD argument |x| + sqrt(x^2+1),
+ *   x + sqrt((x-1)(x+1)), (1+|x|)/(1-|x|); acosh(1) = +0, acosh(x < 1) = NaN,
+ *   atanh(+-1) = +-inf, atanh(|x| > 1) = NaN.  Their u35 entry points run
+ *   the u10 algorithm (no cheaper form keeps the cancellation exact).
+ * Odd functions return -f(|x|) bit for bit; NaN results are the canonical
+ * quiet NaN. */
+sleefcu_status sleefcu_exp2_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp2_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+
 /* ---------------- FP32 family (float-float forms) ----------------
  * The same methods in binary32 arithmetic only, with float-float pairs where
  * the 1-ULP bound needs them (the paper describes the FP64 functions; "all
@@ -207,6 +259,9 @@ typedef enum {
   SLEEFCU_FN_SIN = 0, SLEEFCU_FN_COS, SLEEFCU_FN_TAN, SLEEFCU_FN_SINCOS, SLEEFCU_FN_ASIN,
   SLEEFCU_FN_ACOS, SLEEFCU_FN_ATAN, SLEEFCU_FN_ATAN2, SLEEFCU_FN_EXP, SLEEFCU_FN_LOG, SLEEFCU_FN_POW,
   SLEEFCU_FN_FMOD, SLEEFCU_FN_REMAINDER, SLEEFCU_FN_LOG1P, SLEEFCU_FN_TANH, SLEEFCU_FN_ERF,
+  SLEEFCU_FN_EXP2, SLEEFCU_FN_EXP10, SLEEFCU_FN_EXPM1, SLEEFCU_FN_LOG2, SLEEFCU_FN_LOG10,
+  SLEEFCU_FN_CBRT, SLEEFCU_FN_SINH, SLEEFCU_FN_COSH, SLEEFCU_FN_ASINH, SLEEFCU_FN_ACOSH,
+  SLEEFCU_FN_ATANH,
   SLEEFCU_FN_COUNT
 } sleefcu_fn;
 typedef enum { SLEEFCU_F64 = 0, SLEEFCU_F32 = 1, SLEEFCU_BF16 = 2, SLEEFCU_F16 = 3 } sleefcu_dtype;

@@ -18,6 +18,7 @@
 #include "fmod_f64.cu"
 #include "trig_f32.cu"
 #include "explog_f32.cu"
+#include "derived_f64.cu"
 #undef SLEEFCU_FUNCTORS_ONLY
 
 #include <cstdio>
@@ -30,23 +31,94 @@ namespace batch {
 
 enum Kind { U64, B64, SC64, U32, BF, HF };
 
-// entry point table: (code order) name, kind, functor
-// entry point codes: the index in this list
-static const char *kNames[] = {
-    "sin_u10_f64", "sin_u35_f64", "cos_u10_f64", "cos_u35_f64",
-    "tan_u10_f64", "tan_u35_f64", "sincos_u10_f64", "sincos_u35_f64",
-    "asin_u10_f64", "asin_u35_f64", "acos_u10_f64", "acos_u35_f64",
-    "atan_u10_f64", "atan_u35_f64", "atan2_u10_f64", "atan2_u35_f64",
-    "exp_u10_f64", "exp_u35_f64", "log_u10_f64", "log_u35_f64",
-    "pow_u10_f64", "pow_u35_f64", "fmod_u10_f64", "fmod_u35_f64",
-    "remainder_u10_f64", "remainder_u35_f64", "sin_u10_f32", "sin_u35_f32",
-    "cos_u10_f32", "cos_u35_f32", "exp_u10_f32", "exp_u35_f32",
-    "log_u10_f32", "log_u35_f32", "log1p_u10_f32", "log1p_u35_f32",
-    "tanh_u10_f32", "tanh_u35_f32", "erf_u10_f32", "erf_u35_f32",
-    "erf_u10_bf16", "erf_u35_bf16", "tanh_u10_bf16", "tanh_u35_bf16",
-    "exp_u10_bf16", "exp_u35_bf16", "log1p_u10_bf16", "log1p_u35_bf16",
-    "erf_u10_f16", "erf_u35_f16", "tanh_u10_f16", "tanh_u35_f16",
-    "exp_u10_f16", "exp_u35_f16", "log1p_u10_f16", "log1p_u35_f16"};
+// entry point table: code (= position), name, kind, functor
+#define SLEEFCU_BATCH_TABLE(X) \
+  X(0, "sin_u10_f64", U64, trig64::SinU10) \
+  X(1, "sin_u35_f64", U64, trig64::SinU35) \
+  X(2, "cos_u10_f64", U64, trig64::CosU10) \
+  X(3, "cos_u35_f64", U64, trig64::CosU35) \
+  X(4, "tan_u10_f64", U64, trig64::TanU10) \
+  X(5, "tan_u35_f64", U64, trig64::TanU35) \
+  X(6, "sincos_u10_f64", SC64, trig64::SinCosU10) \
+  X(7, "sincos_u35_f64", SC64, trig64::SinCosU35) \
+  X(8, "asin_u10_f64", U64, invtrig64::AsinU10) \
+  X(9, "asin_u35_f64", U64, invtrig64::AsinU35) \
+  X(10, "acos_u10_f64", U64, invtrig64::AcosU10) \
+  X(11, "acos_u35_f64", U64, invtrig64::AcosU35) \
+  X(12, "atan_u10_f64", U64, invtrig64::AtanU10) \
+  X(13, "atan_u35_f64", U64, invtrig64::AtanU35) \
+  X(14, "atan2_u10_f64", B64, invtrig64::Atan2U10) \
+  X(15, "atan2_u35_f64", B64, invtrig64::Atan2U35) \
+  X(16, "exp_u10_f64", U64, explog64::ExpU10) \
+  X(17, "exp_u35_f64", U64, explog64::ExpU35) \
+  X(18, "log_u10_f64", U64, explog64::LogU10) \
+  X(19, "log_u35_f64", U64, explog64::LogU35) \
+  X(20, "pow_u10_f64", B64, explog64::PowU10) \
+  X(21, "pow_u35_f64", B64, explog64::PowU10) \
+  X(22, "fmod_u10_f64", B64, fmod64::FmodF) \
+  X(23, "fmod_u35_f64", B64, fmod64::FmodF) \
+  X(24, "remainder_u10_f64", B64, fmod64::RemainderF) \
+  X(25, "remainder_u35_f64", B64, fmod64::RemainderF) \
+  X(26, "sin_u10_f32", U32, trig32::SinU10) \
+  X(27, "sin_u35_f32", U32, trig32::SinU35) \
+  X(28, "cos_u10_f32", U32, trig32::CosU10) \
+  X(29, "cos_u35_f32", U32, trig32::CosU35) \
+  X(30, "exp_u10_f32", U32, explog32::ExpU10) \
+  X(31, "exp_u35_f32", U32, explog32::ExpU35) \
+  X(32, "log_u10_f32", U32, explog32::LogU10) \
+  X(33, "log_u35_f32", U32, explog32::LogU35) \
+  X(34, "log1p_u10_f32", U32, explog32::Log1pU10) \
+  X(35, "log1p_u35_f32", U32, explog32::Log1pU35) \
+  X(36, "tanh_u10_f32", U32, explog32::TanhU10) \
+  X(37, "tanh_u35_f32", U32, explog32::TanhU35) \
+  X(38, "erf_u10_f32", U32, explog32::ErfU10) \
+  X(39, "erf_u35_f32", U32, explog32::ErfU35) \
+  X(40, "erf_u10_bf16", BF, explog32::ErfU10) \
+  X(41, "erf_u35_bf16", BF, explog32::ErfU35) \
+  X(42, "tanh_u10_bf16", BF, explog32::TanhU10) \
+  X(43, "tanh_u35_bf16", BF, explog32::TanhU35) \
+  X(44, "exp_u10_bf16", BF, explog32::ExpU10) \
+  X(45, "exp_u35_bf16", BF, explog32::ExpU35) \
+  X(46, "log1p_u10_bf16", BF, explog32::Log1pU10) \
+  X(47, "log1p_u35_bf16", BF, explog32::Log1pU35) \
+  X(48, "erf_u10_f16", HF, explog32::ErfU10) \
+  X(49, "erf_u35_f16", HF, explog32::ErfU35) \
+  X(50, "tanh_u10_f16", HF, explog32::TanhU10) \
+  X(51, "tanh_u35_f16", HF, explog32::TanhU35) \
+  X(52, "exp_u10_f16", HF, explog32::ExpU10) \
+  X(53, "exp_u35_f16", HF, explog32::ExpU35) \
+  X(54, "log1p_u10_f16", HF, explog32::Log1pU10) \
+  X(55, "log1p_u35_f16", HF, explog32::Log1pU35) \
+  X(56, "exp2_u10_f64", U64, derived64::Exp2U10) \
+  X(57, "exp2_u35_f64", U64, derived64::Exp2U35) \
+  X(58, "exp10_u10_f64", U64, derived64::Exp10U10) \
+  X(59, "exp10_u35_f64", U64, derived64::Exp10U35) \
+  X(60, "expm1_u10_f64", U64, derived64::Expm1U10) \
+  X(61, "expm1_u35_f64", U64, derived64::Expm1U35) \
+  X(62, "log2_u10_f64", U64, derived64::Log2U10) \
+  X(63, "log2_u35_f64", U64, derived64::Log2U35) \
+  X(64, "log10_u10_f64", U64, derived64::Log10U10) \
+  X(65, "log10_u35_f64", U64, derived64::Log10U35) \
+  X(66, "log1p_u10_f64", U64, derived64::Log1pU10) \
+  X(67, "log1p_u35_f64", U64, derived64::Log1pU35) \
+  X(68, "cbrt_u10_f64", U64, derived64::CbrtU10) \
+  X(69, "cbrt_u35_f64", U64, derived64::CbrtU35) \
+  X(70, "sinh_u10_f64", U64, derived64::SinhU10) \
+  X(71, "sinh_u35_f64", U64, derived64::SinhU35) \
+  X(72, "cosh_u10_f64", U64, derived64::CoshU10) \
+  X(73, "cosh_u35_f64", U64, derived64::CoshU35) \
+  X(74, "tanh_u10_f64", U64, derived64::TanhU10) \
+  X(75, "tanh_u35_f64", U64, derived64::TanhU35) \
+  X(76, "asinh_u10_f64", U64, derived64::AsinhU10) \
+  X(77, "asinh_u35_f64", U64, derived64::AsinhU10) \
+  X(78, "acosh_u10_f64", U64, derived64::AcoshU10) \
+  X(79, "acosh_u35_f64", U64, derived64::AcoshU10) \
+  X(80, "atanh_u10_f64", U64, derived64::AtanhU10) \
+  X(81, "atanh_u35_f64", U64, derived64::AtanhU10)
+
+#define SLEEFCU_BATCH_NAME(c, name, kind, F) name,
+static const char *kNames[] = {SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_NAME)};
+#undef SLEEFCU_BATCH_NAME
 constexpr int kCodes = sizeof(kNames) / sizeof(kNames[0]);
 
 struct Desc {
@@ -136,62 +208,10 @@ __global__ void __launch_bounds__(512) k_batch(const Desc *__restrict__ d, const
     long long b = (t - pre[item]) * (long long)tile;
     long long e = b + tile < D.n ? b + tile : D.n;
     switch (D.code) {
-      case 0: run<U64, trig64::SinU10>(D, b, e, vec); break;
-      case 1: run<U64, trig64::SinU35>(D, b, e, vec); break;
-      case 2: run<U64, trig64::CosU10>(D, b, e, vec); break;
-      case 3: run<U64, trig64::CosU35>(D, b, e, vec); break;
-      case 4: run<U64, trig64::TanU10>(D, b, e, vec); break;
-      case 5: run<U64, trig64::TanU35>(D, b, e, vec); break;
-      case 6: run<SC64, trig64::SinCosU10>(D, b, e, vec); break;
-      case 7: run<SC64, trig64::SinCosU35>(D, b, e, vec); break;
-      case 8: run<U64, invtrig64::AsinU10>(D, b, e, vec); break;
-      case 9: run<U64, invtrig64::AsinU35>(D, b, e, vec); break;
-      case 10: run<U64, invtrig64::AcosU10>(D, b, e, vec); break;
-      case 11: run<U64, invtrig64::AcosU35>(D, b, e, vec); break;
-      case 12: run<U64, invtrig64::AtanU10>(D, b, e, vec); break;
-      case 13: run<U64, invtrig64::AtanU35>(D, b, e, vec); break;
-      case 14: run<B64, invtrig64::Atan2U10>(D, b, e, vec); break;
-      case 15: run<B64, invtrig64::Atan2U35>(D, b, e, vec); break;
-      case 16: run<U64, explog64::ExpU10>(D, b, e, vec); break;
-      case 17: run<U64, explog64::ExpU35>(D, b, e, vec); break;
-      case 18: run<U64, explog64::LogU10>(D, b, e, vec); break;
-      case 19: run<U64, explog64::LogU35>(D, b, e, vec); break;
-      case 20: run<B64, explog64::PowU10>(D, b, e, vec); break;
-      case 21: run<B64, explog64::PowU10>(D, b, e, vec); break;
-      case 22: run<B64, fmod64::FmodF>(D, b, e, vec); break;
-      case 23: run<B64, fmod64::FmodF>(D, b, e, vec); break;
-      case 24: run<B64, fmod64::RemainderF>(D, b, e, vec); break;
-      case 25: run<B64, fmod64::RemainderF>(D, b, e, vec); break;
-      case 26: run<U32, trig32::SinU10>(D, b, e, vec); break;
-      case 27: run<U32, trig32::SinU35>(D, b, e, vec); break;
-      case 28: run<U32, trig32::CosU10>(D, b, e, vec); break;
-      case 29: run<U32, trig32::CosU35>(D, b, e, vec); break;
-      case 30: run<U32, explog32::ExpU10>(D, b, e, vec); break;
-      case 31: run<U32, explog32::ExpU35>(D, b, e, vec); break;
-      case 32: run<U32, explog32::LogU10>(D, b, e, vec); break;
-      case 33: run<U32, explog32::LogU35>(D, b, e, vec); break;
-      case 34: run<U32, explog32::Log1pU10>(D, b, e, vec); break;
-      case 35: run<U32, explog32::Log1pU35>(D, b, e, vec); break;
-      case 36: run<U32, explog32::TanhU10>(D, b, e, vec); break;
-      case 37: run<U32, explog32::TanhU35>(D, b, e, vec); break;
-      case 38: run<U32, explog32::ErfU10>(D, b, e, vec); break;
-      case 39: run<U32, explog32::ErfU35>(D, b, e, vec); break;
-      case 40: run<BF, explog32::ErfU10>(D, b, e, vec); break;
-      case 41: run<BF, explog32::ErfU35>(D, b, e, vec); break;
-      case 42: run<BF, explog32::TanhU10>(D, b, e, vec); break;
-      case 43: run<BF, explog32::TanhU35>(D, b, e, vec); break;
-      case 44: run<BF, explog32::ExpU10>(D, b, e, vec); break;
-      case 45: run<BF, explog32::ExpU35>(D, b, e, vec); break;
-      case 46: run<BF, explog32::Log1pU10>(D, b, e, vec); break;
-      case 47: run<BF, explog32::Log1pU35>(D, b, e, vec); break;
-      case 48: run<HF, explog32::ErfU10>(D, b, e, vec); break;
-      case 49: run<HF, explog32::ErfU35>(D, b, e, vec); break;
-      case 50: run<HF, explog32::TanhU10>(D, b, e, vec); break;
-      case 51: run<HF, explog32::TanhU35>(D, b, e, vec); break;
-      case 52: run<HF, explog32::ExpU10>(D, b, e, vec); break;
-      case 53: run<HF, explog32::ExpU35>(D, b, e, vec); break;
-      case 54: run<HF, explog32::Log1pU10>(D, b, e, vec); break;
-      case 55: run<HF, explog32::Log1pU35>(D, b, e, vec); break;
+#define SLEEFCU_BATCH_CASE(c, name, kind, F) \
+  case c: run<kind, F>(D, b, e, vec); break;
+      SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_CASE)
+#undef SLEEFCU_BATCH_CASE
       default: break;
     }
   }
@@ -205,8 +225,10 @@ namespace {
 using namespace sleefcu;
 using namespace sleefcu::batch;
 
-const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin", "cos", "tan", "sincos", "asin", "acos", "atan", "atan2",
-                                          "exp", "log", "pow", "fmod", "remainder", "log1p", "tanh", "erf"};
+const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin",   "cos",   "tan",   "sincos", "asin",  "acos",  "atan",
+                                          "atan2", "exp",   "log",   "pow",    "fmod",  "remainder",
+                                          "log1p", "tanh",  "erf",   "exp2",   "exp10", "expm1", "log2",
+                                          "log10", "cbrt",  "sinh",  "cosh",   "asinh", "acosh", "atanh"};
 const char *kTypeNames[4] = {"f64", "f32", "bf16", "f16"};
 
 int code_of(const sleefcu_batch_item &it) {

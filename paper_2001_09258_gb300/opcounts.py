@@ -47,6 +47,40 @@ OPS = {
     "fmod_u35_f64": {"setup": 4, "step": 17},
     "remainder_u10_f64": {"setup": 9, "step": 17},
     "remainder_u35_f64": {"setup": 9, "step": 17},
+    # functions on the exp/log cores.  Building blocks: exp tail (u10) 20,
+    # DD exp core (k, e^r - 1 as a DD) 46, 2^k s + 2^k - 1 in DD 16, log core
+    # on a DD argument 42 (u35 form 20), DD log 52; DD ops: TwoSum 6,
+    # FastTwoSum 3, DD+DD 8 (fast 5), d+DD 7 (fast 4), DD*d 3, DD*DD 4,
+    # DD/DD 6, 1/DD 4, sqrt of a DD 5; a polynomial of n coefficients costs
+    # n-1 fma plus the squarings of Estrin's scheme
+    "exp2_u10_f64": {"all": 25},
+    "exp2_u35_f64": {"all": 18},
+    "exp10_u10_f64": {"all": 30},
+    "exp10_u35_f64": {"all": 20},
+    "expm1_u10_f64": {"all": 63},
+    "expm1_u35_f64": {"all": 20},
+    "log2_u10_f64": {"all": 54},
+    "log2_u35_f64": {"all": 44},
+    "log10_u10_f64": {"all": 57},
+    "log10_u35_f64": {"all": 45},
+    "log1p_u10_f64": {"all": 59},
+    "log1p_u35_f64": {"all": 27},
+    "cbrt_u10_f64": {"all": 29},
+    "cbrt_u35_f64": {"all": 24},
+    # sinh/cosh: "small" |x| <= 22 (DD formula), "big" otherwise (e^|x|/2)
+    "sinh_u10_f64": {"small": 85, "big": 51},
+    "cosh_u10_f64": {"small": 63, "big": 51},
+    "tanh_u10_f64": {"all": 77},
+    "sinh_u35_f64": {"small": 24, "big": 19},
+    "cosh_u35_f64": {"small": 23, "big": 19},
+    "tanh_u35_f64": {"all": 23},
+    # asinh/acosh: "big" |x| > 2^500 skips the square root
+    "asinh_u10_f64": {"small": 74, "big": 61},
+    "asinh_u35_f64": {"small": 74, "big": 61},
+    "acosh_u10_f64": {"small": 81, "big": 61},
+    "acosh_u35_f64": {"small": 81, "big": 61},
+    "atanh_u10_f64": {"all": 72},
+    "atanh_u35_f64": {"all": 72},
 }
 
 
@@ -73,7 +107,8 @@ def path_mix(name, x, y=None):
         import oracle
         yy = np.abs(np.asarray(y, dtype=np.float64))
         if fn == "remainder":
-            yy = np.where(yy <= 0x1.fffffffffffffp1022, 2 * yy, yy)
+            with np.errstate(over="ignore"):
+                yy = np.where(yy <= float.fromhex("0x1.fffffffffffffp+1022"), 2 * yy, yy)
         f = oracle.lib().oracle_fmod_iters
         m = min(ax.size, 1 << 16)          # step count from a prefix sample, scaled
         steps = sum(f(float(a), float(b)) for a, b in zip(ax[:m], yy[:m])) * (ax.size / max(m, 1))
@@ -81,6 +116,12 @@ def path_mix(name, x, y=None):
     if fn == "atan2":
         ay = np.abs(np.asarray(y, dtype=np.float64))
         return {"base": ax.size, "swap": int((ax > ay).sum()), "yneg": int((np.asarray(y) < 0).sum())}
+    if fn in ("sinh", "cosh"):
+        small = int((ax <= 22).sum())
+        return {"small": small, "big": ax.size - small}
+    if fn in ("asinh", "acosh"):
+        big = int((ax > 2.0 ** 500).sum())
+        return {"small": ax.size - big, "big": big}
     return {"all": int(ax.size)}
 
 
