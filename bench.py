@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP32 / bf16 / f16 family measurements")
     p.add_argument("--n32", type=int, default=1 << 28, help="elements per FP32 entry point")
+    p.add_argument("--n5", type=int, default=1 << 28, help="elements of the large-argument stress")
     return p.parse_args()
 
 
@@ -231,6 +232,70 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
                             "entry_points": f32},
             "bf16_f16_forms": {"shape": list(shape), "inputs": "N(0,3) rounded to the 16-bit format",
                                "entry_points": low}}
+
+
+def fmod_steps(sleefcu, torch, x, y, remainder, sp):
+    """Per-element long-division step counts of the fmod kernel (int64 numpy
+    array), from sleefcu_fmod_steps_f64 on the device operands; remainder
+    divides by 2|y| where that is finite."""
+    import numpy as np
+    yy = y.abs()
+    if remainder:
+        big = float.fromhex("0x1.fffffffffffffp+1022")
+        yy = torch.where(yy <= big, 2 * yy, yy)
+    o = torch.empty_like(x)
+    rc = sleefcu.raw("fmod_steps_f64")(x.data_ptr(), yy.data_ptr(), o.data_ptr(), x.numel(), sp)
+    if rc != 0:
+        raise RuntimeError(sleefcu.last_error())
+    torch.cuda.synchronize()
+    return o.cpu().numpy().astype(np.int64)
+
+
+def stress(sleefcu, torch, device, st, sp, n5, peak_fp64):
+    """Large-argument stress: 2^28 doubles with |x| log-uniform in
+    [1e5, DBL_MAX] through sin/cos/tan/sincos u10 (every lane on the
+    Payne-Hanek path) and fmod/remainder with the divisor log-uniform in
+    [1e-300, 1e300] (up to ~42 long-division steps).  Per entry point:
+    Gelem/s and the FP64-pipe roofline fraction; for fmod/remainder also
+    the histogram of long-division steps per element and per warp (the
+    kernel groups a tile's elements by step count, so a warp's time is
+    its largest count after that grouping)."""
+    from paper_2001_09258_gb300 import inputs as I
+    from paper_2001_09258_gb300 import opcounts
+    import numpy as np
+    out = {}
+    for fn in I.STRESS_FNS:
+        name = f"{fn}_u10_f64"
+        hx = I.stress(fn, n5)
+        hy = I.stress(fn, n5, operand=1) if fn in ("fmod", "remainder") else None
+        ins = [torch.from_numpy(hx).to(device)] + ([torch.from_numpy(hy).to(device)] if hy is not None else [])
+        outs = [torch.empty_like(ins[0]) for _ in range(2 if fn == "sincos" else 1)]
+        ms = time_calls(torch, st, lambda: launch(sleefcu, name, ins, outs, sp), reps=3)
+        it = None
+        if hy is not None:
+            it = fmod_steps(sleefcu, torch, ins[0], ins[1], fn == "remainder", sp)
+        ops = opcounts.ops_per_launch(name, hx, hy, None if it is None else int(it.sum()))
+        rec = {"gelem_s": round(n5 / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+               "ops_per_element": round(ops / n5, 2),
+               "fp64_frac": round(ops / (ms * 1e-3) / peak_fp64, 4)}
+        if it is not None:
+            # the kernel groups each 1024-element tile by the class
+            # ceil((ilogb x - ilogb y) / 52); a warp takes the largest count
+            # of its 32 grouped elements
+            ex = np.frexp(np.abs(hx))[1].astype(np.int64)
+            ey = np.frexp(np.abs(hy))[1].astype(np.int64)
+            cls = np.clip((ex - ey + 51) // 52, 0, 15)
+            m = (n5 // 1024) * 1024
+            order = np.argsort(cls[:m].reshape(-1, 1024), axis=1, kind="stable")
+            grouped = np.take_along_axis(it[:m].reshape(-1, 1024), order, axis=1)
+            warp = grouped.reshape(-1, 32).max(axis=1)
+            rec["steps_per_element"] = {int(k): int(v) for k, v in zip(*np.unique(it, return_counts=True))}
+            rec["steps_per_warp"] = {int(k): int(v) for k, v in zip(*np.unique(warp, return_counts=True))}
+        out[name] = rec
+        del ins, outs
+        torch.cuda.empty_cache()
+    return {"n": n5, "workload": "|x| log-uniform [1e5, DBL_MAX], random sign; divisor log-uniform "
+                                 "[1e-300, 1e300]", "entry_points": out}
 
 
 def batched(sleefcu, torch, device, st, sp, narrays=4096):
@@ -436,9 +501,16 @@ def main():
         ext = extras(sleefcu, torch, device, st, sp, per_fn, measured_peaks(), args.n32)
         torch.cuda.empty_cache()
         ext["batched"] = batched(sleefcu, torch, device, st, sp)
+        torch.cuda.empty_cache()
+        ext["stress"] = stress(sleefcu, torch, device, st, sp, args.n5, peak_fp64)
     dom = max(names, key=lambda nm: avg[nm])
     hx = host[dom.split("_")[0]]
-    ops = opcounts.ops_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None)
+    steps = None
+    if dom.split("_")[0] in ("fmod", "remainder"):
+        dx = [torch.from_numpy(a).to(device) for a in hx]
+        steps = int(fmod_steps(sleefcu, torch, dx[0], dx[1], dom.startswith("remainder"), sp).sum())
+        del dx
+    ops = opcounts.ops_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None, steps)
     achieved = ops / (avg[dom] * 1e-3)
     roof = {"kernel": dom, "bound": "alu", "pipe": "fp64",
             "achieved": round(achieved / 1e12, 5), "peak": round(peak_fp64 / 1e12, 5),

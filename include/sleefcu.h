@@ -296,6 +296,14 @@ void sleefcu_batch_destroy(sleefcu_batch *plan);
 sleefcu_status sleefcu_probe_dfma(double *out, int blocks, int iters, sleefcu_stream stream);
 sleefcu_status sleefcu_probe_ffma(float *out, int blocks, int iters, sleefcu_stream stream);
 
+/* Long-division step count of the remainder kernels (Section 5.9): out[i] =
+ * the number of steps the fmod kernel takes for |x[i]| mod |y[i]| (0 where
+ * x[i] is not finite or y[i] is 0 or not finite), as a double.  For
+ * remainder(x, y) pass 2|y|.  Used for the algorithmic operation count of
+ * the roofline; the same argument rules as the math entry points. */
+sleefcu_status sleefcu_fmod_steps_f64(const double *x, const double *y, double *out, size_t n,
+                                      sleefcu_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,8 +45,10 @@ __device__ __forceinline__ d2 step(d2 r, double D, double rD) {
   return norm_d2(add_d2d2(r, mul_dd(q, -D)));
 }
 
-// |x| mod |y| for finite n >= 0 and finite d > 0
-__device__ __forceinline__ double fmod_abs(double n, double d) {
+// |x| mod |y| for finite n >= 0 and finite d > 0; COUNT adds the number of
+// long-division steps taken to *steps (the diagnostics entry point)
+template <bool COUNT = false>
+__device__ __forceinline__ double fmod_abs(double n, double d, int *steps = nullptr) {
   uint64_t bd = bits(d);
   bool sub = bd < DMIN;
   int kmin = sub ? 54 : 0;
@@ -59,11 +61,15 @@ __device__ __forceinline__ double fmod_abs(double n, double d) {
     int j = ilogb_n(bits(r.x)) - edm - 1000;             // j - kmin
     if (j < 0) j = 0;
     r = step(r, j ? scale_n(dmin, j) : dmin, j ? scale_n(rd0, -j) : rd0);
+    if (COUNT) ++*steps;
   }
   double ret;
   if (sub) {
     r = D2(__dmul_rn(r.x, 0x1p54), __dmul_rn(r.y, 0x1p54));
-    for (int k = 0; k < 4 && (int64_t)bits(r.x) >= (int64_t)bdmin; k++) r = step(r, dmin, rd0);
+    for (int k = 0; k < 4 && (int64_t)bits(r.x) >= (int64_t)bdmin; k++) {
+      r = step(r, dmin, rd0);
+      if (COUNT) ++*steps;
+    }
     ret = __dmul_rn(r.x, 0x1p-54);
     if (__dadd_rn(r.x, r.y) == dmin) ret = 0.0;
   } else {
@@ -116,6 +122,18 @@ struct RemainderF {
   }
 };
 
+// number of long-division steps of |x| mod |y| (0 where fmod is not a
+// division: non-finite x, zero or non-finite y)
+struct FmodSteps {
+  __device__ double operator()(double x, double y) const {
+    uint64_t an = bits(x) & ABS64, ad = bits(y) & ABS64;
+    bool ok = an < INF && ad != 0 && ad < INF;
+    int steps = 0;
+    fmod_abs<true>(ok ? from_bits(an) : 0.0, ok ? from_bits(ad) : 1.0, &steps);
+    return (double)steps;
+  }
+};
+
 }  // namespace fmod64
 }  // namespace sleefcu
 
@@ -132,4 +150,9 @@ BIN64(fmod_u35_f64, FmodF)
 BIN64(remainder_u10_f64, RemainderF)
 BIN64(remainder_u35_f64, RemainderF)
 #undef BIN64
+
+extern "C" sleefcu_status sleefcu_fmod_steps_f64(const double *x, const double *y, double *out, size_t n,
+                                                 sleefcu_stream s) {
+  return launch_binary64<fmod64::FmodSteps>("sleefcu_fmod_steps_f64", x, y, out, n, s);
+}
 #endif  // SLEEFCU_FUNCTORS_ONLY

@@ -171,6 +171,19 @@ def workload(fn, n, key="c2", dtype=np.float64, operand=0):
     return x
 
 
+STRESS_FNS = ("sin", "cos", "tan", "sincos", "fmod", "remainder")
+
+
+def stress(fn, n, key="c5", operand=0):
+    """The large-argument stress workload: |x| log-uniform over [1e5, DBL_MAX]
+    with a random sign (every trig lane takes the Payne-Hanek path); the
+    divisor of fmod/remainder log-uniform over [1e-300, 1e300], random sign."""
+    k = f"{key}/{fn}/{operand}"
+    if operand == 0:
+        return loguniform(k, n, 1e5, 1.7976931348623157e308)
+    return loguniform(k, n, 1e-300, 1e300)
+
+
 def to_bf16_bits(x32):
     """binary32 -> bf16 bit patterns, round-to-nearest-even (input preparation)."""
     b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)

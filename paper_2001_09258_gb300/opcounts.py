@@ -42,7 +42,7 @@ OPS = {
     "atan2_u35_f64": {"base": 26, "swap": 1, "yneg": 1},
     # fmod / remainder: 4 setup ops (division, nextafter-free scaling) plus
     # 17 per step of the long division (trunc product 2, 3D and 2D 2, exact
-    # q*D 2, DD add 8, renormalization 3), steps counted by the oracle
+    # q*D 2, DD add 8, renormalization 3), steps counted by the kernel's loop
     "fmod_u10_f64": {"setup": 4, "step": 17},
     "fmod_u35_f64": {"setup": 4, "step": 17},
     "remainder_u10_f64": {"setup": 9, "step": 17},
@@ -84,8 +84,10 @@ OPS = {
 }
 
 
-def path_mix(name, x, y=None):
-    """Number of elements of x on each path of entry point `name`."""
+def path_mix(name, x, y=None, steps=None):
+    """Number of elements of x on each path of entry point `name` (for
+    fmod/remainder: `steps` = total long-division steps of the launch, as
+    counted by the kernel's own loop)."""
     x = np.asarray(x, dtype=np.float64)
     ax = np.abs(x)
     fn = name.split("_")[0]
@@ -104,14 +106,8 @@ def path_mix(name, x, y=None):
         big = int((~(ax < 1)).sum())
         return {"small": ax.size - big, "big": big}
     if fn in ("fmod", "remainder"):
-        import oracle
-        yy = np.abs(np.asarray(y, dtype=np.float64))
-        if fn == "remainder":
-            with np.errstate(over="ignore"):
-                yy = np.where(yy <= float.fromhex("0x1.fffffffffffffp+1022"), 2 * yy, yy)
-        f = oracle.lib().oracle_fmod_iters
-        m = min(ax.size, 1 << 16)          # step count from a prefix sample, scaled
-        steps = sum(f(float(a), float(b)) for a, b in zip(ax[:m], yy[:m])) * (ax.size / max(m, 1))
+        if steps is None:
+            raise ValueError(f"{name}: pass the total long-division step count (sleefcu_fmod_steps_f64)")
         return {"setup": ax.size, "step": int(steps)}
     if fn == "atan2":
         ay = np.abs(np.asarray(y, dtype=np.float64))
@@ -125,6 +121,6 @@ def path_mix(name, x, y=None):
     return {"all": int(ax.size)}
 
 
-def ops_per_launch(name, x, y=None):
+def ops_per_launch(name, x, y=None, steps=None):
     tbl = OPS[name]
-    return float(sum(tbl[k] * v for k, v in path_mix(name, x, y).items()))
+    return float(sum(tbl[k] * v for k, v in path_mix(name, x, y, steps).items()))
