@@ -6,6 +6,13 @@ Run:  python oracle/coeffs/fit_derived64.py [name ...]
 
   expm1_u35  e^r - 1 = r + r^2 u(r) with the error weighted relative to
          e^r - 1 (not e^r as for exp), |r| <= ln2/2, 12 terms
+  erf_a  erf(x)/x = C0 + t (C1 + t P(t)), t = x^2 in [0, 1], C0 and C1 as DD
+         pairs, error relative to erf(x)/x
+  erfc_F<i>  F(x) = erfc(x) e^(x^2) on [1,2), [2,4), [4,8) as
+         c0 + u (c1 + u P(u)), u = x - (interval midpoint), 24 terms, c0 and c1
+         as DD pairs, relative error
+  erfc_G G(w) = sqrt(pi) x erfc(x) e^(x^2), w = 1/x^2 in [0, 1/64] (x >= 8),
+         where the asymptotic series converges fast enough; 16 terms
   cbrt   start value of the inverse cube root, m^(-1/3) on [1, 2] to about
          2^-26 relative, refined by Newton steps that need no division
 """
@@ -48,7 +55,42 @@ def expm1_w(r):
     return r * r / abs(mp.expm1(r))
 
 
+ERFC_IV = [(1, 2), (2, 4), (4, 8)]
+
+
+def erf_over_x(t):
+    if t < mp.mpf("1e-30"):
+        return 2 / mp.sqrt(mp.pi) * (1 - t / 3)
+    x = mp.sqrt(t)
+    return mp.erf(x) / x
+
+
+def F(x):
+    return mp.erfc(x) * mp.exp(x * x)
+
+
+def G(w):
+    if w < mp.mpf("1e-12"):
+        return 1 - w / 2 + 3 * w * w / 4
+    x = 1 / mp.sqrt(w)
+    return mp.sqrt(mp.pi) * x * F(x)
+
+
+def erfc_job(i, n):
+    a, b = ERFC_IV[i]
+    m = (mp.mpf(a) + mp.mpf(b)) / 2
+    return lambda: fit_rounded(lambda u: F(m + u), lambda u: 1 / F(m + u), range(n), ["dd", "dd"] + ["d"] * (n - 2),
+                               mp.mpf(a) - m, mp.mpf(b) - m, n_grid=3000)
+
+
 JOBS = {
+    "erf_a": lambda: fit_rounded(erf_over_x, lambda t: 1 / erf_over_x(t), range(18), ["dd", "dd"] + ["d"] * 16,
+                                 0, 1, n_grid=3000),
+    "erfc_F0": erfc_job(0, 24),
+    "erfc_F1": erfc_job(1, 24),
+    "erfc_F2": erfc_job(2, 24),
+    "erfc_G": lambda: fit_rounded(G, lambda w: 1 / G(w), range(16), ["dd", "dd"] + ["d"] * 14, 0,
+                                  mp.mpf(1) / 64, n_grid=3000),
     "expm1_u35": lambda: fit_rounded(exp_u, expm1_w, range(10), ["d"] * 10, -LN2H, LN2H, n_grid=4000),
     "cbrt": lambda: fit_rounded(lambda t: icbrt(t + mp.mpf(1.5)), lambda t: icbrt_w(t + mp.mpf(1.5)),
                                 range(8), ["d"] * 8, -mp.mpf(0.5), mp.mpf(0.5)),

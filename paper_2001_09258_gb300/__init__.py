@@ -73,6 +73,8 @@ def lib():
         for probe in ("sleefcu_probe_dfma", "sleefcu_probe_ffma"):
             getattr(L, probe).restype = ctypes.c_int
             getattr(L, probe).argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        L.sleefcu_fmod_steps_f64.restype = ctypes.c_int
+        L.sleefcu_fmod_steps_f64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]
         for name in entry_points():
             fn = name.split("_")[0]
             f = getattr(L, "sleefcu_" + name)
@@ -88,8 +90,13 @@ def last_error():
 
 
 def raw(name):
-    """The ctypes function of entry point sleefcu_<name>."""
-    return getattr(lib(), "sleefcu_" + name)
+    """The ctypes function of entry point sleefcu_<name>.  Every function
+    handed out has its argument types declared: an undeclared ctypes call
+    would pass 64-bit device pointers as C ints."""
+    f = getattr(lib(), "sleefcu_" + name)
+    if f.argtypes is None:
+        raise SleefcuError(f"sleefcu_{name}: no declared signature in the binding")
+    return f
 
 
 def _check(rc, name):

@@ -39,10 +39,8 @@ constexpr uint64_t SIGN = 0x8000000000000000ull;
 constexpr uint64_t B1100 = 0x4091300000000000ull;   // 1100.0
 constexpr uint64_t B350 = 0x4075E00000000000ull;    // 350.0
 constexpr uint64_t B711 = 0x4086380000000000ull;    // 711.0
-constexpr uint64_t B22 = 0x4036000000000000ull;     // 22.0
 constexpr uint64_t B20 = 0x4034000000000000ull;     // 20.0
 constexpr uint64_t BM28 = 0x3E30000000000000ull;    // 2^-28
-constexpr uint64_t B500 = 0x5F30000000000000ull;    // 2^500
 constexpr uint64_t ONE = 0x3FF0000000000000ull;
 
 static __constant__ double kExpm1U35[10] = {
