@@ -287,6 +287,27 @@ sleefcu_status sleefcu_batch_get_config(const sleefcu_batch *plan, int *block, i
                                         int *vec);
 void sleefcu_batch_destroy(sleefcu_batch *plan);
 
+/* Batched launch without allocation (this library's addition; the paper has
+ * no counterpart).  The same evaluation as a plan's sleefcu_batch_launch,
+ * bit for bit, for callers that may not allocate device memory when they
+ * launch: the descriptors, tile prefix sums and tile counter live in one
+ * fixed device array of about 230 KB inside the library instead of
+ * cudaMalloc'd plan buffers.  items: host array of count descriptors (the
+ * same rules as sleefcu_batch_create; items with n == 0 are skipped).
+ * count > 4096 returns SLEEFCU_EINVAL with a message; an unsupported
+ * combination SLEEFCU_EUNSUPPORTED.  The call enqueues two host-to-device
+ * copies of the descriptors (from library-owned host memory), a memset that
+ * zeroes the tile counter, and the kernel, in that order on `stream`; the
+ * configuration is the default one (block 256, tile 4096).  The first call
+ * on each device looks up the array's address with that device current, so
+ * make it before any stream capture that should contain later calls.  One
+ * array serves all callers on a device: calls whose work can overlap (other
+ * streams, other host threads) race on it and corrupt each other's
+ * descriptors; serialize them on one stream or synchronize in between.
+ * Nothing is allocated, by this call or the first one. */
+sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size_t count,
+                                           sleefcu_stream stream);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

@@ -178,10 +178,31 @@ def _batch_lib():
         L.sleefcu_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
         L.sleefcu_batch_set_config.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
         L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.sleefcu_batch_launch_static.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_void_p]
         L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
         L.sleefcu_batch_destroy.restype = None
         L._batch_ready = True
     return L
+
+
+def _items_array(items):
+    arr = (BatchItem * max(len(items), 1))()
+    for i, (name, x, y, out, out2) in enumerate(items):
+        fn, acc, prec = name.split("_")
+        arr[i] = BatchItem(FN_IDS[fn], DTYPE_IDS[prec], int(acc[1:]), 0,
+                           x.data_ptr(), y.data_ptr() if y is not None else None,
+                           out.data_ptr(), out2.data_ptr() if out2 is not None else None, x.numel())
+    return arr
+
+
+def batch_launch_static(items, stream=None):
+    """sleefcu_batch_launch_static on (entry point name, x, y, out, out2)
+    items: the batched evaluation without any device allocation."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    arr = _items_array(items)
+    _check(_batch_lib().sleefcu_batch_launch_static(arr, len(items), ctypes.c_void_p(st.cuda_stream)),
+           "batch_launch_static")
 
 
 class Batch:

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 namespace sleefcu {
@@ -467,4 +468,100 @@ extern "C" sleefcu_status sleefcu_batch_autotune(sleefcu_batch *p, const char *c
     }
   }
   return rc;
+}
+
+// ---------------- batched launch without allocation ----------------
+// sleefcu_batch_create allocates device buffers for a plan.  Some callers
+// cannot do that at the point where they launch: an embedding whose own
+// caching allocator owns all of the device memory (a stray cudaMalloc
+// fragments it or fails outright), or a latency-critical path where an
+// allocation, and the device-wide synchronization that cudaFree implies,
+// is not acceptable.  For them this entry point keeps the descriptors, the
+// tile prefix sums and the tile counter in one fixed device array of file
+// scope, sized for at most kStaticItems arrays (about 230 KB), and runs the
+// same k_batch kernel with the default configuration.
+namespace {
+constexpr size_t kStaticItems = 4096;
+constexpr size_t kStaticDescBytes = kStaticItems * sizeof(sleefcu::batch::Desc);
+constexpr size_t kStaticPreBytes = (kStaticItems + 1) * sizeof(long long);
+constexpr size_t kStaticBytes = kStaticDescBytes + kStaticPreBytes + sizeof(unsigned long long);
+constexpr int kStaticMaxDevices = 64;
+constexpr int kStaticBlock = 256, kStaticTile = 4096, kStaticGridMult = 2, kStaticVec = 2;
+
+std::mutex g_static_mu;                                   // guards the host staging and the table
+void *g_static_dev[kStaticMaxDevices];                     // scratch address per device
+sleefcu::batch::Desc g_static_hdesc[kStaticItems];         // host staging, reused by every call
+long long g_static_hpre[kStaticItems + 1];
+}  // namespace
+
+// layout: Desc[kStaticItems], long long pre[kStaticItems + 1], tile counter
+static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
+
+extern "C" sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size_t count,
+                                                      sleefcu_stream s) {
+  if (count > kStaticItems) {
+    set_error("sleefcu_batch_launch_static: %zu items exceed the fixed scratch limit of %zu", count,
+              kStaticItems);
+    return SLEEFCU_EINVAL;
+  }
+  if (count && !items) { set_error("sleefcu_batch_launch_static: null item array"); return SLEEFCU_EINVAL; }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { set_error("sleefcu_batch_launch_static: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  if (dev < 0 || dev >= kStaticMaxDevices) {
+    set_error("sleefcu_batch_launch_static: device %d beyond the %d supported", dev, kStaticMaxDevices);
+    return SLEEFCU_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_dev[dev]) {                               // first call on this device (device current)
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_batch_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("sleefcu_batch_launch_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return SLEEFCU_ECUDA;
+    }
+    g_static_dev[dev] = p;
+  }
+  size_t nd = 0;
+  g_static_hpre[0] = 0;
+  for (size_t i = 0; i < count; i++) {
+    const sleefcu_batch_item &it = items[i];
+    int c = code_of(it);
+    if (c < 0) {
+      set_error("sleefcu_batch_launch_static: item %zu: unsupported (fn %u, dtype %u, ulp %u)", i, it.fn,
+                it.dtype, it.ulp);
+      return SLEEFCU_EUNSUPPORTED;
+    }
+    if (it.n == 0) continue;
+    if (!it.x || !it.out || (needs_y(c) && !it.y) || (needs_out2(c) && !it.out2)) {
+      set_error("sleefcu_batch_launch_static: item %zu: null pointer with n = %zu", i, it.n);
+      return SLEEFCU_EINVAL;
+    }
+    g_static_hdesc[nd] = Desc{it.x, it.y, it.out, it.out2, (long long)it.n, c, 0};
+    g_static_hpre[nd + 1] = g_static_hpre[nd] + (long long)((it.n + kStaticTile - 1) / kStaticTile);
+    nd++;
+  }
+  long long ntiles = g_static_hpre[nd];
+  if (ntiles == 0) return SLEEFCU_OK;
+  unsigned char *base = (unsigned char *)g_static_dev[dev];
+  Desc *d_desc = (Desc *)base;
+  long long *d_pre = (long long *)(base + kStaticDescBytes);
+  unsigned long long *d_ctr = (unsigned long long *)(base + kStaticDescBytes + kStaticPreBytes);
+  cudaStream_t st = (cudaStream_t)s;
+  // pageable sources: each copy returns once the bytes are staged, so the
+  // host arrays may be refilled by the next call
+  e = cudaMemcpyAsync(d_desc, g_static_hdesc, nd * sizeof(Desc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_pre, g_static_hpre, (nd + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);   // counter starts at 0
+  if (e != cudaSuccess) { set_error("sleefcu_batch_launch_static: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_batch, kStaticBlock, 0);
+  if (per < 1) per = 1;
+  long long g = (long long)sms * per * kStaticGridMult;
+  if (g > ntiles) g = ntiles;
+  if (g < 1) g = 1;
+  k_batch<<<(int)g, kStaticBlock, 0, st>>>(d_desc, d_pre, (int)nd, ntiles, kStaticTile, kStaticVec, d_ctr);
+  return check_launch("sleefcu_batch_launch_static");
 }
