@@ -284,7 +284,7 @@ def stress(sleefcu, torch, device, st, sp, n5, peak_fp64):
             # of its 32 grouped elements
             ex = np.frexp(np.abs(hx))[1].astype(np.int64)
             ey = np.frexp(np.abs(hy))[1].astype(np.int64)
-            cls = np.clip((ex - ey + 51) // 52, 0, 15)
+            cls = np.clip((ex - ey + 51) // 52, 0, 47)
             m = (n5 // 1024) * 1024
             order = np.argsort(cls[:m].reshape(-1, 1024), axis=1, kind="stable")
             grouped = np.take_along_axis(it[:m].reshape(-1, 1024), order, axis=1)

@@ -272,7 +272,14 @@ struct CbrtU10 { __device__ double operator()(double x) const { return cbrt_core
 struct CbrtU35 { __device__ double operator()(double x) const { return cbrt_core<false>(x); } };
 
 // ---------------- sinh, cosh, tanh ----------------
+// sinh/cosh lanes split at |x| = 22 (DD formula or e^|x|/2), asinh/acosh at
+// 2^500 (square root or not): the sorted-tile kernel keeps each warp on one
+__device__ __forceinline__ int cls_22(double x) { return (bits(x) & ABS64) > 0x4036000000000000ull; }
+__device__ __forceinline__ int cls_500(double x) { return (bits(x) & ABS64) > 0x5F30000000000000ull; }
+
 struct SinhU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_22(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= B711 ? from_bits(ab) : 0.0;
@@ -294,6 +301,8 @@ struct SinhU10 {
   }
 };
 struct CoshU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_22(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= B711 ? from_bits(ab) : 0.0;
@@ -327,6 +336,8 @@ struct TanhU10 {
   }
 };
 struct SinhU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_22(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= B711 ? from_bits(ab) : 0.0;
@@ -346,6 +357,8 @@ struct SinhU35 {
   }
 };
 struct CoshU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_22(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= B711 ? from_bits(ab) : 0.0;
@@ -379,6 +392,8 @@ struct TanhU35 {
 
 // ---------------- asinh, acosh, atanh ----------------
 struct AsinhU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_500(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= DMAX ? from_bits(ab) : 1.0;
@@ -399,6 +414,8 @@ struct AsinhU10 {
   }
 };
 struct AcoshU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_500(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     bool inr = x >= 1.0 && bx <= DMAX;
@@ -443,6 +460,11 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_unary64<derived64::F>("sleefcu_" #NAME, x, out, n, s);                    \
   }
+#define SORTED64(NAME, F)                                                                   \
+  extern "C" sleefcu_status sleefcu_##NAME(const double *x, double *out, size_t n,          \
+                                           sleefcu_stream s) {                              \
+    return launch_sorted64<derived64::F>("sleefcu_" #NAME, x, out, n, s);                   \
+  }
 UNARY64(exp2_u10_f64, Exp2U10)
 UNARY64(exp2_u35_f64, Exp2U35)
 UNARY64(exp10_u10_f64, Exp10U10)
@@ -457,17 +479,18 @@ UNARY64(log1p_u10_f64, Log1pU10)
 UNARY64(log1p_u35_f64, Log1pU35)
 UNARY64(cbrt_u10_f64, CbrtU10)
 UNARY64(cbrt_u35_f64, CbrtU35)
-UNARY64(sinh_u10_f64, SinhU10)
-UNARY64(sinh_u35_f64, SinhU35)
-UNARY64(cosh_u10_f64, CoshU10)
-UNARY64(cosh_u35_f64, CoshU35)
+SORTED64(sinh_u10_f64, SinhU10)
+SORTED64(sinh_u35_f64, SinhU35)
+SORTED64(cosh_u10_f64, CoshU10)
+SORTED64(cosh_u35_f64, CoshU35)
 UNARY64(tanh_u10_f64, TanhU10)
 UNARY64(tanh_u35_f64, TanhU35)
-UNARY64(asinh_u10_f64, AsinhU10)
-UNARY64(asinh_u35_f64, AsinhU10)
-UNARY64(acosh_u10_f64, AcoshU10)
-UNARY64(acosh_u35_f64, AcoshU10)
+SORTED64(asinh_u10_f64, AsinhU10)
+SORTED64(asinh_u35_f64, AsinhU10)
+SORTED64(acosh_u10_f64, AcoshU10)
+SORTED64(acosh_u35_f64, AcoshU10)
 UNARY64(atanh_u10_f64, AtanhU10)
 UNARY64(atanh_u35_f64, AtanhU10)
 #undef UNARY64
+#undef SORTED64
 #endif  // SLEEFCU_FUNCTORS_ONLY

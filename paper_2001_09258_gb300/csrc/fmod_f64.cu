@@ -10,7 +10,7 @@
 // 1000), which is the listing itself whenever n/d < 2^1000; a subnormal d
 // (kmin = 54) is rescaled by 2^54 once r < d 2^54, as in the listing.
 // Elements are grouped in divergence-sorted tiles by their expected trip
-// count ceil((ilogb n - ilogb d) / 52), so the lanes of a warp leave the loop
+// count ceil((ilogb n - ilogb d) / 52) (48 classes), so the lanes of a warp leave the loop
 // together (the listing's "terminate once every element of the vector is
 // done").  Comparisons of the non-negative operands run on the integer pipe.
 //
@@ -79,15 +79,17 @@ __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = null
   return ret;
 }
 
-// expected trip-count class of |x| mod |y| (for the tile sort)
+// expected trip-count class of |x| mod |y| (for the tile sort): one class
+// per step count up to the 44-step maximum
+constexpr int kTripClasses = 48;
 __device__ __forceinline__ int trip_class(double x, double y) {
   int en = ilogb_n(bits(x) & ABS64), ed = ilogb_n(bits(y) & ABS64);
   int t = (en - ed + 51) / 52;
-  return t < 0 ? 0 : (t > 15 ? 15 : t);
+  return t < 0 ? 0 : (t > kTripClasses - 1 ? kTripClasses - 1 : t);
 }
 
 struct FmodF {
-  static constexpr int NCLS = 16;
+  static constexpr int NCLS = kTripClasses;
   __device__ static int cls(double x, double y) { return trip_class(x, y); }
   __device__ double operator()(double x, double y) const {
     uint64_t bx = bits(x), by = bits(y);
@@ -102,7 +104,7 @@ struct FmodF {
 };
 
 struct RemainderF {
-  static constexpr int NCLS = 16;
+  static constexpr int NCLS = kTripClasses;
   __device__ static int cls(double x, double y) { return trip_class(x, y); }
   __device__ double operator()(double x, double y) const {
     uint64_t bx = bits(x), by = bits(y);

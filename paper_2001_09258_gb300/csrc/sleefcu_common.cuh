@@ -179,14 +179,25 @@ __device__ __forceinline__ void sort_scatter(const int (&cl)[kSortEPT], int *cnt
   const unsigned lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
   for (int j = 0; j < kSortEPT; j++) {
+    if constexpr (NC > 4) {
+      // many classes: the lanes of one class find each other with a match
+      // instead of one ballot per class
+      unsigned m = __match_any_sync(0xffffffffu, cl[j]);
+      int leader = __ffs(m) - 1;
+      int b = 0;
+      if ((int)lane == leader && cl[j] >= 0) b = atomicAdd(&cur[cl[j]], __popc(m));
+      b = __shfl_sync(0xffffffffu, b, leader);
+      if (cl[j] >= 0) sidx[b + __popc(m & lt)] = (unsigned short)(j * kBlock + tid);
+    } else {
 #pragma unroll
-    for (int c = 0; c < NC; c++) {
-      unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
-      if (m) {
-        int b = 0;
-        if (lane == 0) b = atomicAdd(&cur[c], __popc(m));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (cl[j] == c) sidx[b + __popc(m & lt)] = (unsigned short)(j * kBlock + tid);
+      for (int c = 0; c < NC; c++) {
+        unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
+        if (m) {
+          int b = 0;
+          if (lane == 0) b = atomicAdd(&cur[c], __popc(m));
+          b = __shfl_sync(0xffffffffu, b, 0);
+          if (cl[j] == c) sidx[b + __popc(m & lt)] = (unsigned short)(j * kBlock + tid);
+        }
       }
     }
   }
@@ -197,10 +208,15 @@ template <int NC>
 __device__ __forceinline__ void sort_count(const int (&cl)[kSortEPT], int *cnt, int tid) {
   const unsigned lane = tid & 31;
   for (int j = 0; j < kSortEPT; j++) {
+    if constexpr (NC > 4) {
+      unsigned m = __match_any_sync(0xffffffffu, cl[j]);
+      if ((int)lane == __ffs(m) - 1 && cl[j] >= 0) atomicAdd(&cnt[cl[j]], __popc(m));
+    } else {
 #pragma unroll
-    for (int c = 0; c < NC; c++) {
-      unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
-      if (lane == 0 && m) atomicAdd(&cnt[c], __popc(m));
+      for (int c = 0; c < NC; c++) {
+        unsigned m = __ballot_sync(0xffffffffu, cl[j] == c);
+        if (lane == 0 && m) atomicAdd(&cnt[c], __popc(m));
+      }
     }
   }
 }
