@@ -405,3 +405,133 @@ double oracle_atanh_u10_f64(double x) {
 double oracle_asinh_u35_f64(double x) { return oracle_asinh_u10_f64(x); }
 double oracle_acosh_u35_f64(double x) { return oracle_acosh_u10_f64(x); }
 double oracle_atanh_u35_f64(double x) { return oracle_atanh_u10_f64(x); }
+
+/* ---------------- erf, erfc ----------------
+ * erf   |x| < 1: x (C0 + t (C1 + t (c2 + t P(t)))), t = x^2 exact as a DD and
+ *       the three leading levels in DD; 1 <= |x| < 6: 1 - erfc(|x|) in DD; +-1 beyond.
+ * erfc  |x| < 1: 1 -+ erf(|x|) in DD; 1 <= |x| <= 27.5: F(|x|) e^(-x^2) with
+ *       F = erfc(x) e^(x^2) a polynomial about the midpoint of [1,2), [2,4)
+ *       or [4,8) (leading two terms in DD) or, from 8 on, G(1/x^2) / (sqrt(pi) x)
+ *       with G the asymptotic factor; e^(-x^2) from the DD exp core on the
+ *       exact DD x^2 and scaled by 2^k in two steps (subnormal results rounded
+ *       once); erfc(-x) = 2 - erfc(x).
+ * The u35 erf evaluates the same pieces in double (e^(-x^2) from the
+ * residual-carrying reduction and the 12-term e^r - 1 polynomial); the u35
+ * erfc runs the u10 algorithm (1 - erf near 1 and the DD argument of the
+ * exponential are needed for any bound). */
+#define RSQPIH 0x1.20dd750429b6dp-1     /* 1/sqrt(pi) as a DD */
+#define RSQPIL 0x1.1ae3a914f6e1fp-57
+
+static const double ERF_H[4] = { ERF_A_HEAD };
+static const double ERF_P[11] = { ERF_A_COEFFS };
+static const double ERFC_FH[3][4] = { { ERFC_F0_HEAD }, { ERFC_F1_HEAD }, { ERFC_F2_HEAD } };
+static const double ERFC_FP[3][22] = { { ERFC_F0_COEFFS }, { ERFC_F1_COEFFS }, { ERFC_F2_COEFFS } };
+static const double ERFC_GH[4] = { ERFC_G_HEAD };
+static const double ERFC_GP[9] = { ERFC_G_COEFFS };
+static const double ERFC_MID[3] = { 1.5, 3.0, 6.0 };
+
+/* erf(a)/a as a DD, 0 <= a < 1: C0 + T (C1 + T (c2 + t P(t))) with T = a^2
+ * exact and the three outer levels in DD (1 - erf near a = 1 magnifies the
+ * error of erf five-fold) */
+static dd_t erf_s(double a) {
+  dd_t T = ddmul_d2_d_d(a, a);
+  double p = poly_d(T.x, ERF_P + 1, 10);
+  dd_t in = ddadd2_d2_d_d(ERF_P[0], T.x * p);
+  in = ddadd2_d2_d2_d2(dd(ERF_H[2], ERF_H[3]), ddmul_d2_d2_d2(T, in));
+  return ddadd2_d2_d2_d2(dd(ERF_H[0], ERF_H[1]), ddmul_d2_d2_d2(T, in));
+}
+
+static int erfc_iv(double a) { return a < 2 ? 0 : (a < 4 ? 1 : 2); }
+
+/* F(a) = erfc(a) e^(a^2) as a DD, 1 <= a <= 27.5 */
+static dd_t erfc_F(double a) {
+  if (a < 8) {
+    int i = erfc_iv(a);
+    double u = a - ERFC_MID[i];
+    double p = poly_d(u, ERFC_FP[i], 22);
+    dd_t in = ddadd2_d2_d2_d(dd(ERFC_FH[i][2], ERFC_FH[i][3]), u * p);
+    return ddadd2_d2_d2_d2(dd(ERFC_FH[i][0], ERFC_FH[i][1]), ddmul_d2_d2_d(in, u));
+  }
+  double w = 1.0 / (a * a);
+  double p = poly_d(w, ERFC_GP, 9);
+  dd_t in = ddadd2_d2_d2_d(dd(ERFC_GH[2], ERFC_GH[3]), w * p);
+  dd_t g = ddadd2_d2_d2_d2(dd(ERFC_GH[0], ERFC_GH[1]), ddmul_d2_d2_d(in, w));
+  return dddiv_d2_d2_d2(ddmul_d2_d2_d2(g, dd(RSQPIH, RSQPIL)), dd(a, 0.0));
+}
+
+/* erfc(a) = c 2^k with c = F(a) e^(-a^2 - k ln2) as a DD, 1 <= a <= 27.5 */
+static dd_t erfc_core(double a, double *k) {
+  dd_t Y = ddmul_d2_d_d(a, a);
+  dd_t s = oracle_expk_s(dd(-Y.x, -Y.y), k);
+  return ddmul_d2_d2_d2(erfc_F(a), ddadd_d2_d_d2(1.0, s));
+}
+
+double oracle_erf_u10_f64(double x) {
+  double a = fabs(x);
+  double y;
+  if (a < 1) {
+    dd_t e = ddmul_d2_d2_d(erf_s(a), a);
+    y = e.x + e.y;
+  } else if (a < 6) {
+    double k;
+    dd_t c = erfc_core(a, &k);
+    c = ddscale_d2_d2_d(c, ldexp(1.0, (int)k));
+    dd_t r = ddadd2_d2_d_d2(1.0, dd(-c.x, -c.y));
+    y = r.x + r.y;
+  } else {
+    y = 1.0;
+  }
+  if (isnan(x)) y = NAN;
+  return canon(copysign(y, x));
+}
+
+double oracle_erfc_u10_f64(double x) {
+  double a = fabs(x);
+  double y;
+  if (a < 1) {
+    dd_t e = ddmul_d2_d2_d(erf_s(a), a);
+    if (x > 0) e = dd(-e.x, -e.y);
+    dd_t r = ddadd2_d2_d_d2(1.0, e);
+    y = r.x + r.y;
+  } else if (a <= 27.5) {
+    double k;
+    dd_t c = erfc_core(a, &k);
+    if (x > 0) {
+      y = oracle_scale2(c.x + c.y, (int)k);
+    } else if (a < 8) {
+      c = ddscale_d2_d2_d(c, ldexp(1.0, (int)k));
+      dd_t r = ddadd2_d2_d_d2(2.0, dd(-c.x, -c.y));
+      y = r.x + r.y;
+    } else {
+      y = 2.0;
+    }
+  } else {
+    y = x > 0 ? 0.0 : 2.0;
+  }
+  if (isnan(x)) y = NAN;
+  return canon(y);
+}
+
+double oracle_erf_u35_f64(double x) {
+  double a = fabs(x);
+  double y;
+  if (a < 1) {
+    double t = a * a;
+    y = a * fma(t, fma(t, poly_d(t, ERF_P, 11), ERF_H[2]), ERF_H[0]);
+  } else if (a < 6) {
+    int i = erfc_iv(a);
+    double u = a - ERFC_MID[i];
+    double F = fma(u, fma(u, poly_d(u, ERFC_FP[i], 22), ERFC_FH[i][2]), ERFC_FH[i][0]);
+    dd_t Y = ddmul_d2_d_d(a, a);
+    double k = rint(-Y.x * R_LN2);
+    double r = fma(k, -L2B, fma(k, -L2A, -Y.x)) - Y.y;
+    double E = (1.0 + em1_r_u35(r)) * ldexp(1.0, (int)k);
+    y = fma(-F, E, 1.0);
+  } else {
+    y = 1.0;
+  }
+  if (isnan(x)) y = NAN;
+  return canon(copysign(y, x));
+}
+
+double oracle_erfc_u35_f64(double x) { return oracle_erfc_u10_f64(x); }

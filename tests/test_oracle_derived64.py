@@ -123,3 +123,45 @@ def test_composite_identities():
     x = U("z3", 50000, -1, 1)
     c, s = oracle.apply("cosh_u10_f64", x), oracle.apply("sinh_u10_f64", x)
     assert np.max(np.abs((c - s) * (c + s) - 1)) < 2.0 ** -50
+
+
+ERF_SETS = {
+    "erf": lambda: [U("e1", N, -6, 6), U("e2", N, -1, 1), L("e3", N, 1e-300, 1e-3), U("e4", N, 0.9, 1.1),
+                    U("e5", N, 1.9, 2.1), U("e6", N, 3.9, 4.1), U("e7", N, 5.5, 6.5), L("e8", N, 5e-324, 1e-300)],
+    "erfc": lambda: [U("f1", N, -6, 27.3), U("f2", N, -1, 1), L("f3", N, 1e-300, 1e-3), U("f4", N, 0.9, 1.1),
+                     U("f5", N, 1.9, 2.1), U("f6", N, 3.9, 4.1), U("f7", N, 7.9, 8.1), U("f8", N, 26, 27.5),
+                     U("f9", N, -27, -0.9)],
+}
+
+
+@needs_quad
+@pytest.mark.parametrize("fn", list(ERF_SETS))
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_erf_ulp_bound(fn, acc):
+    x = np.concatenate(ERF_SETS[fn]() + [I.SPECIALS_F64])
+    y = oracle.apply(f"{fn}_{acc}_f64", x)
+    err = quadref.ulp_err(fn, x, y)
+    i = int(np.argmax(err))
+    assert err.max() <= BOUND[acc], (fn, acc, x[i], y[i], err.max())
+
+
+@pytest.mark.parametrize("fn", ["erf", "erfc"])
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_erf_special_values(fn, acc):
+    f = getattr(_libm, fn)
+    f.restype, f.argtypes = ctypes.c_double, [ctypes.c_double]
+    x = np.array(EDGE + [6.0, -6.0, 27.2, 27.3, 27.5, 28.0, -28.0, 8.0, -8.0, 4.0, 1.0, -1.0])
+    y = oracle.apply(f"{fn}_{acc}_f64", x)
+    for xi, yi in zip(x, y):
+        want = f(float(xi))
+        if math.isnan(want) or math.isinf(xi) or want == 0 or abs(want) in (1.0, 2.0) or xi == 0:
+            assert _same(yi, want), (fn, acc, xi, yi, want)
+
+
+def test_erf_identities():
+    x = np.concatenate([U("g1", 50000, -6, 6), L("g2", 20000, 1e-300, 1)])
+    e, c = oracle.apply("erf_u10_f64", x), oracle.apply("erfc_u10_f64", x)
+    assert np.max(np.abs(e + c - 1)) <= 2.0 ** -52
+    assert np.array_equal(oracle.apply("erf_u10_f64", -x), -e)
+    c2 = oracle.apply("erfc_u10_f64", -x)
+    assert np.max(np.abs(c + c2 - 2)) <= 2.0 ** -51
