@@ -188,6 +188,19 @@ sleefcu_status sleefcu_acosh_u35_f64(const double *x, double *out, size_t n, sle
 sleefcu_status sleefcu_atanh_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 sleefcu_status sleefcu_atanh_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 
+/* erf / erfc, FP64: erf(x) = x (C0 + T (C1 + T (c2 + t P(t)))) for |x| < 1
+ * (T = x^2 exact, outer levels in DD), 1 - erfc(|x|) up to 6, +-1 beyond;
+ * erfc(x) = 1 -+ erf(|x|) for |x| < 1, else F(|x|) e^(-x^2) with
+ * F = erfc e^(x^2) one polynomial per interval [1,2), [2,4), [4,8) and the
+ * asymptotic factor G(1/x^2) / (sqrt(pi) x) from 8 on, e^(-x^2) in DD and
+ * subnormal results rounded once; erfc(-x) = 2 - erfc(x); erfc(x > 27.3)
+ * underflows to +0.  erf(+-0) = +-0, erf(+-inf) = +-1, erfc(-inf) = 2,
+ * erfc(+inf) = +0.  The erfc u35 entry point runs the u10 algorithm. */
+sleefcu_status sleefcu_erf_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+
 /* ---------------- FP32 family (float-float forms) ----------------
  * The same methods in binary32 arithmetic only, with float-float pairs where
  * the 1-ULP bound needs them (the paper describes the FP64 functions; "all
@@ -261,7 +274,7 @@ typedef enum {
   SLEEFCU_FN_FMOD, SLEEFCU_FN_REMAINDER, SLEEFCU_FN_LOG1P, SLEEFCU_FN_TANH, SLEEFCU_FN_ERF,
   SLEEFCU_FN_EXP2, SLEEFCU_FN_EXP10, SLEEFCU_FN_EXPM1, SLEEFCU_FN_LOG2, SLEEFCU_FN_LOG10,
   SLEEFCU_FN_CBRT, SLEEFCU_FN_SINH, SLEEFCU_FN_COSH, SLEEFCU_FN_ASINH, SLEEFCU_FN_ACOSH,
-  SLEEFCU_FN_ATANH,
+  SLEEFCU_FN_ATANH, SLEEFCU_FN_ERFC,
   SLEEFCU_FN_COUNT
 } sleefcu_fn;
 typedef enum { SLEEFCU_F64 = 0, SLEEFCU_F32 = 1, SLEEFCU_BF16 = 2, SLEEFCU_F16 = 3 } sleefcu_dtype;

@@ -115,7 +115,11 @@ enum Kind { U64, B64, SC64, U32, BF, HF };
   X(78, "acosh_u10_f64", U64, derived64::AcoshU10) \
   X(79, "acosh_u35_f64", U64, derived64::AcoshU10) \
   X(80, "atanh_u10_f64", U64, derived64::AtanhU10) \
-  X(81, "atanh_u35_f64", U64, derived64::AtanhU10)
+  X(81, "atanh_u35_f64", U64, derived64::AtanhU10) \
+  X(82, "erf_u10_f64", U64, derived64::ErfU10) \
+  X(83, "erf_u35_f64", U64, derived64::ErfU35) \
+  X(84, "erfc_u10_f64", U64, derived64::ErfcU10) \
+  X(85, "erfc_u35_f64", U64, derived64::ErfcU10)
 
 #define SLEEFCU_BATCH_NAME(c, name, kind, F) name,
 static const char *kNames[] = {SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_NAME)};
@@ -229,7 +233,8 @@ using namespace sleefcu::batch;
 const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin",   "cos",   "tan",   "sincos", "asin",  "acos",  "atan",
                                           "atan2", "exp",   "log",   "pow",    "fmod",  "remainder",
                                           "log1p", "tanh",  "erf",   "exp2",   "exp10", "expm1", "log2",
-                                          "log10", "cbrt",  "sinh",  "cosh",   "asinh", "acosh", "atanh"};
+                                          "log10", "cbrt",  "sinh",  "cosh",   "asinh", "acosh", "atanh",
+                                          "erfc"};
 const char *kTypeNames[4] = {"f64", "f32", "bf16", "f16"};
 
 int code_of(const sleefcu_batch_item &it) {

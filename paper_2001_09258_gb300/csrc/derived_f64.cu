@@ -1,6 +1,6 @@
 // FP64 functions built on the exp/log cores (u10 and u35) for sm_103a:
 // exp2, exp10, expm1, log2, log10, log1p, cbrt, sinh, cosh, tanh, asinh,
-// acosh, atanh.  The paper lists them in the library without giving their
+// acosh, atanh, erf, erfc.  The paper lists them in the library without giving their
 // steps; each one here is a short fixed sequence of IEEE operations (DD where
 // the 1-ULP bound needs it, Section 3) on top of the Section 5.5-5.7 cores:
 //
@@ -449,6 +449,180 @@ struct AtanhU10 {
   }
 };
 
+
+// ---------------- erf, erfc ----------------
+// erf: |x| < 1: x (C0 + T (C1 + T (c2 + t P(t)))), T = x^2 exact, the three
+// outer levels in DD; 1 <= |x| < 6: 1 - erfc(|x|) in DD; +-1 beyond.
+// erfc: |x| < 1: 1 -+ erf(|x|) in DD; 1 <= |x| <= 27.5: F(|x|) e^(-x^2) with
+// F = erfc e^(x^2) a polynomial about the midpoint of [1,2), [2,4), [4,8)
+// (two leading terms in DD) or G(1/x^2) / (sqrt(pi) x) from 8 on; e^(-x^2)
+// from the DD exp core on the exact DD x^2; 2^k applied by two
+// multiplications (one rounding for subnormal results); erfc(-x) = 2 - erfc(x).
+// The tile sort groups lanes by interval so that each warp reads one row of
+// the coefficient tables.  u35 erf: the same pieces in double; u35 erfc runs
+// the u10 algorithm.
+constexpr double RSQPIH = 0x1.20dd750429b6dp-1, RSQPIL = 0x1.1ae3a914f6e1fp-57;   // 1/sqrt(pi)
+static __constant__ double kErfH[4] = {0x1.20dd750429b6dp+0, 0x1.18308016146fep-56, -0x1.812746b0379e6p-2, 0x1.dd80e959672c6p-58};
+static __constant__ double kErfP[11] = {
+    0x1.ce2f21a042b20p-4, -0x1.b82ce31284967p-6, 0x1.565bcd0daf845p-8, -0x1.c02db3d8c8f93p-11,
+    0x1.f9a3219c76949p-14, -0x1.f4d1ded722b03p-17, 0x1.b9deec50ab26ap-20, -0x1.5f1d06eacf4c6p-23,
+    0x1.f7a1f36ad5781p-27, -0x1.3863e3c35d413p-30, 0x1.0566538cb8283p-34};
+static __constant__ double kErfcFH[3][4] = {
+    {0x1.494daffa2ad68p-2, 0x1.39bdf0f0798c4p-56, -0x1.4f1988444caf7p-3, 0x1.24ac537655c12p-57},
+    {0x1.6e9827d229d2dp-3, -0x1.90756fe6b9db3p-58, -0x1.bd6ae4d14b16fp-5, 0x1.8d8b238907b15p-61},
+    {0x1.7c0348489d721p-4, 0x1.ca79ab435b660p-58, -0x1.ed7f66d9d09fep-7, 0x1.3b520acfa96f3p-62}};
+static __constant__ double kErfcFP[3][22] = {
+  {
+    0x1.37ea271bc54bdp-4, -0x1.0dc51d2941e6dp-5, 0x1.b65944f34f7adp-7, -0x1.513ed7600d1c0p-8,
+    0x1.ee705e736464dp-10, -0x1.5b0abfe65a32dp-11, 0x1.d4509d0d417b9p-13, -0x1.30c0ec743bcedp-14,
+    0x1.7f997923557c4p-16, -0x1.d4157188ae920p-18, 0x1.156c936a3105dp-19, -0x1.4004eff6f7f58p-21,
+    0x1.67cf5f0988c05p-23, -0x1.8adc1a9fe6189p-25, 0x1.a779871f4a7bdp-27, -0x1.bc5770d3295a2p-29,
+    0x1.c8a6eada5b280p-31, -0x1.cbfeb0383b565p-33, 0x1.c520022695974p-35, -0x1.b81dd79ebf9adp-37,
+    0x1.c82b760607022p-39, -0x1.a70fd6017ce87p-41},
+  {
+    0x1.043fe1a98c0cdp-6, -0x1.259061ba85692p-8, 0x1.409cc2ed3fefbp-10, -0x1.53dec9d089553p-12,
+    0x1.5e739304850bcp-14, -0x1.6025103c1981bp-16, 0x1.595f1b5dbff18p-18, -0x1.4b14628647c09p-20,
+    0x1.369904b947a56p-22, -0x1.1d791455a0f11p-24, 0x1.01508df8e0a1fp-26, -0x1.c752068f0a96ep-29,
+    0x1.8bbf3f6db12c5p-31, -0x1.522804d7a7020p-33, 0x1.1c3dc4fa8a305p-35, -0x1.d66d6369f7643p-38,
+    0x1.8003b981c62cdp-40, -0x1.3453718d4c0bfp-42, 0x1.dbc8fa69f1588p-45, -0x1.7551e98792b95p-47,
+    0x1.6ca3dddd58940p-49, -0x1.10f3c57b6b0d7p-51},
+  {
+    0x1.3c7764a81f462p-9, -0x1.9106a7cd79e3bp-12, 0x1.f64cd9c07b5c5p-15, -0x1.370d0641775e4p-17,
+    0x1.7d0e03edb73e5p-20, -0x1.cde4cecce654ep-23, 0x1.1513469d8602cp-25, -0x1.491bb0ca940c5p-28,
+    0x1.83201ae0eb1dcp-31, -0x1.c312ca4fcf13cp-34, 0x1.045ff3e648ff3p-36, -0x1.29e5d7aaf7613p-39,
+    0x1.51dbcb9512727p-42, -0x1.7be13c8006386p-45, 0x1.a72a1d41d3c2ap-48, -0x1.d40a279e38d1dp-51,
+    0x1.040a46c482170p-53, -0x1.1a97bd1e37a50p-56, 0x1.0dfc0cce80407p-59, -0x1.24502b98063a1p-62,
+    0x1.0709dd4f990c4p-64, -0x1.11b59748cdbf2p-67}};
+static __constant__ double kErfcGH[4] = {0x1.0000000000000p+0, -0x1.38b4a1f7dc331p-66, -0x1.ffffffffffffbp-2, -0x1.449ed132ba430p-56};
+static __constant__ double kErfcGP[9] = {
+    0x1.7ffffffffe83fp-1, -0x1.dffffffd0f32bp+0, 0x1.a3fffe80c9ac6p+2, -0x1.d87f8dc75c4bdp+4,
+    0x1.44cd52e365bc6p+7, -0x1.0749c46c91cccp+10, 0x1.e1ba8d8295a72p+12, -0x1.b7be9d06eea96p+15,
+    0x1.142dd87ba7a2cp+18};
+
+__device__ __forceinline__ d2 neg_d2(d2 a) { return D2(-a.x, -a.y); }
+// erf(a)/a as a DD, 0 <= a < 1
+__device__ __forceinline__ d2 erf_s(double a) {
+  d2 T = mul_dd(a, a);
+  double p = poly_p<10>(T.x, kErfP + 1);
+  d2 in = add_dd(kErfP[0], __dmul_rn(T.x, p));
+  in = add_d2d2(D2(kErfH[2], kErfH[3]), mul_d2d2(T, in));
+  return add_d2d2(D2(kErfH[0], kErfH[1]), mul_d2d2(T, in));
+}
+__device__ __forceinline__ int erfc_iv(double a) { return a < 2.0 ? 0 : (a < 4.0 ? 1 : 2); }
+// F(a) = erfc(a) e^(a^2) as a DD, 1 <= a <= 27.5
+__device__ __forceinline__ d2 erfc_F(double a) {
+  if (a < 8.0) {
+    int i = erfc_iv(a);
+    double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
+    double p = poly_p<22>(u, kErfcFP[i]);
+    d2 in = add_d2_d(D2(kErfcFH[i][2], kErfcFH[i][3]), __dmul_rn(u, p));
+    return add_d2d2(D2(kErfcFH[i][0], kErfcFH[i][1]), mul_d2_d(in, u));
+  }
+  double w = __ddiv_rn(1.0, __dmul_rn(a, a));
+  double p = poly_p<9>(w, kErfcGP);
+  d2 in = add_d2_d(D2(kErfcGH[2], kErfcGH[3]), __dmul_rn(w, p));
+  d2 g = add_d2d2(D2(kErfcGH[0], kErfcGH[1]), mul_d2_d(in, w));
+  return div_d2d2(mul_d2d2(g, D2(RSQPIH, RSQPIL)), D2(a, 0.0));
+}
+// erfc(a) = c 2^k, 1 <= a <= 27.5
+__device__ __forceinline__ d2 erfc_core(double a, double &k) {
+  d2 Y = mul_dd(a, a);
+  d2 s = expk_s(D2(-Y.x, -Y.y), k);
+  return mul_d2d2(erfc_F(a), add_d_d2_fast(1.0, s));
+}
+// y 2^k by two multiplications with normal powers of two (one rounding)
+__device__ __forceinline__ double scale2_two(double y, int k) {
+  int k1 = k / 2, k2 = k - k1;
+  return __dmul_rn(__dmul_rn(y, pow2i(k1)), pow2i(k2));
+}
+
+struct ErfU10 {
+  static constexpr int NCLS = 5;
+  __device__ static int cls(double x) {
+    double a = from_bits(bits(x) & ABS64);
+    return a < 1.0 ? 0 : (a < 2.0 ? 1 : (a < 4.0 ? 2 : (a < 6.0 ? 3 : 4)));
+  }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    double a = from_bits(bx & ABS64);
+    double y;
+    if (a < 1.0) {
+      d2 e = mul_d2_d(erf_s(a), a);
+      y = __dadd_rn(e.x, e.y);
+    } else if (a < 6.0) {
+      double k;
+      d2 c = erfc_core(a, k);
+      c = scale_d2(c, pow2i(int_of(k)));
+      d2 r = add_d_d2(1.0, neg_d2(c));
+      y = __dadd_rn(r.x, r.y);
+    } else {
+      y = 1.0;
+    }
+    if (is_nan_b(bx)) y = from_bits(QNAN64);
+    return canon(copysign_b(y, bx));
+  }
+};
+struct ErfcU10 {
+  static constexpr int NCLS = 6;
+  __device__ static int cls(double x) {
+    double a = from_bits(bits(x) & ABS64);
+    return a < 1.0 ? 0 : (a < 2.0 ? 1 : (a < 4.0 ? 2 : (a < 8.0 ? 3 : (a <= 27.5 ? 4 : 5))));
+  }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    double a = from_bits(bx & ABS64);
+    double y;
+    if (a < 1.0) {
+      d2 e = mul_d2_d(erf_s(a), a);
+      if (x > 0.0) e = neg_d2(e);
+      d2 r = add_d_d2(1.0, e);
+      y = __dadd_rn(r.x, r.y);
+    } else if (a <= 27.5) {
+      double k;
+      d2 c = erfc_core(a, k);
+      if (x > 0.0) {
+        y = scale2_two(__dadd_rn(c.x, c.y), int_of(k));
+      } else if (a < 8.0) {
+        c = scale_d2(c, pow2i(int_of(k)));
+        d2 r = add_d_d2(2.0, neg_d2(c));
+        y = __dadd_rn(r.x, r.y);
+      } else {
+        y = 2.0;
+      }
+    } else {
+      y = x > 0.0 ? 0.0 : 2.0;
+    }
+    if (is_nan_b(bx)) y = from_bits(QNAN64);
+    return canon(y);
+  }
+};
+struct ErfU35 {
+  static constexpr int NCLS = 5;
+  __device__ static int cls(double x) { return ErfU10::cls(x); }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    double a = from_bits(bx & ABS64);
+    double y;
+    if (a < 1.0) {
+      double t = __dmul_rn(a, a);
+      y = __dmul_rn(a, __fma_rn(t, __fma_rn(t, poly(t, kErfP), kErfH[2]), kErfH[0]));
+    } else if (a < 6.0) {
+      int i = erfc_iv(a);
+      double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
+      double F = __fma_rn(u, __fma_rn(u, poly_p<22>(u, kErfcFP[i]), kErfcFH[i][2]), kErfcFH[i][0]);
+      d2 Y = mul_dd(a, a);
+      double k = rint(__dmul_rn(-Y.x, R_LN2));
+      double r = __dsub_rn(__fma_rn(k, -L2B, __fma_rn(k, -L2A, -Y.x)), Y.y);
+      double E = __dmul_rn(__dadd_rn(1.0, em1_r_u35(r)), pow2i(int_of(k)));
+      y = __fma_rn(-F, E, 1.0);
+    } else {
+      y = 1.0;
+    }
+    if (is_nan_b(bx)) y = from_bits(QNAN64);
+    return canon(copysign_b(y, bx));
+  }
+};
+
 }  // namespace derived64
 }  // namespace sleefcu
 
@@ -489,6 +663,10 @@ SORTED64(asinh_u10_f64, AsinhU10)
 SORTED64(asinh_u35_f64, AsinhU10)
 SORTED64(acosh_u10_f64, AcoshU10)
 SORTED64(acosh_u35_f64, AcoshU10)
+SORTED64(erf_u10_f64, ErfU10)
+SORTED64(erf_u35_f64, ErfU35)
+SORTED64(erfc_u10_f64, ErfcU10)
+SORTED64(erfc_u35_f64, ErfcU10)
 UNARY64(atanh_u10_f64, AtanhU10)
 UNARY64(atanh_u35_f64, AtanhU10)
 #undef UNARY64

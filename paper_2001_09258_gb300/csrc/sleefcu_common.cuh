@@ -78,6 +78,17 @@ __device__ __forceinline__ double poly(double t, const double (&c)[N]) {
   if (N > 16) pw[4] = __dmul_rn(pw[3], pw[3]);
   return Estrin<N>::d(c, pw);
 }
+// the same for N coefficients starting at c (a row of a table)
+template <int N>
+__device__ __forceinline__ double poly_p(double t, const double *c) {
+  double pw[5];
+  pw[0] = t;
+  if (N > 2) pw[1] = __dmul_rn(t, t);
+  if (N > 4) pw[2] = __dmul_rn(pw[1], pw[1]);
+  if (N > 8) pw[3] = __dmul_rn(pw[2], pw[2]);
+  if (N > 16) pw[4] = __dmul_rn(pw[3], pw[3]);
+  return Estrin<N>::d(c, pw);
+}
 template <int N>
 __device__ __forceinline__ float polyf(float t, const float (&c)[N]) {
   float pw[5];

@@ -81,6 +81,15 @@ OPS = {
     "acosh_u35_f64": {"small": 81, "big": 61},
     "atanh_u10_f64": {"all": 72},
     "atanh_u35_f64": {"all": 72},
+    # erf/erfc: "a" |x| < 1 (DD erf kernel 45: erf 49, erfc 56), "f" 1 <= |x|
+    # < 6 (erf) or 8 (erfc) (interval polynomial in DD 45 + DD exp core 46 +
+    # x^2, 1 + s and the product 10: erf 111, erfc 104 for x > 0 and 111 for
+    # x < 0), "g" 8 <= |x| <= 27.5 (asymptotic form 42: erfc 101), "sat"
+    # beyond (no arithmetic); u35 erf: 17 and 52
+    "erf_u10_f64": {"a": 49, "f": 111, "g": 0, "sat": 0},
+    "erfc_u10_f64": {"a": 56, "f": 104, "fneg": 111, "g": 101, "sat": 0},
+    "erfc_u35_f64": {"a": 56, "f": 104, "fneg": 111, "g": 101, "sat": 0},
+    "erf_u35_f64": {"a": 17, "f": 52, "g": 0, "sat": 0},
 }
 
 
@@ -115,6 +124,17 @@ def path_mix(name, x, y=None, steps=None):
     if fn in ("sinh", "cosh"):
         small = int((ax <= 22).sum())
         return {"small": small, "big": ax.size - small}
+    if fn in ("erf", "erfc"):
+        a = ax < 1
+        f = (ax >= 1) & (ax < (6 if fn == "erf" else 8))
+        g = (ax >= 8) & (ax <= 27.5) if fn == "erfc" else np.zeros_like(a)
+        out = {"a": int(a.sum()), "g": int(g.sum()), "sat": int(ax.size - a.sum() - f.sum() - g.sum())}
+        if fn == "erfc":
+            out["f"] = int((f & (x > 0)).sum())
+            out["fneg"] = int((f & ~(x > 0)).sum())
+        else:
+            out["f"] = int(f.sum())
+        return out
     if fn in ("asinh", "acosh"):
         big = int((ax > 2.0 ** 500).sum())
         return {"small": ax.size - big, "big": big}
