@@ -460,35 +460,38 @@ def main():
     total_el = n * len(names) * args.steps * ws
     value = total_el / (ms_max * 1e-3) / 1e9
 
-    # e2e: the public API from pinned host buffers, copies inside the timed region
+    # e2e: the library's host-memory entry point (sleefcu_eval_host) on pinned
+    # host arrays: every step copies each input in, evaluates and copies each
+    # result out, overlapped chunk by chunk inside the library; host clock
+    # around whole steps (each call returns with its results in host memory)
     e2e = None
     if not args.no_e2e:
         hin = {fn: [torch.from_numpy(a).pin_memory() for a in xs] for fn, xs in host.items()}
         hout = {name: [torch.empty(n, dtype=torch.float64).pin_memory() for _ in outs[name]] for name in names}
         h2d = sum(sum(a.numel() * 8 for a in hin[nm.split("_")[0]]) for nm in names)
         d2h = sum(sum(a.numel() * 8 for a in hout[nm]) for nm in names)
+        hin_np = {fn: [t.numpy() for t in ts] for fn, ts in hin.items()}
+        hout_np = {nm: [t.numpy() for t in ts] for nm, ts in hout.items()}
 
         def e2e_step():
             for name in names:
-                fn = name.split("_")[0]
-                for d, h in zip(dev[fn], hin[fn]):
-                    d.copy_(h, non_blocking=True)
-                launch(sleefcu, name, dev[fn], outs[name], sp)
-                for h, d in zip(hout[name], outs[name]):
-                    h.copy_(d, non_blocking=True)
+                xs, os_ = hin_np[name.split("_")[0]], hout_np[name]
+                sleefcu.eval_host(name, xs[0], xs[1] if len(xs) > 1 else None,
+                                  os_[0], os_[1] if len(os_) > 1 else None)
         e2e_step()
         torch.cuda.synchronize()
         barrier(ws)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
+        t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
-        b.record(st)
         torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3
         barrier(ws)
-        e_ms = allmax(ws, a.elapsed_time(b), device)
+        e_ms = allmax(ws, e_ms, device)
         e2e = {"value": round(total_el / (e_ms * 1e-3) / 1e9, 4), "unit": "Gelem/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "sleefcu_eval_host (pinned host arrays, 3 chunks of 2^22 in flight)",
+               "timer": "host clock around whole steps"}
 
     if rank != 0:
         return

@@ -321,6 +321,22 @@ void sleefcu_batch_destroy(sleefcu_batch *plan);
 sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size_t count,
                                            sleefcu_stream stream);
 
+/* ---------------- evaluation from host memory ----------------
+ * The end-to-end form of every entry point: item describes one array exactly
+ * as for the batched launch, but x, y, out, out2 are HOST pointers.  The
+ * library streams the arrays through device buffers it owns in chunks of
+ * `chunk` elements (0: 4,194,304), keeping three chunks in flight: copy in
+ * of chunk i+1, the entry point's kernel on chunk i and copy out of chunk
+ * i-1 run concurrently on three library streams.  Results equal the device
+ * entry point's bit for bit.  The call is synchronous: it returns when out
+ * (and out2) hold every result.  Host arrays should be page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to overlap; pageable
+ * memory works at lower speed.  The staging buffers (3 x 4 x chunk x element
+ * size bytes of device memory) and streams are created on the first call
+ * per device and kept; ENOMEM if they cannot be allocated.  Calls from
+ * several host threads on one device are serialized. */
+sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

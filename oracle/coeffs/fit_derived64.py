@@ -13,6 +13,14 @@ Run:  python oracle/coeffs/fit_derived64.py [name ...]
          as DD pairs, relative error
   erfc_G G(w) = sqrt(pi) x erfc(x) e^(x^2), w = 1/x^2 in [0, 1/64] (x >= 8),
          where the asymptotic series converges fast enough; 16 terms
+  lgamma_r2  R(e) = lgamma(2 + e) / e on [-0.25, 0.5] (x in [1.75, 2.5)) as
+         c1 + e (c2 + e Q(e)), c1 and c2 DD pairs, relative error; 18 terms
+  lgamma_m   lgamma(1.5 + u) on [-0.25, 0.25] (x in [1.25, 1.75), around the
+         minimum) as c0 + u (c1 + u Q(u)), c0 and c1 DD pairs; 18 terms
+  lgamma_st  the Stirling correction x (lgamma(x) - (x - 1/2) log x + x -
+         log(2 pi)/2) as a polynomial in w = 1/x^2 on [0, 1/64] (x >= 8)
+  sinpi  sin(pi s) = s (pi + t (c1 + t Q(t))), t = s^2 in [0, 1/4], pi and c1
+         DD pairs
   cbrt   start value of the inverse cube root, m^(-1/3) on [1, 2] to about
          2^-26 relative, refined by Newton steps that need no division
 """
@@ -83,7 +91,40 @@ def erfc_job(i, n):
                                mp.mpf(a) - m, mp.mpf(b) - m, n_grid=3000)
 
 
+def lg_r2(e):
+    if abs(e) < mp.mpf("1e-25"):
+        return 1 - mp.euler + (mp.zeta(2) - 1) / 2 * e
+    return mp.loggamma(2 + e) / e
+
+
+def lg_st(w):
+    if w < mp.mpf("1e-30"):
+        return mp.mpf(1) / 12 - w / 360
+    x = 1 / mp.sqrt(w)
+    return x * (mp.loggamma(x) - ((x - mp.mpf(0.5)) * mp.log(x) - x + mp.log(2 * mp.pi) / 2))
+
+
+def sinpi_q(t):
+    if t < mp.mpf("1e-30"):
+        return -mp.pi ** 3 / 6 + mp.pi ** 5 / 120 * t
+    s = mp.sqrt(t)
+    return (mp.sin(mp.pi * s) / s - mp.pi) / t
+
+
+def sinpi_w(t):
+    s = mp.sqrt(t)
+    return t * s / mp.sin(mp.pi * s) if t != 0 else mp.mpf(0)
+
+
 JOBS = {
+    "lgamma_r2": lambda: fit_rounded(lg_r2, lambda e: 1 / abs(lg_r2(e)), range(18), ["dd", "dd"] + ["d"] * 16,
+                                     -mp.mpf("0.25"), mp.mpf("0.5"), n_grid=3000),
+    "lgamma_m": lambda: fit_rounded(lambda u: mp.loggamma(mp.mpf("1.5") + u),
+                                    lambda u: 1 / abs(mp.loggamma(mp.mpf("1.5") + u)), range(18),
+                                    ["dd", "dd"] + ["d"] * 16, -mp.mpf("0.25"), mp.mpf("0.25"), n_grid=3000),
+    "lgamma_st": lambda: fit_rounded(lg_st, lambda w: 1 / lg_st(w), range(10), ["d"] * 10, 0, mp.mpf(1) / 64,
+                                     n_grid=3000),
+    "sinpi": lambda: fit_rounded(sinpi_q, sinpi_w, range(12), ["dd"] + ["d"] * 11, 0, mp.mpf("0.25"), n_grid=3000),
     "erf_a": lambda: fit_rounded(erf_over_x, lambda t: 1 / erf_over_x(t), range(18), ["dd", "dd"] + ["d"] * 16,
                                  0, 1, n_grid=3000),
     "erfc_F0": erfc_job(0, 24),

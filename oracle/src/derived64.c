@@ -535,3 +535,4 @@ double oracle_erf_u35_f64(double x) {
 }
 
 double oracle_erfc_u35_f64(double x) { return oracle_erfc_u10_f64(x); }
+

@@ -208,6 +208,31 @@ static double expk(dd_t Y) {
   return y;
 }
 
+/* log of a DD y > 0 (finite) with the internal log of pow: y = m 2^e with m
+ * in [0.75, 1.5) taken from the head, z = 2(m-1)/(m+1) in DD and the 11-term
+ * DD polynomial; about 2^-66 relative */
+dd_t oracle_logk_dd(dd_t y) {
+  int off = 0;
+  if (y.x < 0x1p-1022) { y = ddscale_d2_d2_d(y, 0x1p64); off = 64; }
+  int ex = ilogb(y.x);
+  dd_t m = ddscale_d2_d2_d(y, ldexp(1.0, -ex));
+  if (m.x >= 1.5) { m = ddscale_d2_d2_d(m, 0.5); ex++; }
+  dd_t num = ddscale_d2_d2_d(ddadd2_d2_d_d(m.x - 1.0, m.y), 2.0);
+  dd_t z = dddiv_d2_d2_d2(num, ddadd2_d2_d_d2(1.0, m));
+  dd_t t = ddsqu_d2_d2(z);
+  double q = poly_d(t.x, POWLOG, 9);
+  dd_t w = ddadd_d2_d2_d(dd(PL_C1H, PL_C1L), t.x * q);
+  w = ddmul_d2_d2_d2(t, w);
+  w = ddmul_d2_d2_d2(z, w);
+  dd_t lm = ddadd_d2_d2_d2(z, w);
+  double ed = (double)(ex - off);
+  return ddadd2_d2_d2_d2(dd(ed * L2H, ed * L2L), lm);
+}
+
+/* e^Y for a DD Y (the internal exp of pow): overflow to +inf, underflow with
+ * subnormals rounded once */
+double oracle_exp_dd(dd_t Y) { return expk(Y); }
+
 double oracle_pow_u10_f64(double x, double y) {
   double ax = fabs(x);
   double axc = (ax > 0 && ax <= 0x1.fffffffffffffp1023) ? ax : 1.0;

@@ -177,6 +177,7 @@ def _batch_lib():
         L.sleefcu_batch_set_config.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
         L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.sleefcu_batch_launch_static.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_void_p]
+        L.sleefcu_eval_host.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t]
         L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
         L.sleefcu_batch_destroy.restype = None
         L._batch_ready = True
@@ -201,6 +202,21 @@ def batch_launch_static(items, stream=None):
     arr = _items_array(items)
     _check(_batch_lib().sleefcu_batch_launch_static(arr, len(items), ctypes.c_void_p(st.cuda_stream)),
            "batch_launch_static")
+
+
+def eval_host(name, x, y=None, out=None, out2=None, chunk=0):
+    """sleefcu_eval_host on host arrays (numpy arrays or raw addresses): the
+    library copies chunks in, runs entry point `name` and copies results out,
+    overlapped; returns when out holds every result."""
+    import numpy as np
+    fn, acc, prec = name.split("_")
+    ptr = lambda a: None if a is None else (a.ctypes.data if isinstance(a, np.ndarray) else int(a))
+    n = x.size if isinstance(x, np.ndarray) else None
+    if n is None:
+        raise SleefcuError("eval_host: pass numpy arrays")
+    item = BatchItem(FN_IDS[fn], DTYPE_IDS[prec], int(acc[1:]), 0, ptr(x), ptr(y), ptr(out), ptr(out2), n)
+    _check(_batch_lib().sleefcu_eval_host(ctypes.byref(item), chunk), "eval_host")
+    return out
 
 
 class Batch:
