@@ -16,7 +16,7 @@ Run:  python oracle/coeffs/fit_derived64.py [name ...]
   lgamma_r2  R(e) = lgamma(2 + e) / e on [-0.25, 0.5] (x in [1.75, 2.5)) as
          c1 + e (c2 + e Q(e)), c1 and c2 DD pairs, relative error; 18 terms
   lgamma_m   lgamma(1.5 + u) on [-0.25, 0.25] (x in [1.25, 1.75), around the
-         minimum) as c0 + u (c1 + u Q(u)), c0 and c1 DD pairs; 18 terms
+         minimum) as c0 + u (c1 + u (c2 + u Q(u))), c0, c1, c2 DD pairs; 18 terms
   lgamma_st  the Stirling correction x (lgamma(x) - (x - 1/2) log x + x -
          log(2 pi)/2) as a polynomial in w = 1/x^2 on [0, 1/64] (x >= 8)
   sinpi  sin(pi s) = s (pi + t (c1 + t Q(t))), t = s^2 in [0, 1/4], pi and c1
@@ -121,7 +121,7 @@ JOBS = {
                                      -mp.mpf("0.25"), mp.mpf("0.5"), n_grid=3000),
     "lgamma_m": lambda: fit_rounded(lambda u: mp.loggamma(mp.mpf("1.5") + u),
                                     lambda u: 1 / abs(mp.loggamma(mp.mpf("1.5") + u)), range(18),
-                                    ["dd", "dd"] + ["d"] * 16, -mp.mpf("0.25"), mp.mpf("0.25"), n_grid=3000),
+                                    ["dd", "dd", "dd"] + ["d"] * 15, -mp.mpf("0.25"), mp.mpf("0.25"), n_grid=3000),
     "lgamma_st": lambda: fit_rounded(lg_st, lambda w: 1 / lg_st(w), range(10), ["d"] * 10, 0, mp.mpf(1) / 64,
                                      n_grid=3000),
     "sinpi": lambda: fit_rounded(sinpi_q, sinpi_w, range(12), ["dd"] + ["d"] * 11, 0, mp.mpf("0.25"), n_grid=3000),

@@ -54,6 +54,10 @@ double oracle_erf_u10_f64(double);
 double oracle_erf_u35_f64(double);
 double oracle_erfc_u10_f64(double);
 double oracle_erfc_u35_f64(double);
+double oracle_tgamma_u10_f64(double);
+double oracle_tgamma_u35_f64(double);
+double oracle_lgamma_u10_f64(double);
+double oracle_lgamma_u35_f64(double);
 double oracle_pow_u10_f64(double, double);
 double oracle_pow_u35_f64(double, double);
 double oracle_asin_u10_f64(double);

@@ -165,3 +165,70 @@ def test_erf_identities():
     assert np.array_equal(oracle.apply("erf_u10_f64", -x), -e)
     c2 = oracle.apply("erfc_u10_f64", -x)
     assert np.max(np.abs(c + c2 - 2)) <= 2.0 ** -51
+
+
+GAMMA_SETS = {
+    "tgamma": lambda: [U("t1", N, -170, 171.6), U("t2", N, 0, 3), L("t3", N, 1e-300, 1e-3), U("t4", N, -5, 0),
+                       U("t5", N, 160, 171.62), U("t6", N, -190, -170), L("t7", N, 5e-324, 1e-300, signed=False),
+                       U("t8", N, 0.99, 2.01)],
+    "lgamma": lambda: [U("l1", N, 0, 1000), U("l2", N, 0, 3), L("l3", N, 1e-300, 2.5e305, signed=False),
+                       U("l4", N, 0.99, 1.01), U("l5", N, 1.99, 2.01), U("l6", N, 1.2, 1.8), U("l7", N, 2.4, 8.5),
+                       U("l9", N, 0.5, 0.8), L("l10", N, 5e-324, 1e-300, signed=False)],
+}
+
+
+@needs_quad
+@pytest.mark.parametrize("fn", list(GAMMA_SETS))
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_gamma_ulp_bound(fn, acc):
+    """tgamma everywhere, lgamma on x > 0 (relative accuracy across its zeros
+    at 1 and 2): within the 1-ULP bound (u35 runs the same algorithm)."""
+    x = np.concatenate(GAMMA_SETS[fn]() + [I.SPECIALS_F64[I.SPECIALS_F64 > 0] if fn == "lgamma" else I.SPECIALS_F64])
+    y = oracle.apply(f"{fn}_{acc}_f64", x)
+    err = quadref.ulp_err(fn, x, y)
+    i = int(np.argmax(err))
+    assert err.max() <= 1.0, (fn, acc, x[i], y[i], err.max())
+
+
+@needs_quad
+def test_lgamma_negative_axis():
+    """x < 0: the reflection cancels near the zeros of lgamma (x = -2.457...,
+    -2.747..., ...), as in every libm, so the bound there is absolute:
+    |error| <= 2^-51 max(1, |lgamma x|); away from them (|lgamma x| >= 1) it
+    is the 1-ULP bound."""
+    x = np.concatenate([U("n1", N, -1000, 0), U("n2", N, -5, 0), U("n3", N, -2.5, -2.4),
+                        L("n4", N, 1e-300, 1e-3, signed=False) * -1])
+    x = x[x != np.rint(x)]
+    y = oracle.apply("lgamma_u10_f64", x)
+    ref = quadref.ref("lgamma", x)
+    assert np.max(np.abs(y - ref) / np.maximum(1, np.abs(ref))) <= 2.0 ** -51
+    far = np.abs(ref) >= 1
+    err = quadref.ulp_err("lgamma", x[far], y[far])
+    assert err.max() <= 1.0, (x[far][np.argmax(err)], err.max())
+
+
+@pytest.mark.parametrize("fn", ["tgamma", "lgamma"])
+def test_gamma_special_values(fn):
+    f = getattr(_libm, fn)
+    f.restype, f.argtypes = ctypes.c_double, [ctypes.c_double]
+    x = np.array([0.0, -0.0, 1.0, 2.0, -1.0, -2.0, -1e300, math.inf, -math.inf, math.nan, 172.0, 171.7,
+                  -200.5, -201.5, 2.6e305, 5e-324, -0.5, 0.5, 3.0])
+    y = oracle.apply(f"{fn}_u10_f64", x)
+    for xi, yi in zip(x, y):
+        want = f(float(xi))
+        if math.isnan(want) or math.isinf(want) or want == 0 or xi in (1.0, 2.0):
+            assert _same(yi, want), (fn, xi, yi, want)
+
+
+@needs_quad
+def test_gamma_identities():
+    n = np.arange(1, 24, dtype=np.float64)
+    fact = np.array([float(math.factorial(int(k) - 1)) for k in n])
+    assert np.all(quadref.ulp_err("tgamma", n, oracle.apply("tgamma_u10_f64", n)) <= 1.0)
+    assert np.max(np.abs(oracle.apply("tgamma_u10_f64", n) / fact - 1)) <= 2.0 ** -52
+    x = np.round(U("gi", 20000, 0.1, 100) * 2.0 ** 40) * 2.0 ** -40      # x + 1 exact
+    t, t1 = oracle.apply("tgamma_u10_f64", x), oracle.apply("tgamma_u10_f64", x + 1)
+    ok = np.abs(t1 / (x * t) - 1) <= 2.0 ** -50
+    assert ok.all()
+    lg = oracle.apply("lgamma_u10_f64", x)
+    assert np.max(np.abs(lg - np.log(t)) / np.maximum(1, np.abs(lg))) <= 2.0 ** -50
