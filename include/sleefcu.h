@@ -201,6 +201,22 @@ sleefcu_status sleefcu_erf_u35_f64(const double *x, double *out, size_t n, sleef
 sleefcu_status sleefcu_erfc_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 sleefcu_status sleefcu_erfc_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 
+/* tgamma / lgamma, FP64: log-gamma as a DD from Stirling's form (y >= 8,
+ * with the DD logarithm of pow), polynomials about 2 and 1.5 (relative
+ * accuracy across the zeros at 1 and 2), the shift y -> y + n with the
+ * product in DD, and for y < 0 the reflection with sin(pi y) reduced
+ * exactly; tgamma = exp of the DD log-gamma with the sign of sin(pi y).
+ * tgamma(+-0) = +-inf, tgamma(negative integer or -inf) = NaN, overflow to
+ * +inf above 171.62, underflow to +-0 below -190; lgamma(0 or a non-positive
+ * integer or +-inf) = +inf, overflow to +inf above 2.556e305.  Near the
+ * zeros of lgamma on the negative axis the error is bounded in absolute
+ * terms (2^-51 max(1, |lgamma|)).  The u35 entry points run the u10
+ * algorithm. */
+sleefcu_status sleefcu_tgamma_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tgamma_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+
 /* ---------------- FP32 family (float-float forms) ----------------
  * The same methods in binary32 arithmetic only, with float-float pairs where
  * the 1-ULP bound needs them (the paper describes the FP64 functions; "all
@@ -274,7 +290,7 @@ typedef enum {
   SLEEFCU_FN_FMOD, SLEEFCU_FN_REMAINDER, SLEEFCU_FN_LOG1P, SLEEFCU_FN_TANH, SLEEFCU_FN_ERF,
   SLEEFCU_FN_EXP2, SLEEFCU_FN_EXP10, SLEEFCU_FN_EXPM1, SLEEFCU_FN_LOG2, SLEEFCU_FN_LOG10,
   SLEEFCU_FN_CBRT, SLEEFCU_FN_SINH, SLEEFCU_FN_COSH, SLEEFCU_FN_ASINH, SLEEFCU_FN_ACOSH,
-  SLEEFCU_FN_ATANH, SLEEFCU_FN_ERFC,
+  SLEEFCU_FN_ATANH, SLEEFCU_FN_ERFC, SLEEFCU_FN_TGAMMA, SLEEFCU_FN_LGAMMA,
   SLEEFCU_FN_COUNT
 } sleefcu_fn;
 typedef enum { SLEEFCU_F64 = 0, SLEEFCU_F32 = 1, SLEEFCU_BF16 = 2, SLEEFCU_F16 = 3 } sleefcu_dtype;

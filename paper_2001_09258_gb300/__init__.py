@@ -30,6 +30,7 @@ FUNCS = {
     "log1p": "u", "tanh": "u", "erf": "u",
     "exp2": "u", "exp10": "u", "expm1": "u", "log2": "u", "log10": "u", "cbrt": "u",
     "sinh": "u", "cosh": "u", "asinh": "u", "acosh": "u", "atanh": "u", "erfc": "u",
+    "tgamma": "u", "lgamma": "u",
 }
 PRECS = {fn: ("f64",) for fn in FUNCS}
 for _fn in ("sin", "cos", "exp", "log", "log1p", "tanh", "erf"):
@@ -156,7 +157,7 @@ for _fn in FUNCS:
 FN_IDS = {name: i for i, name in enumerate(
     ["sin", "cos", "tan", "sincos", "asin", "acos", "atan", "atan2", "exp", "log", "pow", "fmod",
      "remainder", "log1p", "tanh", "erf", "exp2", "exp10", "expm1", "log2", "log10", "cbrt", "sinh",
-     "cosh", "asinh", "acosh", "atanh", "erfc"])}
+     "cosh", "asinh", "acosh", "atanh", "erfc", "tgamma", "lgamma"])}
 DTYPE_IDS = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 
 

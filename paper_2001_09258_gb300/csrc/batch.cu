@@ -19,6 +19,7 @@
 #include "trig_f32.cu"
 #include "explog_f32.cu"
 #include "derived_f64.cu"
+#include "gamma_f64.cu"
 #undef SLEEFCU_FUNCTORS_ONLY
 
 #include <cstdio>
@@ -119,7 +120,11 @@ enum Kind { U64, B64, SC64, U32, BF, HF };
   X(82, "erf_u10_f64", U64, derived64::ErfU10) \
   X(83, "erf_u35_f64", U64, derived64::ErfU35) \
   X(84, "erfc_u10_f64", U64, derived64::ErfcU10) \
-  X(85, "erfc_u35_f64", U64, derived64::ErfcU10)
+  X(85, "erfc_u35_f64", U64, derived64::ErfcU10) \
+  X(86, "tgamma_u10_f64", U64, gamma64::TgammaU10) \
+  X(87, "tgamma_u35_f64", U64, gamma64::TgammaU10) \
+  X(88, "lgamma_u10_f64", U64, gamma64::LgammaU10) \
+  X(89, "lgamma_u35_f64", U64, gamma64::LgammaU10)
 
 #define SLEEFCU_BATCH_NAME(c, name, kind, F) name,
 static const char *kNames[] = {SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_NAME)};
@@ -234,7 +239,7 @@ const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin",   "cos",   "tan",   "sincos", "
                                           "atan2", "exp",   "log",   "pow",    "fmod",  "remainder",
                                           "log1p", "tanh",  "erf",   "exp2",   "exp10", "expm1", "log2",
                                           "log10", "cbrt",  "sinh",  "cosh",   "asinh", "acosh", "atanh",
-                                          "erfc"};
+                                          "erfc",  "tgamma", "lgamma"};
 const char *kTypeNames[4] = {"f64", "f32", "bf16", "f16"};
 
 int code_of(const sleefcu_batch_item &it) {

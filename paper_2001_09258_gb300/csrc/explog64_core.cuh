@@ -96,6 +96,19 @@ __device__ __forceinline__ d2 expk_s(d2 Y, double &k) {
   return add_d2_d(s, v);
 }
 
+// e^Y for a DD Y (the exponential inside pow, Section 5.7): overflow to
+// +inf, underflow with subnormals rounded once
+__device__ __forceinline__ double expk(d2 Y) {
+  bool inr = (bits(Y.x) & ABS64) <= B746;
+  double yh = inr ? Y.x : 0.0, yl = inr ? Y.y : 0.0;
+  double k;
+  d2 s = expk_s(D2(yh, yl), k);
+  s = add_d_d2_fast(1.0, s);
+  double y = scale2(__dadd_rn(s.x, s.y), int_of(k));
+  if (!inr) y = (bits(Y.x) >> 63) ? 0.0 : from_bits(INF);
+  return y;
+}
+
 // log of a DD a > 0 with a finite head: a = m 2^e, m in [0.75, 1.5) (heads
 // below DBL_MIN scaled by 2^64 first); returns log m = z + z^3 P(z^2) as a DD
 // with z = 2(m-1)/(m+1) in DD (Section 5.5 on a DD argument)
@@ -126,6 +139,27 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   double t = __dmul_rn(z, z);
   e = ex - off;
   return __fma_rn(__dmul_rn(z, t), poly(t, kLogU35), z);
+}
+
+// log of a DD y > 0 with the 11-term DD polynomial of pow's logarithm
+// (about 2^-66 relative): m in [0.75, 1.5) from the head, z = 2(m-1)/(m+1)
+// in DD
+__device__ __forceinline__ d2 logk_dd(d2 y) {
+  int off = 0;
+  if (y.x < 0x1p-1022) { y = scale_d2(y, 0x1p64); off = 64; }
+  int ex = (int)(bits(y.x) >> 52) - 1023;
+  d2 m = scale_d2(y, pow2_any(-ex));
+  if (m.x >= 1.5) { m = scale_d2(m, 0.5); ex++; }
+  d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
+  d2 z = div_d2d2(num, add_d_d2(1.0, m));
+  d2 t = sqr_d2(z);
+  double q = poly(t.x, kPowLog);
+  d2 w = add_d2_d_fast(D2(PL_C1H, PL_C1L), __dmul_rn(t.x, q));
+  w = mul_d2d2(t, w);
+  w = mul_d2d2(z, w);
+  d2 lm = add_d2d2_fast(z, w);
+  double ed = dbl_of(ex - off);
+  return add_d2d2(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), lm);
 }
 
 }  // namespace explog64

@@ -109,16 +109,6 @@ __device__ __forceinline__ d2 logk(uint64_t a) {
   double ed = dbl_of(e);
   return add_d2d2_fast(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), lm);
 }
-__device__ __forceinline__ double expk(d2 Y) {
-  bool inr = (bits(Y.x) & ABS64) <= B746;
-  double yh = inr ? Y.x : 0.0, yl = inr ? Y.y : 0.0;
-  double k;
-  d2 s = expk_s(D2(yh, yl), k);
-  s = add_d_d2_fast(1.0, s);
-  double y = scale2(__dadd_rn(s.x, s.y), int_of(k));
-  if (!inr) y = (bits(Y.x) >> 63) ? 0.0 : from_bits(INF);
-  return y;
-}
 
 struct PowU10 {
   __device__ double operator()(double x, double y) const {

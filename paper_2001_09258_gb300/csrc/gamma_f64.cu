@@ -1,0 +1,175 @@
+// FP64 tgamma and lgamma (u10; the u35 entry points run the same kernels)
+// for sm_103a.  The paper lists both in the library without their steps;
+// the design, as in the oracle:
+//   y >= 8           Stirling: (y - 1/2) log y - y + log(2 pi)/2 + G(1/y^2)/y
+//                    with the DD logarithm of pow (Section 5.7)
+//   1.75 <= y < 2.5  lgamma(2 + e) = e (c1 + e (c2 + e P(e))), e = y - 2
+//   1.25 <= y < 1.75 lgamma(1.5 + u) = c0 + u (c1 + u (c2 + u P(u)))
+//   0.5 <= y < 1.25  lgamma(y + 1) - log y with those polynomials
+//   otherwise        lgamma(y + n) - log(y (y+1) ... (y+n-1)), y + n in [8, 9)
+//   y < 0            log pi - log|sin(pi y)| - lgamma(1 - y), sin(pi y) from
+//                    y reduced exactly to [-1/2, 1/2]
+// tgamma = sign * exp(L) with L the DD log-gamma.  Lanes are grouped by path
+// in sorted tiles (the shift path runs a loop of up to seven DD products).
+#include "explog64_core.cuh"
+
+namespace sleefcu {
+namespace gamma64 {
+using namespace explog64;
+
+constexpr double LOG2PI_H = 0x1.d67f1c864beb5p-1, LOG2PI_L = -0x1.65b5a1b7ff5dfp-55;   // log(2 pi)/2
+constexpr double LOGPI_H = 0x1.250d048e7a1bdp+0, LOGPI_L = 0x1.7abf2ad8d5088p-57;      // log(pi)
+constexpr double PI_H = 0x1.921fb54442d18p+1, PI_L = 0x1.1a62633145c07p-53;
+constexpr uint64_t SIGN = 0x8000000000000000ull;
+
+static __constant__ double kLgR2H[4] = {0x1.b0ee6072093cep-2, 0x1.6c58518ef209cp-58, 0x1.4a34cc4a60fa6p-2, 0x1.1b98b7d24eb82p-56};
+static __constant__ double kLgR2P[16] = {
+    -0x1.13e001a557606p-4, 0x1.51322ac7d846dp-6, -0x1.e404fc218fc23p-8, 0x1.7add6eadbd405p-9,
+    -0x1.38ac5c2b8a199p-10, 0x1.0b36af7f23772p-11, -0x1.d3fd4cdaf22e0p-13, 0x1.a127b9082ca84p-14,
+    -0x1.78de521792e56p-15, 0x1.580b6a9b7953fp-16, -0x1.3cb65d569461dp-17, 0x1.25e70a4f871bep-18,
+    -0x1.139ba270fa662p-19, 0x1.ffad5d0754437p-21, -0x1.99a8f419f8596p-22, 0x1.7da6d390ec3f8p-24};
+static __constant__ double kLgMH[6] = {
+    -0x1.eeb95b094c191p-4, -0x1.34022180247c2p-58, 0x1.2aed059bd608ap-5, 0x1.7e1a96f7c7ed0p-63,
+    0x1.de9e64df22ef3p-2, -0x1.b1d5ff59dcc8fp-56};
+static __constant__ double kLgMP[15] = {
+    -0x1.1ae55b180726bp-3, 0x1.e0f840dad650ap-5, -0x1.da59d5374aed9p-6, 0x1.f9ca39da28ed7p-7,
+    -0x1.1a8ba4f054ba6p-7, 0x1.456f1b2745dc9p-8, -0x1.7edb81cde7f7cp-9, 0x1.c973218d36f11p-10,
+    -0x1.148a003bbd58dp-10, 0x1.51884c3b797c0p-11, -0x1.9f11b5ad1c5d2p-12, 0x1.fea4040bd8d69p-13,
+    -0x1.3d5aec9602328p-13, 0x1.bf0b984ee3abdp-14, -0x1.1a86a63641821p-14};
+static __constant__ double kLgSt[10] = {
+    0x1.5555555555555p-4, -0x1.6c16c16c16c16p-9, 0x1.a01a01a0196bap-11, -0x1.381381362b216p-11,
+    0x1.b951df87db260p-11, -0x1.f6a98a1bab42ap-10, 0x1.a3e150e3f70bdp-8, -0x1.dee553034d0abp-6,
+    0x1.490abb645435cp-3, -0x1.7031193624fc5p-1};
+static __constant__ double kSpH[2] = {-0x1.4abbce625be53p+2, 0x1.05511c684d1cbp-52};
+static __constant__ double kSpP[11] = {
+    0x1.466bc6775aae2p+1, -0x1.32d2cce62bddep-1, 0x1.50783487f6d9cp-4, -0x1.e3074fec25b1dp-8,
+    0x1.e8f4422d6f029p-12, -0x1.6fb6226ceb4fdp-16, 0x1.b1dd7b5e6be80p-21, -0x1.5249d9e04752dp-24,
+    0x1.46d5e635ea9dep-23, -0x1.f9b2ef7ed3d1ep-23, 0x1.563183599af6cp-23};
+
+__device__ __forceinline__ d2 neg(d2 a) { return D2(-a.x, -a.y); }
+
+// lgamma(2 + e), -0.25 <= e < 0.5
+__device__ __forceinline__ d2 lg_r2(d2 e) {
+  double p = poly_p<16>(e.x, kLgR2P);
+  d2 in = add_d2_d(D2(kLgR2H[2], kLgR2H[3]), __dmul_rn(e.x, p));
+  in = add_d2d2(D2(kLgR2H[0], kLgR2H[1]), mul_d2d2(in, e));
+  return mul_d2d2(in, e);
+}
+// lgamma(1.5 + u), -0.25 <= u < 0.25
+__device__ __forceinline__ d2 lg_m(d2 u) {
+  double p = poly_p<15>(u.x, kLgMP);
+  d2 in = add_d2_d(D2(kLgMH[4], kLgMH[5]), __dmul_rn(u.x, p));
+  in = add_d2d2(D2(kLgMH[2], kLgMH[3]), mul_d2d2(in, u));
+  return add_d2d2(D2(kLgMH[0], kLgMH[1]), mul_d2d2(in, u));
+}
+// Stirling's form, DD y >= 8
+__device__ __forceinline__ d2 lg_stirling(d2 y) {
+  d2 ly = logk_dd(y);
+  d2 r = mul_d2d2(add_d2_d(y, -0.5), ly);
+  r = add_d2d2(r, neg(y));
+  r = add_d2d2(r, D2(LOG2PI_H, LOG2PI_L));
+  double w = __ddiv_rn(1.0, __dmul_rn(y.x, y.x));
+  return add_d2_d(r, __ddiv_rn(poly(w, kLgSt), y.x));
+}
+// lgamma of a DD y > 0
+__device__ __forceinline__ d2 lgamma_pos(d2 y) {
+  if (y.x >= 8.0) return lg_stirling(y);
+  if (y.x >= 1.75 && y.x < 2.5) return lg_r2(norm_d2(add_d2_d(y, -2.0)));
+  if (y.x >= 1.25 && y.x < 1.75) return lg_m(norm_d2(add_d2_d(y, -1.5)));
+  if (y.x >= 0.5 && y.x < 1.25) {
+    d2 r = y.x < 0.75 ? lg_m(norm_d2(add_d2_d(y, -0.5))) : lg_r2(norm_d2(add_d2_d(y, -1.0)));
+    return add_d2d2(r, neg(logk_dd(y)));
+  }
+  int n = (int)__dsub_rn(8.0, floor(y.x));           // y + n in [8, 9)
+  d2 P = y, z = y;
+  for (int i = 1; i < n; i++) {
+    z = add_d2_d(z, 1.0);
+    P = mul_d2d2(P, z);
+  }
+  d2 s = lg_stirling(add_d2_d(y, (double)n));
+  return add_d2d2(s, neg(logk_dd(P)));
+}
+// sin(pi x) as a DD, |x| < 2^52
+__device__ __forceinline__ d2 sinpi_dd(double x) {
+  double r = __dsub_rn(x, __dmul_rn(2.0, rint(__dmul_rn(0.5, x))));
+  double s = r > 0.5 ? __dsub_rn(1.0, r) : (r < -0.5 ? __dsub_rn(-1.0, r) : r);
+  d2 T = mul_dd(s, s);
+  double p = poly_p<11>(T.x, kSpP);
+  d2 in = add_d2_d(D2(kSpH[0], kSpH[1]), __dmul_rn(T.x, p));
+  in = add_d2d2(D2(PI_H, PI_L), mul_d2d2(T, in));
+  return mul_d2_d(in, s);
+}
+// log-gamma as a DD, sign of gamma (finite x, not a non-positive integer)
+__device__ __forceinline__ d2 lgamma_dd(double x, int &sign) {
+  sign = 1;
+  if (x > 0.0) return lgamma_pos(D2(x, 0.0));
+  d2 sp = sinpi_dd(x);
+  bool negs = sp.x < 0.0;
+  sign = negs ? -1 : 1;
+  d2 l = logk_dd(D2(fabs(sp.x), negs ? -sp.y : sp.y));
+  d2 r = add_d2d2(D2(LOGPI_H, LOGPI_L), neg(l));
+  d2 g = lgamma_pos(add_dd(1.0, -x));
+  return add_d2d2(r, neg(g));
+}
+// path class for the sorted tiles
+__device__ __forceinline__ int gamma_cls(double x) {
+  double a = fabs(x);
+  if (!(a <= 0x1p1015) || a == 0.0) return 7;
+  if (x < 0.0) return a >= 7.0 ? 5 : 6;
+  if (x >= 8.0) return 0;
+  if (x >= 1.75 && x < 2.5) return 1;
+  if (x >= 1.25 && x < 1.75) return 2;
+  if (x >= 0.5 && x < 1.25) return 3;
+  return 4;
+}
+__device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (all |x| >= 2^52 are)
+  return x < 0.0 && (fabs(x) >= 0x1p52 || x == rint(x));
+}
+
+struct LgammaU10 {
+  static constexpr int NCLS = 8;
+  __device__ static int cls(double x) { return gamma_cls(x); }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    if (is_nan_b(bx)) return from_bits(QNAN64);
+    if ((bx & ABS64) == INF || x == 0.0 || neg_int(x) || x > 0x1p1015) return from_bits(INF);
+    int sign;
+    d2 L = lgamma_dd(x, sign);
+    double y = __dadd_rn(L.x, L.y);
+    if ((bits(y) & ABS64) >= INF) y = from_bits(INF);
+    return canon(y);
+  }
+};
+struct TgammaU10 {
+  static constexpr int NCLS = 8;
+  __device__ static int cls(double x) { return gamma_cls(x); }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    if (is_nan_b(bx) || bx == (INF | SIGN) || neg_int(x)) return from_bits(QNAN64);
+    if (x == 0.0) return from_bits(INF | (bx & SIGN));
+    if (x > 172.0) return from_bits(INF);
+    if (x < -190.0) return sinpi_dd(x).x < 0.0 ? -0.0 : 0.0;
+    int sign;
+    d2 L = lgamma_dd(x, sign);
+    double y = expk(L);
+    return canon(sign < 0 ? -y : y);
+  }
+};
+
+}  // namespace gamma64
+}  // namespace sleefcu
+
+#ifndef SLEEFCU_FUNCTORS_ONLY
+using namespace sleefcu;
+
+#define SORTED64(NAME, F)                                                                   \
+  extern "C" sleefcu_status sleefcu_##NAME(const double *x, double *out, size_t n,          \
+                                           sleefcu_stream s) {                              \
+    return launch_sorted64<gamma64::F>("sleefcu_" #NAME, x, out, n, s);                     \
+  }
+SORTED64(tgamma_u10_f64, TgammaU10)
+SORTED64(tgamma_u35_f64, TgammaU10)
+SORTED64(lgamma_u10_f64, LgammaU10)
+SORTED64(lgamma_u35_f64, LgammaU10)
+#undef SORTED64
+#endif  // SLEEFCU_FUNCTORS_ONLY

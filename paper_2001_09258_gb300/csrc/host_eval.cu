@@ -116,6 +116,10 @@ const Entry kEntries[] = {
   HE_U(acosh_u35_f64, double, 8)
   HE_U(atanh_u10_f64, double, 8)
   HE_U(atanh_u35_f64, double, 8)
+  HE_U(tgamma_u10_f64, double, 8)
+  HE_U(tgamma_u35_f64, double, 8)
+  HE_U(lgamma_u10_f64, double, 8)
+  HE_U(lgamma_u35_f64, double, 8)
   HE_U(erfc_u10_f64, double, 8)
   HE_U(erfc_u35_f64, double, 8)
 };
@@ -127,7 +131,7 @@ const char *kFn[SLEEFCU_FN_COUNT] = {"sin",   "cos",   "tan",   "sincos", "asin"
                                      "atan2", "exp",   "log",   "pow",    "fmod",  "remainder",
                                      "log1p", "tanh",  "erf",   "exp2",   "exp10", "expm1", "log2",
                                      "log10", "cbrt",  "sinh",  "cosh",   "asinh", "acosh", "atanh",
-                                     "erfc"};
+                                     "erfc",  "tgamma", "lgamma"};
 const char *kType[4] = {"f64", "f32", "bf16", "f16"};
 
 const Entry *find(const sleefcu_batch_item &it) {

@@ -90,6 +90,16 @@ OPS = {
     "erfc_u10_f64": {"a": 56, "f": 104, "fneg": 111, "g": 101, "sat": 0},
     "erfc_u35_f64": {"a": 56, "f": 104, "fneg": 111, "g": 101, "sat": 0},
     "erf_u35_f64": {"a": 17, "f": 52, "g": 0, "sat": 0},
+    # tgamma/lgamma by path class: "st" x >= 8 (Stirling with the DD log of
+    # pow, 119), "r2" [1.75, 2.5) (52), "m" [1.25, 1.75) (59), "lo" [0.5, 1.25)
+    # (polynomial and a DD log, 136), "sh" other x > 0 (shift: up to seven DD
+    # products, a DD log and Stirling, ~240), "rs" x < -7 (reflection: exact
+    # sin(pi x) 42, DD log, Stirling on 1 - x, 253), "rn" -7 <= x < 0 (~330),
+    # "sp" specials; tgamma adds the DD exponential (51)
+    "lgamma_u10_f64": {"st": 119, "r2": 52, "m": 59, "lo": 136, "sh": 240, "rs": 253, "rn": 330, "sp": 0},
+    "lgamma_u35_f64": {"st": 119, "r2": 52, "m": 59, "lo": 136, "sh": 240, "rs": 253, "rn": 330, "sp": 0},
+    "tgamma_u10_f64": {"st": 170, "r2": 103, "m": 110, "lo": 187, "sh": 291, "rs": 304, "rn": 381, "sp": 0},
+    "tgamma_u35_f64": {"st": 170, "r2": 103, "m": 110, "lo": 187, "sh": 291, "rs": 304, "rn": 381, "sp": 0},
 }
 
 
@@ -134,6 +144,22 @@ def path_mix(name, x, y=None, steps=None):
             out["fneg"] = int((f & ~(x > 0)).sum())
         else:
             out["f"] = int(f.sum())
+        return out
+    if fn in ("tgamma", "lgamma"):
+        fin = np.isfinite(x) & (x != 0) & ~((x < 0) & (x == np.rint(x)))
+        big = ax > 2.0 ** 1015
+        pos, neg = fin & (x > 0) & ~big, fin & (x < 0)
+        st = pos & (x >= 8)
+        r2 = pos & (x >= 1.75) & (x < 2.5)
+        m = pos & (x >= 1.25) & (x < 1.75)
+        lo = pos & (x >= 0.5) & (x < 1.25)
+        sh = pos & ~st & ~r2 & ~m & ~lo
+        rs, rn = neg & (x < -7), neg & (x >= -7)
+        if fn == "tgamma":
+            rs, rn = rs & (x >= -190), rn
+        c = {"st": st, "r2": r2, "m": m, "lo": lo, "sh": sh, "rs": rs, "rn": rn}
+        out = {k: int(v.sum()) for k, v in c.items()}
+        out["sp"] = int(ax.size - sum(out.values()))
         return out
     if fn in ("asinh", "acosh"):
         big = int((ax > 2.0 ** 500).sum())

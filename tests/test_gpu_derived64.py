@@ -12,13 +12,15 @@ from paper_2001_09258_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 FNS = ("exp2", "exp10", "expm1", "log2", "log10", "log1p", "cbrt", "sinh", "cosh", "tanh",
-       "asinh", "acosh", "atanh", "erf", "erfc")
+       "asinh", "acosh", "atanh", "erf", "erfc", "tgamma", "lgamma")
 NAMES = [f"{fn}_{a}_f64" for fn in FNS for a in ("u10", "u35")]
 EDGE = [0.0, -0.0, math.inf, -math.inf, math.nan, 1.0, -1.0, 2.0, -2.0, 5e-324, -5e-324,
         2.2250738585072014e-308, 1.7976931348623157e308, -1.7976931348623157e308, 1024.0, -1075.0,
         -1074.5, 308.25, 308.26, -323.6, -324.0, 709.78, 709.79, 710.47, 710.48, 711.0, -40.0, -39.9,
         19.0, 20.0, 20.5, 22.0, 22.1, 1e-30, -1e-30, 2.0 ** -28, 2.0 ** 500, 0.999999, 1.000001, 8.0, 27.0,
-        4.0, -4.0, 6.0, -6.0, 5.99999, 7.99999, -8.0, 27.3, 27.5, 27.50001, -27.5]
+        4.0, -4.0, 6.0, -6.0, 5.99999, 7.99999, -8.0, 27.3, 27.5, 27.50001, -27.5,
+        -0.5, -1.5, -2.457, -2.747, -7.0, -7.5, -190.5, -200.5, 0.5, 0.75, 1.25, 1.75, 2.5, 171.62, 171.63,
+        2.5e305, 2.6e305, 1e-310, -1e-310]
 
 
 def check(name, x, **kw):
@@ -36,7 +38,7 @@ def test_bitexact_mixed(name):
 
 
 @pytest.mark.parametrize("name", ["expm1_u10_f64", "cbrt_u10_f64", "sinh_u35_f64", "acosh_u10_f64",
-                                  "erfc_u10_f64"])
+                                  "erfc_u10_f64", "tgamma_u10_f64", "lgamma_u10_f64"])
 @pytest.mark.parametrize("n", [1, 3, 33, 1023, 1025, 4097])
 def test_ragged(name, n):
     check(name, I.workload(name.split("_")[0], n, key=f"rgd{n}"))
