@@ -160,6 +160,13 @@ static inline ff_t ffdiv_f2_f2_f2(ff_t n, ff_t d) {
   return ff(q, r * t);
 }
 static inline ff_t ffrec_f2_f(float d) { float t = 1.0f / d; return ff(t, t * fmaf(-t, d, 1.0f)); }
+/* 1 / FF */
+static inline ff_t ffrec_f2_f2(ff_t d) {
+  float t = 1.0f / d.x;
+  float r = fmaf(-t, d.x, 1.0f);
+  r = fmaf(-t, d.y, r);
+  return ff(t, r * t);
+}
 static inline ff_t ffsqrt_f2_f2(ff_t d) {
   float h = sqrtf(d.x);
   float r = fmaf(-h, h, d.x) + d.y;

@@ -236,3 +236,118 @@ float oracle_erf_u35_f32(float x) {
   if (isnan(x)) y = NAN;
   return canonf(y);
 }
+
+/* ---------------- cores shared with the other FP32 functions ---------------- */
+static const float POWLOGF[5] = { POWLOGF_COEFFS };
+
+float oracle_scale2f(float y, int k) { return scale2f(y, k); }
+
+/* 2^k (1 + r + rl) with the 1-ULP polynomial, |r| <= ln2/2 */
+float oracle_expf_tail_u10(float r, float rl, float k) {
+  float w = fmaf(r * r, poly_f(r, EXPF_U10, 6), rl);
+  ff_t o = ffadd_f2_f_f(1.0f, r);
+  return scale2f(o.x + (o.y + w), (int)k);
+}
+
+/* e^(a.x + a.y) = o 2^k with o an FF pair in [0.7, 1.42], for |a.x| <= 160 */
+ff_t oracle_expf_parts(ff_t a, float *kp) {
+  float k = rintf(a.x * R_LN2F);
+  float h = fmaf(k, -L2AF, a.x);
+  ff_t r = ffadd2_f2_f_f(h, fmaf(k, -L2BF, a.y));
+  float w = fmaf(r.x * r.x, poly_f(r.x, EXPF_U10, 6), r.y);
+  ff_t o = ffadd_f2_f_f(1.0f, r.x);
+  *kp = k;
+  return ff(o.x, o.y + w);
+}
+
+/* e^r - 1 as an FF pair and k with a = k ln2 + r, |a| <= 160 */
+ff_t oracle_expm1f_s(float a, float *kp) {
+  float k = rintf(a * R_LN2F);
+  float h = fmaf(k, -L2AF, a);
+  float r = fmaf(k, -L2BF, h);
+  float rl = fmaf(k, -L2BF, h - r);
+  ff_t rr = ff(r, rl);
+  ff_t q = ffscale_f2_f2_f(ffsqu_f2_f2(rr), 0.5f);
+  float v = ((r * r) * r) * poly_f(r, EXPM1F, 5);
+  ff_t s = ffadd2_f2_f2_f2(rr, q);
+  *kp = k;
+  return ffadd2_f2_f2_f(s, v);
+}
+
+/* FF argument a > 0 (finite): log m as an FF pair with a = m 2^e, m in
+ * [0.75, 1.5) (the u10 core without e ln2) */
+ff_t oracle_logmf_u10(ff_t a, int *ep) {
+  int e;
+  float m = logf_reduce(a.x, &e);
+  float ml = ldexpf(a.y, -e);
+  ff_t num = ffscale_f2_f2_f(ffadd2_f2_f_f(m - 1.0f, ml), 2.0f);
+  ff_t den = ffadd2_f2_f_f2(1.0f, ff(m, ml));
+  ff_t z = ffdiv_f2_f2_f2(num, den);
+  float t = z.x * z.x;
+  float corr = (z.x * t) * poly_f(t, LOGF_U10, 4);
+  *ep = e;
+  return ffadd_f2_f2_f(z, corr);
+}
+
+/* log of an FF a > 0 as an FF pair: e ln2 + log m with the FF core */
+ff_t oracle_logf_ff(ff_t a) {
+  int e;
+  ff_t lm = oracle_logmf_u10(a, &e);
+  float ed = (float)e;
+  return ffadd2_f2_f2_f2(ff(ed * L2HF, ed * L2LF), lm);
+}
+
+/* log of an FF a > 0 to about 2^-40: the internal log of powf (first
+ * coefficient FF, the correction in FF products) */
+ff_t oracle_logkf(ff_t a) {
+  int e;
+  float m = logf_reduce(a.x, &e);
+  float ml = ldexpf(a.y, -e);
+  ff_t num = ffscale_f2_f2_f(ffadd2_f2_f_f(m - 1.0f, ml), 2.0f);
+  ff_t z = ffdiv_f2_f2_f2(num, ffadd2_f2_f_f2(1.0f, ff(m, ml)));
+  ff_t t = ffsqu_f2_f2(z);
+  float q = poly_f(t.x, POWLOGF, 5);
+  ff_t w = ffadd_f2_f2_f(ff(POWLOGF_C1H, POWLOGF_C1L), t.x * q);
+  w = ffmul_f2_f2_f2(t, w);
+  w = ffmul_f2_f2_f2(z, w);
+  ff_t lm = ffadd_f2_f2_f2(z, w);
+  float ed = (float)e;
+  return ffadd2_f2_f2_f2(ff(ed * L2HF, ed * L2LF), lm);
+}
+
+/* L(x) = log(erfc(x) e^(x^2)) as an FF pair, 1 <= x <= 10.1: c0 + u (c1 +
+ * u P(u)) about 2.5 (x < 3.95) or 7, c0 and c1 FF pairs */
+static const float ERFCF_B[14] = { ERFCF_B_COEFFS };
+static const float ERFCF_BH[4] = { ERFCF_B_HEAD };
+static const float ERFCF_C[11] = { ERFCF_C_COEFFS };
+static const float ERFCF_CH[4] = { ERFCF_C_HEAD };
+ff_t oracle_erfcf_L(float x) {
+  int tail = x >= 3.95f;
+  const float *h = tail ? ERFCF_CH : ERFCF_BH;
+  float u = x - (tail ? 7.0f : 2.5f);
+  float p = tail ? poly_f(u, ERFCF_C, 11) : poly_f(u, ERFCF_B, 14);
+  ff_t in = ffadd2_f2_f2_f(ff(h[2], h[3]), u * p);
+  return ffadd2_f2_f2_f2(ff(h[0], h[1]), ffmul_f2_f2_f(in, u));
+}
+
+/* erf(a) for 0 <= a < 1 as an FF pair with three FF levels, C0 + T (C1 + T
+ * (C2 + t P(t))), T = a^2 exact (erfc's 1 - erf near 1) */
+static const float ERFCF_AH[6] = { ERFCF_A_HEAD };
+static const float ERFCF_A[6] = { ERFCF_A_COEFFS };
+ff_t oracle_erfcf_a(float a) {
+  ff_t T = ffmul_f2_f_f(a, a);
+  float p = poly_f(T.x, ERFCF_A, 6);
+  ff_t in = ffadd2_f2_f2_f(ff(ERFCF_AH[4], ERFCF_AH[5]), T.x * p);
+  in = ffadd2_f2_f2_f2(ff(ERFCF_AH[2], ERFCF_AH[3]), ffmul_f2_f2_f2(T, in));
+  in = ffadd2_f2_f2_f2(ff(ERFCF_AH[0], ERFCF_AH[1]), ffmul_f2_f2_f2(T, in));
+  return ffmul_f2_f2_f(in, a);
+}
+
+/* erf(a) for 0 <= a < 1 as an FF pair (the u10 kernel) */
+ff_t oracle_erff_a(float a) {
+  ff_t t = ffmul_f2_f_f(a, a);
+  float p = poly_f(t.x, ERFF_A + 1, 6);
+  ff_t w1 = ffadd_f2_f_f(ERFF_A[0], t.x * p);
+  ff_t w = ffadd_f2_f2_f2(ff(ERFF_A_C1H, ERFF_A_C1L), ffmul_f2_f2_f2(t, w1));
+  return ffmul_f2_f2_f(w, a);
+}

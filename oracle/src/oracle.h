@@ -80,6 +80,52 @@ float oracle_sin_u10_f32(float);
 float oracle_sin_u35_f32(float);
 float oracle_cos_u10_f32(float);
 float oracle_cos_u35_f32(float);
+float oracle_exp2_u10_f32(float);
+float oracle_exp2_u35_f32(float);
+float oracle_exp10_u10_f32(float);
+float oracle_exp10_u35_f32(float);
+float oracle_expm1_u10_f32(float);
+float oracle_expm1_u35_f32(float);
+float oracle_log2_u10_f32(float);
+float oracle_log2_u35_f32(float);
+float oracle_log10_u10_f32(float);
+float oracle_log10_u35_f32(float);
+float oracle_sinh_u10_f32(float);
+float oracle_sinh_u35_f32(float);
+float oracle_cosh_u10_f32(float);
+float oracle_cosh_u35_f32(float);
+float oracle_asinh_u10_f32(float);
+float oracle_asinh_u35_f32(float);
+float oracle_acosh_u10_f32(float);
+float oracle_acosh_u35_f32(float);
+float oracle_atanh_u10_f32(float);
+float oracle_atanh_u35_f32(float);
+float oracle_cbrt_u10_f32(float);
+float oracle_cbrt_u35_f32(float);
+float oracle_erfc_u10_f32(float);
+float oracle_erfc_u35_f32(float);
+float oracle_pow_u10_f32(float, float);
+float oracle_pow_u35_f32(float, float);
+float oracle_tan_u10_f32(float);
+float oracle_tan_u35_f32(float);
+float oracle_asin_u10_f32(float);
+float oracle_asin_u35_f32(float);
+float oracle_acos_u10_f32(float);
+float oracle_acos_u35_f32(float);
+float oracle_atan_u10_f32(float);
+float oracle_atan_u35_f32(float);
+float oracle_tgamma_u10_f32(float);
+float oracle_tgamma_u35_f32(float);
+float oracle_lgamma_u10_f32(float);
+float oracle_lgamma_u35_f32(float);
+float oracle_atan2_u10_f32(float, float);
+float oracle_atan2_u35_f32(float, float);
+float oracle_fmod_u10_f32(float, float);
+float oracle_fmod_u35_f32(float, float);
+float oracle_remainder_u10_f32(float, float);
+float oracle_remainder_u35_f32(float, float);
+void oracle_sincos_u10_f32(float, float *, float *);
+void oracle_sincos_u35_f32(float, float *, float *);
 float oracle_exp_u10_f32(float);
 float oracle_exp_u35_f32(float);
 float oracle_log_u10_f32(float);

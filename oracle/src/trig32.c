@@ -153,3 +153,76 @@ void oracle_ph_reduce_f32(float x, int *q, float *hi, float *lo) {
   *hi = r.x;
   *lo = r.y;
 }
+
+/* ---------------- tan, sincos (quarter-turn reduction) ----------------
+ * s = x - Q pi/2 in [-pi/4, pi/4] with Q = rint(x 2/pi) (Cody-Waite levels
+ * as above; Payne-Hanek's quarter turns beyond 2^20).  tan s = s + s t (c1 +
+ * t P(t)) with the leading products in FF (u10), -1/tan s for odd Q;
+ * sincos from one reduction: sin s as above and cos s = 1 - t/2 + t^2 C(t)
+ * (FF for u10), swapped and signed by Q mod 4. */
+#define R_2_PIF 0x1.45f306p-1f
+static const float TANF_P10[8] = { TANF_U10_COEFFS };
+static const float TANF_P35[8] = { TANF_U35_COEFFS };
+static const float COSF_P[3] = { COSF_U10_COEFFS };
+
+static ff_t reduce_quarterf(float x, int *q) {
+  float ax = fabsf(x);
+  if (ax < 0x1p20f) {
+    float Q = rintf(x * R_2_PIF);
+    *q = (int)((int32_t)Q & 3);
+    return ax < 125.0f ? cw1f(x, Q) : cw2f(x, Q);
+  }
+  ff_t r = oracle_ph_reduce_ff(x, q);
+  *q &= 3;
+  return r;
+}
+
+float oracle_tan_u10_f32(float x) {
+  int q;
+  ff_t s = reduce_quarterf(x, &q);
+  ff_t t = ffsqu_f2_f2(s);
+  float p = poly_f(t.x, TANF_P10, 8);
+  ff_t w = ffadd_f2_f2_f(ff(TANF_U10_C1H, TANF_U10_C1L), t.x * p);
+  w = ffmul_f2_f2_f2(s, ffmul_f2_f2_f2(t, w));
+  ff_t r = ffadd_f2_f2_f2(s, w);
+  if (q & 1) r = ffdiv_f2_f2_f2(ff(-1.0f, 0.0f), r);
+  float y = r.x + r.y;
+  if (x == 0) y = x;
+  return canonf(y);
+}
+float oracle_tan_u35_f32(float x) {
+  int q;
+  ff_t s = reduce_quarterf(x, &q);
+  float s1 = s.x + s.y, t = s1 * s1;
+  float r = fmaf(s1 * t, poly_f(t, TANF_P35, 8), s1);
+  if (q & 1) r = -1.0f / r;
+  if (x == 0) r = x;
+  return canonf(r);
+}
+
+static void sincos_out(int q, float sn, float cs, float x, float *os, float *oc) {
+  float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;
+  if (q == 1 || q == 2) b = -b;
+  if (q & 2) a = -a;
+  if (x == 0) a = x;
+  *os = canonf(a);
+  *oc = canonf(b);
+}
+void oracle_sincos_u10_f32(float x, float *os, float *oc) {
+  int q;
+  ff_t s = reduce_quarterf(x, &q);
+  float sn = sinf_poly_u10(s);
+  ff_t t = ffsqu_f2_f2(s);
+  float v = (t.x * t.x) * poly_f(t.x, COSF_P, 3);
+  ff_t c = ffadd2_f2_f_f2(1.0f, ffscale_f2_f2_f(t, -0.5f));
+  c = ffadd_f2_f2_f(c, v);
+  sincos_out(q, sn, c.x + c.y, x, os, oc);
+}
+void oracle_sincos_u35_f32(float x, float *os, float *oc) {
+  int q;
+  ff_t s = reduce_quarterf(x, &q);
+  float s1 = s.x + s.y, t = s1 * s1;
+  float sn = sinf_poly_u35(s1);
+  float cs = fmaf(t * t, poly_f(t, COSF_P, 3), fmaf(t, -0.5f, 1.0f));
+  sincos_out(q, sn, cs, x, os, oc);
+}
