@@ -240,6 +240,73 @@ sleefcu_status sleefcu_tanh_u35_f32(const float *x, float *out, size_t n, sleefc
 sleefcu_status sleefcu_erf_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
 sleefcu_status sleefcu_erf_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
 
+/* The rest of the FP32 family: every FP64 function above also in binary32,
+ * float-float where the 1-ULP bound needs it, no FP64 anywhere.  tan and
+ * sincos reduce to quarter turns (Cody-Waite, the FF Payne-Hanek reduction
+ * beyond 2^20) with one shared reduction for sincos; asin/acos/atan/atan2,
+ * exp2/exp10/expm1, log2/log10, pow, cbrt, the hyperbolics and their
+ * inverses, erfc, tgamma/lgamma follow the FP64 designs on the binary32
+ * cores; fmod/remainder are exact (the long division with FF remainders, at
+ * most 24 steps).  Special values as for FP64.  The u35 entry points of
+ * expm1, sinh, cosh, asinh, acosh, atanh, pow, erfc, tgamma, lgamma, fmod and
+ * remainder run the u10 algorithm. */
+sleefcu_status sleefcu_tan_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tan_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sincos_u10_f32(const float *x, float *out_sin, float *out_cos, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_sincos_u35_f32(const float *x, float *out_sin, float *out_cos, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_asin_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asin_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u10_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u35_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u10_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u35_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_fmod_u10_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_fmod_u35_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u10_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u35_f32(const float *x, const float *y, float *out, size_t n,
+                                   sleefcu_stream stream);
+sleefcu_status sleefcu_exp2_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp2_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tgamma_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_tgamma_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u10_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+
 /* ---------------- bf16 / f16 activation forms ----------------
  * x and out hold n 16-bit values (bf16 or IEEE binary16, as the suffix says).
  * Each element is converted exactly to binary32, evaluated with the FP32

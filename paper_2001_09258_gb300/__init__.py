@@ -32,9 +32,7 @@ FUNCS = {
     "sinh": "u", "cosh": "u", "asinh": "u", "acosh": "u", "atanh": "u", "erfc": "u",
     "tgamma": "u", "lgamma": "u",
 }
-PRECS = {fn: ("f64",) for fn in FUNCS}
-for _fn in ("sin", "cos", "exp", "log", "log1p", "tanh", "erf"):
-    PRECS[_fn] = ("f64", "f32")
+PRECS = {fn: ("f64", "f32") for fn in FUNCS}
 for _fn in ("erf", "tanh", "exp", "log1p"):
     PRECS[_fn] = PRECS[_fn] + ("bf16", "f16")
 ACCS = ("u10", "u35")

@@ -20,6 +20,7 @@
 #include "explog_f32.cu"
 #include "derived_f64.cu"
 #include "gamma_f64.cu"
+#include "derived_f32.cu"
 #undef SLEEFCU_FUNCTORS_ONLY
 
 #include <cstdio>
@@ -31,7 +32,7 @@
 namespace sleefcu {
 namespace batch {
 
-enum Kind { U64, B64, SC64, U32, BF, HF };
+enum Kind { U64, B64, SC64, U32, B32, SC32, BF, HF };
 
 // entry point table: code (= position), name, kind, functor
 #define SLEEFCU_BATCH_TABLE(X) \
@@ -124,7 +125,53 @@ enum Kind { U64, B64, SC64, U32, BF, HF };
   X(86, "tgamma_u10_f64", U64, gamma64::TgammaU10) \
   X(87, "tgamma_u35_f64", U64, gamma64::TgammaU10) \
   X(88, "lgamma_u10_f64", U64, gamma64::LgammaU10) \
-  X(89, "lgamma_u35_f64", U64, gamma64::LgammaU10)
+  X(89, "lgamma_u35_f64", U64, gamma64::LgammaU10) \
+  X(90, "tan_u10_f32", U32, derived32::TanU10) \
+  X(91, "tan_u35_f32", U32, derived32::TanU35) \
+  X(92, "sincos_u10_f32", SC32, derived32::SinCosU10) \
+  X(93, "sincos_u35_f32", SC32, derived32::SinCosU35) \
+  X(94, "asin_u10_f32", U32, derived32::AsinU10) \
+  X(95, "asin_u35_f32", U32, derived32::AsinU35) \
+  X(96, "acos_u10_f32", U32, derived32::AcosU10) \
+  X(97, "acos_u35_f32", U32, derived32::AcosU35) \
+  X(98, "atan_u10_f32", U32, derived32::AtanU10) \
+  X(99, "atan_u35_f32", U32, derived32::AtanU35) \
+  X(100, "atan2_u10_f32", B32, derived32::Atan2U10) \
+  X(101, "atan2_u35_f32", B32, derived32::Atan2U35) \
+  X(102, "exp2_u10_f32", U32, derived32::Exp2U10) \
+  X(103, "exp2_u35_f32", U32, derived32::Exp2U35) \
+  X(104, "exp10_u10_f32", U32, derived32::Exp10U10) \
+  X(105, "exp10_u35_f32", U32, derived32::Exp10U35) \
+  X(106, "expm1_u10_f32", U32, derived32::Expm1U10) \
+  X(107, "expm1_u35_f32", U32, derived32::Expm1U10) \
+  X(108, "log2_u10_f32", U32, derived32::Log2U10) \
+  X(109, "log2_u35_f32", U32, derived32::Log2U35) \
+  X(110, "log10_u10_f32", U32, derived32::Log10U10) \
+  X(111, "log10_u35_f32", U32, derived32::Log10U35) \
+  X(112, "pow_u10_f32", B32, derived32::PowU10) \
+  X(113, "pow_u35_f32", B32, derived32::PowU10) \
+  X(114, "cbrt_u10_f32", U32, derived32::CbrtU10) \
+  X(115, "cbrt_u35_f32", U32, derived32::CbrtU35) \
+  X(116, "sinh_u10_f32", U32, derived32::SinhU10) \
+  X(117, "sinh_u35_f32", U32, derived32::SinhU10) \
+  X(118, "cosh_u10_f32", U32, derived32::CoshU10) \
+  X(119, "cosh_u35_f32", U32, derived32::CoshU10) \
+  X(120, "asinh_u10_f32", U32, derived32::AsinhU10) \
+  X(121, "asinh_u35_f32", U32, derived32::AsinhU10) \
+  X(122, "acosh_u10_f32", U32, derived32::AcoshU10) \
+  X(123, "acosh_u35_f32", U32, derived32::AcoshU10) \
+  X(124, "atanh_u10_f32", U32, derived32::AtanhU10) \
+  X(125, "atanh_u35_f32", U32, derived32::AtanhU10) \
+  X(126, "erfc_u10_f32", U32, derived32::ErfcU10) \
+  X(127, "erfc_u35_f32", U32, derived32::ErfcU10) \
+  X(128, "fmod_u10_f32", B32, derived32::FmodF) \
+  X(129, "fmod_u35_f32", B32, derived32::FmodF) \
+  X(130, "remainder_u10_f32", B32, derived32::RemainderF) \
+  X(131, "remainder_u35_f32", B32, derived32::RemainderF) \
+  X(132, "tgamma_u10_f32", U32, derived32::TgammaU10) \
+  X(133, "tgamma_u35_f32", U32, derived32::TgammaU10) \
+  X(134, "lgamma_u10_f32", U32, derived32::LgammaU10) \
+  X(135, "lgamma_u35_f32", U32, derived32::LgammaU10)
 
 #define SLEEFCU_BATCH_NAME(c, name, kind, F) name,
 static const char *kNames[] = {SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_NAME)};
@@ -184,6 +231,14 @@ __device__ __forceinline__ void run(const Desc &D, long long b, long long e, int
     } else {
       for (long long i = b + tid; i < e; i += nt) o[i] = f(x[i]);
     }
+  } else if constexpr (K == B32) {
+    const float *x = (const float *)D.x, *y = (const float *)D.y;
+    float *o = (float *)D.out;
+    for (long long i = b + tid; i < e; i += nt) o[i] = f(x[i], y[i]);
+  } else if constexpr (K == SC32) {
+    const float *x = (const float *)D.x;
+    float *o = (float *)D.out, *o2 = (float *)D.out2;
+    for (long long i = b + tid; i < e; i += nt) f.dual(x[i], o[i], o2[i]);
   } else {
     const uint16_t *x = (const uint16_t *)D.x;
     uint16_t *o = (uint16_t *)D.out;

@@ -1,0 +1,982 @@
+// FP32 functions beyond sin, cos, exp, log, log1p, tanh and erf, binary32
+// only (float-float where the 1-ULP bound needs it), for sm_103a:
+//   tan, sincos   quarter-turn reduction (Cody-Waite, FF Payne-Hanek beyond
+//                 2^20); tan s = s + s t (c1 + t P), -1/tan s for odd
+//                 quadrants; sincos from one reduction, cos = 1 - t/2 + t^2 C
+//   asin, acos    u + u t (c1 + t P) on [0, 1/2], pi/2 - 2 asin(sqrt((1-a)/2))
+//   atan, atan2   s + s t (c1 + t P) on [0, 1], 1/a beyond; atan2 on min/max
+//                 with tiny operands scaled by 2^64; Annex F special pairs
+//   exp2, exp10, expm1, log2, log10, sinh, cosh, asinh, acosh, atanh, pow,
+//   cbrt, erfc    the FP64 designs on the binary32 exp/log cores in FF
+//   fmod, remainder  the long division of Section 5.9 with FF remainders
+//   tgamma, lgamma   Stirling, two polynomials, shift and reflection in FF
+// Every op sequence is the oracle's, so results are identical bit for bit.
+#include "explog32_core.cuh"
+#include "trig32_core.cuh"
+
+namespace sleefcu {
+namespace derived32 {
+using namespace explog32;
+using trig32::cw1;
+using trig32::cw2;
+using trig32::ph;
+using trig32::q_of;
+using trig32::sin_poly_u10;
+using trig32::sin_poly_u35;
+
+constexpr float LN10HF = 0x1.26bb1cp+1f, LN10LF = -0x1.12aabap-25f;
+constexpr float RL2HF = 0x1.715476p+0f, RL2LF = 0x1.4ae0c0p-26f;
+constexpr float RL10HF = 0x1.bcb7b2p-2f, RL10LF = -0x1.5b235ep-27f;
+constexpr float L10AF = 0x1.344136p-2f, L10BF = -0x1.ec10c0p-27f;
+constexpr float LG2HF = 0x1.344000p-2f, LG2LF = 0x1.3509f8p-18f;
+constexpr float LOG2_10F = 0x1.a934f0p+1f, THIRDF = 0x1.555556p-2f;
+constexpr float PIO2HF = 0x1.921fb6p+0f, PIO2LF = -0x1.777a5cp-25f;
+constexpr float PIHF = 0x1.921fb6p+1f, PILF = -0x1.777a5cp-24f;
+constexpr float PIO4F = 0x1.921fb6p-1f, P3O4F = 0x1.2d97c8p+1f;
+constexpr float R_2_PIF = 0x1.45f306p-1f;
+constexpr float LOG2PI_HF = 0x1.d67f1cp-1f, LOG2PI_LF = 0x1.0c97d6p-26f;
+constexpr float LOGPI_HF = 0x1.250d04p+0f, LOGPI_LF = 0x1.1cf438p-25f;
+constexpr uint32_t SIGN32 = 0x80000000u, B2P20 = 0x49800000u, B125 = 0x42fa0000u;
+
+constexpr float POWLOG_C1H = 0x1.5555560000000p-4f, POWLOG_C1L = -0x1.556c1c0000000p-29f;
+constexpr float TAN_C1H = 0x1.5555580000000p-2f, TAN_C1L = -0x1.f1c2420000000p-27f;
+constexpr float ASIN_C1H = 0x1.5555c80000000p-3f, ASIN_C1L = 0x1.0680980000000p-28f;
+constexpr float ATAN_C1H = -0x1.5555520000000p-2f, ATAN_C1L = 0x1.f7f7280000000p-27f;
+static __constant__ float kPowLog[5] = {
+    0x1.99999a0000000p-7f, 0x1.2492040000000p-9f, 0x1.c7407e0000000p-12f, 0x1.7009440000000p-14f,
+    0x1.76e4040000000p-16f};
+static __constant__ float kErfcA[6] = {
+    -0x1.b82cb80000000p-6f, 0x1.56584c0000000p-8f, -0x1.bfdbf80000000p-11f, 0x1.f541640000000p-14f,
+    -0x1.d15b760000000p-17f, 0x1.19300c0000000p-20f};
+static __constant__ float kErfcAH[6] = {
+    0x1.20dd760000000p+0f, -0x1.f7ae9c0000000p-25f, -0x1.8127460000000p-2f, -0x1.5b642c0000000p-27f,
+    0x1.ce2f200000000p-4f, 0x1.2ea15c0000000p-29f};
+static __constant__ float kErfcB[14] = {
+    0x1.cb9f5e0000000p-5f, -0x1.63cc1e0000000p-7f, 0x1.1bd5580000000p-9f, -0x1.b961360000000p-12f,
+    0x1.4317420000000p-14f, -0x1.ac04e40000000p-17f, 0x1.dad5380000000p-20f, -0x1.4e96480000000p-23f,
+    -0x1.aea6480000000p-27f, 0x1.73651a0000000p-27f, -0x1.e6b6360000000p-29f, 0x1.ea77ae0000000p-31f,
+    -0x1.602d9c0000000p-33f, 0x1.d3d48e0000000p-37f};
+static __constant__ float kErfcBH[4] = {
+    -0x1.8e8b720000000p+0f, -0x1.a46ed80000000p-28f, -0x1.6925240000000p-2f, -0x1.1b4e660000000p-27f};
+static __constant__ float kErfcC[11] = {
+    0x1.3b79080000000p-7f, -0x1.c61c140000000p-11f, 0x1.6916d80000000p-14f, -0x1.2cc17c0000000p-17f,
+    0x1.0041580000000p-20f, -0x1.bacafe0000000p-24f, 0x1.7e68c80000000p-27f, -0x1.34435a0000000p-30f,
+    0x1.0245ec0000000p-33f, -0x1.44273e0000000p-36f, 0x1.12c9fe0000000p-39f};
+static __constant__ float kErfcCH[4] = {
+    -0x1.439d140000000p+1f, 0x1.afdc740000000p-25f, -0x1.1ee25c0000000p-3f, -0x1.30b6180000000p-29f};
+static __constant__ float kCbrt[4] = {
+    0x1.bf29700000000p-1f, -0x1.8cd3a20000000p-3f, 0x1.7d18a20000000p-4f, -0x1.9915440000000p-5f};
+static __constant__ float kCos[3] = {
+    0x1.55553c0000000p-5f, -0x1.6c04a00000000p-10f, 0x1.9800920000000p-16f};
+static __constant__ float kTan10[8] = {
+    0x1.11106c0000000p-3f, 0x1.ba469c0000000p-5f, 0x1.6395d80000000p-6f, 0x1.3b30280000000p-7f,
+    0x1.970c880000000p-10f, 0x1.3758500000000p-8f, -0x1.3fc6b60000000p-9f, 0x1.9a952c0000000p-10f};
+static __constant__ float kTan35[8] = {
+    0x1.5555480000000p-2f, 0x1.11153e0000000p-3f, 0x1.b93aa40000000p-5f, 0x1.7197bc0000000p-6f,
+    0x1.a783120000000p-8f, 0x1.1109d80000000p-7f, -0x1.e31e620000000p-9f, 0x1.a35f120000000p-9f};
+static __constant__ float kAsin10[4] = {
+    0x1.3301e40000000p-4f, 0x1.747e5c0000000p-5f, 0x1.8c27500000000p-6f, 0x1.596e1c0000000p-5f};
+static __constant__ float kAsin35[5] = {
+    0x1.5555c80000000p-3f, 0x1.3302040000000p-4f, 0x1.747bba0000000p-5f, 0x1.8c3e280000000p-6f,
+    0x1.595c920000000p-5f};
+static __constant__ float kAtan10[9] = {
+    0x1.9997e00000000p-3f, -0x1.2473700000000p-3f, 0x1.c4f1ac0000000p-4f, -0x1.68e6020000000p-4f,
+    0x1.141fc60000000p-4f, -0x1.6e0e460000000p-5f, 0x1.7131e00000000p-6f, -0x1.df5afe0000000p-8f,
+    0x1.23be480000000p-10f};
+static __constant__ float kAtan35[9] = {
+    -0x1.55553e0000000p-2f, 0x1.9991e40000000p-3f, -0x1.2420860000000p-3f, 0x1.c08c500000000p-4f,
+    -0x1.58091e0000000p-4f, 0x1.da29780000000p-5f, -0x1.fd7a1c0000000p-6f, 0x1.641bb60000000p-7f,
+    -0x1.d33df60000000p-10f};
+static __constant__ float kLgR[8] = {
+    -0x1.13e0020000000p-4f, 0x1.51322c0000000p-6f, -0x1.e403d20000000p-8f, 0x1.7ad7f40000000p-9f,
+    -0x1.3907620000000p-10f, 0x1.0d8da60000000p-11f, -0x1.c863b00000000p-13f, 0x1.0a56680000000p-14f};
+static __constant__ float kLgRH[4] = {
+    0x1.b0ee600000000p-2f, 0x1.c8549e0000000p-28f, 0x1.4a34cc0000000p-2f, 0x1.28cfac0000000p-28f};
+static __constant__ float kLgM[7] = {
+    -0x1.1ae55a0000000p-3f, 0x1.e0f90a0000000p-5f, -0x1.da5b4a0000000p-6f, 0x1.f942200000000p-7f,
+    -0x1.1a24040000000p-7f, 0x1.5848220000000p-8f, -0x1.97fcc40000000p-9f};
+static __constant__ float kLgMH[6] = {
+    -0x1.eeb95c0000000p-4f, 0x1.edf4060000000p-29f, 0x1.2aed060000000p-5f, -0x1.97d1220000000p-31f,
+    0x1.de9e640000000p-2f, 0x1.5640560000000p-27f};
+static __constant__ float kLgSt[4] = {
+    0x1.5555560000000p-4f, -0x1.6c76ba0000000p-9f, 0x1.4ff8120000000p-10f, -0x1.5e9a820000000p-6f};
+static __constant__ float kSpi[5] = {
+    0x1.466bc60000000p+1f, -0x1.32d29a0000000p-1f, 0x1.5068d20000000p-4f, -0x1.df0b940000000p-8f,
+    0x1.83836c0000000p-12f};
+static __constant__ float kSpiH[4] = {
+    0x1.921fb60000000p+1f, -0x1.777a940000000p-24f, -0x1.4abbce0000000p+2f, -0x1.891fc40000000p-24f};
+
+
+__device__ __forceinline__ f2 fneg(f2 a) { return F2(-a.x, -a.y); }
+__device__ __forceinline__ float csign(float v, uint32_t bx) {
+  return from_fbits((fbits(v) & ABS32) | (bx & SIGN32));
+}
+__device__ __forceinline__ bool isnan_f(float x) { return (fbits(x) & ABS32) > INF; }
+__device__ __forceinline__ bool isinf_f(float x) { return (fbits(x) & ABS32) == INF; }
+__device__ __forceinline__ float pow2f_any(int k) {   // 2^k, k in [-149, 127]
+  return k >= -126 ? pow2f(k) : from_fbits(1u << (k + 149));
+}
+// y 2^k in two multiplications by normal powers of two (one rounding)
+// v 2^j for |j| up to ~250 with both steps exact (normal intermediate and result)
+__device__ __forceinline__ float scale_exact(float v, int j) {
+  int j1 = j / 2;
+  return __fmul_rn(__fmul_rn(v, pow2f_any(j1)), pow2f_any(j - j1));
+}
+__device__ __forceinline__ float scale2f_two(float y, int k) {
+  int k1 = k / 2, k2 = k - k1;
+  return __fmul_rn(__fmul_rn(y, pow2f(k1)), pow2f(k2));
+}
+
+// ---------------- cores (mirrors of the oracle's exported FP32 cores) ----------------
+__device__ __forceinline__ float exp_tail_u10(float r, float rl, float k) {
+  float w = __fmaf_rn(__fmul_rn(r, r), polyf(r, kExpU10), rl);
+  f2 o = add_ff_fast(1.0f, r);
+  return scale2f(__fadd_rn(o.x, __fadd_rn(o.y, w)), int_off(k));
+}
+__device__ __forceinline__ f2 exp_parts(f2 a, float &k) {
+  k = rintf(__fmul_rn(a.x, R_LN2F));
+  float h = __fmaf_rn(k, -L2AF, a.x);
+  f2 r = add_ff(h, __fmaf_rn(k, -L2BF, a.y));
+  float w = __fmaf_rn(__fmul_rn(r.x, r.x), polyf(r.x, kExpU10), r.y);
+  f2 o = add_ff_fast(1.0f, r.x);
+  return F2(o.x, __fadd_rn(o.y, w));
+}
+__device__ __forceinline__ f2 expm1_s(float a, float &k) {
+  k = rintf(__fmul_rn(a, R_LN2F));
+  float h = __fmaf_rn(k, -L2AF, a);
+  float r = __fmaf_rn(k, -L2BF, h);
+  float rl = __fmaf_rn(k, -L2BF, __fsub_rn(h, r));
+  f2 rr = F2(r, rl);
+  f2 q = scale_f2(sqr_f2(rr), 0.5f);
+  float v = __fmul_rn(__fmul_rn(__fmul_rn(r, r), r), polyf(r, kExpm1));
+  f2 s = add_f2f2(rr, q);
+  return add_f2_f(s, v);
+}
+// a > 0 finite FF: log m (FF) and e, a = m 2^e
+__device__ __forceinline__ f2 logm_u10(f2 a, int &e) {
+  float m = log_reduce(fbits(a.x), e);
+  float ml = ldexp_small(a.y, e);
+  f2 num = scale_f2(add_ff(__fsub_rn(m, 1.0f), ml), 2.0f);
+  f2 den = add_f_f2(1.0f, F2(m, ml));
+  f2 z = div_f2f2(num, den);
+  float t = __fmul_rn(z.x, z.x);
+  float corr = __fmul_rn(__fmul_rn(z.x, t), polyf(t, kLogU10));
+  return add_f2_f_fast(z, corr);
+}
+__device__ __forceinline__ f2 log_ff(f2 a) {
+  int e;
+  f2 lm = logm_u10(a, e);
+  float ed = fl_of(e);
+  return add_f2f2(F2(__fmul_rn(ed, L2HF), __fmul_rn(ed, L2LF)), lm);
+}
+__device__ __forceinline__ f2 logk_ff(f2 a) {
+  int e;
+  float m = log_reduce(fbits(a.x), e);
+  float ml = ldexp_small(a.y, e);
+  f2 num = scale_f2(add_ff(__fsub_rn(m, 1.0f), ml), 2.0f);
+  f2 z = div_f2f2(num, add_f_f2(1.0f, F2(m, ml)));
+  f2 t = sqr_f2(z);
+  float q = polyf(t.x, kPowLog);
+  f2 w = add_f2_f_fast(F2(POWLOG_C1H, POWLOG_C1L), __fmul_rn(t.x, q));
+  w = mul_f2f2(t, w);
+  w = mul_f2f2(z, w);
+  f2 lm = add_f2f2_fast(z, w);
+  float ed = fl_of(e);
+  return add_f2f2(F2(__fmul_rn(ed, L2HF), __fmul_rn(ed, L2LF)), lm);
+}
+
+// ---------------- exp2, exp10, expm1 ----------------
+__device__ __forceinline__ float exp_out(float x, float y, float lim) {
+  if (!(fabsf(x) <= lim)) y = isnan_f(x) ? from_fbits(QNAN32) : (x > 0.0f ? from_fbits(INF) : 0.0f);
+  return canonf(y);
+}
+struct Exp2U10 {
+  __device__ float operator()(float x) const {
+    float xc = fabsf(x) <= 160.0f ? x : 0.0f;
+    float k = rintf(xc);
+    f2 t = mul_f2_f(F2(L2AF, L2BF), __fsub_rn(xc, k));
+    return exp_out(x, exp_tail_u10(t.x, t.y, k), 160.0f);
+  }
+};
+struct Exp2U35 {
+  __device__ float operator()(float x) const {
+    float xc = fabsf(x) <= 160.0f ? x : 0.0f;
+    float k = rintf(xc);
+    float t = __fmul_rn(__fsub_rn(xc, k), L2AF);
+    float v = __fmaf_rn(__fmul_rn(t, t), polyf(t, kExpU35), t);
+    return exp_out(x, scale2f(__fadd_rn(1.0f, v), int_off(k)), 160.0f);
+  }
+};
+struct Exp10U10 {
+  __device__ float operator()(float x) const {
+    float xc = fabsf(x) <= 50.0f ? x : 0.0f;
+    float k = rintf(__fmul_rn(xc, LOG2_10F));
+    float h = __fmaf_rn(k, -L10AF, xc);
+    float r = __fmaf_rn(k, -L10BF, h);
+    float rl = __fmaf_rn(k, -L10BF, __fsub_rn(h, r));
+    f2 t = mul_f2f2(F2(r, rl), F2(LN10HF, LN10LF));
+    return exp_out(x, exp_tail_u10(t.x, t.y, k), 50.0f);
+  }
+};
+struct Exp10U35 {
+  __device__ float operator()(float x) const {
+    float xc = fabsf(x) <= 50.0f ? x : 0.0f;
+    float k = rintf(__fmul_rn(xc, LOG2_10F));
+    float t = __fmul_rn(__fmaf_rn(k, -L10BF, __fmaf_rn(k, -L10AF, xc)), LN10HF);
+    float v = __fmaf_rn(__fmul_rn(t, t), polyf(t, kExpU35), t);
+    return exp_out(x, scale2f(__fadd_rn(1.0f, v), int_off(k)), 50.0f);
+  }
+};
+__device__ __forceinline__ f2 em1f(float a) {      // e^a - 1 in FF, -18 < a <= 40
+  float k;
+  f2 s = expm1_s(a, k);
+  float p = pow2f(int_off(k));
+  return add_f2f2(add_ff(p, -1.0f), scale_f2(s, p));
+}
+struct Expm1U10 {
+  __device__ float operator()(float x) const {
+    bool inr = x > -18.0f && x < 89.0f;
+    float xc = inr ? x : 0.0f;
+    float k;
+    f2 s = expm1_s(xc, k);
+    float y;
+    if (k > 100.0f) {
+      f2 e = add_f_f2_fast(1.0f, s);
+      y = scale2f_two(__fadd_rn(e.x, e.y), int_off(k));
+    } else {
+      float p = pow2f(int_off(k));
+      f2 r = add_f2f2(add_ff(p, -1.0f), scale_f2(s, p));
+      y = __fadd_rn(r.x, r.y);
+    }
+    if (x == 0.0f) y = x;
+    if (!inr) y = x >= 89.0f ? from_fbits(INF) : (x <= -18.0f ? -1.0f : from_fbits(QNAN32));
+    return canonf(y);
+  }
+};
+
+// ---------------- log2, log10 ----------------
+__device__ __forceinline__ float logf_out(float x, float y) {
+  uint32_t b = fbits(x);
+  if ((b & ABS32) == 0) return from_fbits(0xFF800000u);
+  if ((b >> 31) || (b & ABS32) > INF) return from_fbits(QNAN32);
+  if (b == INF) return from_fbits(INF);
+  return canonf(y);
+}
+__device__ __forceinline__ float log_arg(float x) {
+  uint32_t b = fbits(x);
+  return (b - 1u) < FMAX ? x : 1.0f;
+}
+struct Log2U10 {
+  __device__ float operator()(float x) const {
+    int e;
+    f2 lm = logm_u10(F2(log_arg(x), 0.0f), e);
+    f2 p = mul_f2f2(lm, F2(RL2HF, RL2LF));
+    f2 r = add_f_f2(fl_of(e), p);
+    return logf_out(x, __fadd_rn(r.x, r.y));
+  }
+};
+struct Log2U35 {
+  __device__ float operator()(float x) const {
+    int e;
+    f2 lm = logm_u10(F2(log_arg(x), 0.0f), e);
+    return logf_out(x, __fmaf_rn(__fadd_rn(lm.x, lm.y), RL2HF, fl_of(e)));
+  }
+};
+struct Log10U10 {
+  __device__ float operator()(float x) const {
+    int e;
+    f2 lm = logm_u10(F2(log_arg(x), 0.0f), e);
+    f2 p = mul_f2f2(lm, F2(RL10HF, RL10LF));
+    float ed = fl_of(e);
+    f2 r = add_f2f2(F2(__fmul_rn(ed, LG2HF), __fmul_rn(ed, LG2LF)), p);
+    return logf_out(x, __fadd_rn(r.x, r.y));
+  }
+};
+struct Log10U35 {
+  __device__ float operator()(float x) const {
+    int e;
+    f2 lm = logm_u10(F2(log_arg(x), 0.0f), e);
+    return logf_out(x, __fmaf_rn(fl_of(e), L10AF, __fmul_rn(__fadd_rn(lm.x, lm.y), RL10HF)));
+  }
+};
+
+// ---------------- sinh, cosh ----------------
+__device__ __forceinline__ float exph_big(float a) {    // e^a / 2 for 12 < a <= 89.5
+  float k;
+  f2 o = exp_parts(add_f_f2(a, F2(-L2AF, -L2BF)), k);
+  return scale2f(__fadd_rn(o.x, o.y), int_off(k));
+}
+struct SinhU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 12.0f; }
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    float a = fabsf(x);
+    float ac = a <= 89.5f ? a : 0.0f;
+    float y;
+    if (ac > 12.0f) {
+      y = exph_big(ac);
+    } else {
+      f2 em = em1f(ac);
+      f2 f = div_f2f2(em, add_f_f2(1.0f, em));
+      f2 h = add_f2f2(em, f);
+      y = __fmul_rn(0.5f, __fadd_rn(h.x, h.y));
+    }
+    if (a < 0x1p-12f) y = a;
+    if (!(a <= 89.5f)) y = isnan_f(x) ? from_fbits(QNAN32) : from_fbits(INF);
+    return canonf(csign(y, bx));
+  }
+};
+struct CoshU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 12.0f; }
+  __device__ float operator()(float x) const {
+    float a = fabsf(x);
+    float ac = a <= 89.5f ? a : 0.0f;
+    float y;
+    if (ac > 12.0f) {
+      y = exph_big(ac);
+    } else {
+      f2 E = add_f_f2(1.0f, em1f(ac));
+      f2 h = add_f2f2_fast(E, rec_f2(E));
+      y = __fmul_rn(0.5f, __fadd_rn(h.x, h.y));
+    }
+    if (!(a <= 89.5f)) y = isnan_f(x) ? from_fbits(QNAN32) : from_fbits(INF);
+    return canonf(y);
+  }
+};
+
+// ---------------- asinh, acosh, atanh ----------------
+struct AsinhU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 0x1p60f; }
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    float a = fabsf(x);
+    float ac = (fbits(a) <= FMAX) ? a : 1.0f;
+    f2 r;
+    if (ac > 0x1p60f) {
+      r = add_f2f2(log_ff(F2(ac, 0.0f)), F2(L2AF, L2BF));
+    } else {
+      f2 w = sqrt_f2(add_f2_f(mul_ff(ac, ac), 1.0f));
+      r = log_ff(add_f2_f(w, ac));
+    }
+    float y = __fadd_rn(r.x, r.y);
+    if (a < 0x1p-12f) y = a;
+    if (!(fbits(a) <= FMAX)) y = isnan_f(x) ? from_fbits(QNAN32) : from_fbits(INF);
+    return canonf(csign(y, bx));
+  }
+};
+struct AcoshU10 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 0x1p60f; }
+  __device__ float operator()(float x) const {
+    bool inr = x >= 1.0f && fbits(x) <= FMAX;
+    float xc = inr ? x : 1.0f;
+    f2 r;
+    if (xc > 0x1p60f) {
+      r = add_f2f2(log_ff(F2(xc, 0.0f)), F2(L2AF, L2BF));
+    } else {
+      f2 d = mul_f2f2(add_ff(xc, -1.0f), add_ff(xc, 1.0f));
+      r = log_ff(add_f2_f(sqrt_f2(d), xc));
+    }
+    float y = __fadd_rn(r.x, r.y);
+    if (xc == 1.0f) y = 0.0f;
+    if (!inr) y = fbits(x) == INF ? from_fbits(INF) : from_fbits(QNAN32);
+    return canonf(y);
+  }
+};
+struct AtanhU10 {
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    float a = fabsf(x);
+    float ac = a < 1.0f ? a : 0.5f;
+    f2 q = div_f2f2(add_ff(1.0f, ac), add_ff(1.0f, -ac));
+    f2 r = log_ff(q);
+    float y = __fmul_rn(0.5f, __fadd_rn(r.x, r.y));
+    if (a < 0x1p-12f) y = a;
+    if (!(a < 1.0f)) y = a == 1.0f ? from_fbits(INF) : from_fbits(QNAN32);
+    return canonf(csign(y, bx));
+  }
+};
+
+// ---------------- pow ----------------
+__device__ __forceinline__ float expkf(f2 Y) {
+  if (!(fabsf(Y.x) <= 160.0f)) return Y.x > 0.0f ? from_fbits(INF) : 0.0f;
+  float k;
+  f2 o = exp_parts(Y, k);
+  return scale2f(__fadd_rn(o.x, o.y), int_off(k));
+}
+struct PowU10 {
+  __device__ float operator()(float x, float y) const {
+    uint32_t bx = fbits(x);
+    float ax = fabsf(x);
+    float axc = (ax > 0.0f && fbits(ax) <= FMAX) ? ax : 1.0f;
+    bool yfin = (fbits(y) & ABS32) < INF, xfin = (bx & ABS32) < INF;
+    float yc = yfin ? y : 0.0f;
+    bool yint = yfin && y == truncf(y);
+    bool yodd = yint && fabsf(y) < 0x1p24f && ((int)y & 1);
+    float r = expkf(mul_f2_f(logk_ff(F2(axc, 0.0f)), yc));
+    if (x < 0.0f && yodd) r = -r;
+    if (x < 0.0f && xfin && yfin && !yint) r = from_fbits(QNAN32);
+    if (x == 0.0f) {
+      if (y < 0.0f) r = yodd ? csign(from_fbits(INF), bx) : from_fbits(INF);
+      else if (y > 0.0f) r = yodd ? x : 0.0f;
+    }
+    if (isinf_f(y)) {
+      if (ax == 1.0f) r = 1.0f;
+      else r = ((ax < 1.0f) == (y < 0.0f)) ? from_fbits(INF) : 0.0f;
+    }
+    if (isinf_f(x)) {
+      if (x > 0.0f) r = y < 0.0f ? 0.0f : from_fbits(INF);
+      else if (y < 0.0f) r = yodd ? -0.0f : 0.0f;
+      else r = yodd ? from_fbits(0xFF800000u) : from_fbits(INF);
+    }
+    if (isnan_f(x) || isnan_f(y)) r = from_fbits(QNAN32);
+    if (y == 0.0f || x == 1.0f) r = 1.0f;
+    return canonf(r);
+  }
+};
+
+// ---------------- cbrt ----------------
+template <bool U10>
+__device__ __forceinline__ float cbrt_core(float x) {
+  uint32_t bx = fbits(x), ab = bx & ABS32;
+  bool fin = ab - 1u < INF - 1u;
+  float a0 = fin ? from_fbits(ab) : 1.0f;
+  int off = 0;
+  if (a0 < 0x1p-126f) { a0 = __fmul_rn(a0, 0x1p24f); off = 8; }
+  uint32_t b0 = fbits(a0);
+  int e = (int)(b0 >> 23) - 127;
+  int q = e >= 0 ? e / 3 : -((2 - e) / 3);
+  int i = e - 3 * q;
+  float m = from_fbits((b0 & 0x7FFFFFu) | 0x3F800000u);
+  float a = __fmul_rn(m, pow2f(i));
+  float c = i == 0 ? 1.0f : (i == 1 ? 0x1.965feap-1f : 0x1.428a30p-1f);
+  float z = __fmul_rn(polyf(__fsub_rn(m, 1.5f), kCbrt), c);
+  float z3 = __fmul_rn(__fmul_rn(z, z), z);
+  z = __fmaf_rn(__fmul_rn(z, __fmaf_rn(-a, z3, 1.0f)), THIRDF, z);
+  float zz = __fmul_rn(z, z);
+  float y = __fmul_rn(a, zz);
+  float d;
+  if (U10) {
+    f2 y3 = mul_f2_f(mul_ff(y, y), y);
+    d = __fadd_rn(__fsub_rn(y3.x, a), y3.y);
+  } else {
+    d = __fmaf_rn(__fmul_rn(y, y), y, -a);
+  }
+  y = __fmaf_rn(-d, __fmul_rn(zz, THIRDF), y);
+  y = __fmul_rn(y, pow2f(q - off));
+  if (!fin) y = __fadd_rn(x, x);
+  return canonf(csign(y, bx));
+}
+struct CbrtU10 { __device__ float operator()(float x) const { return cbrt_core<true>(x); } };
+struct CbrtU35 { __device__ float operator()(float x) const { return cbrt_core<false>(x); } };
+
+// ---------------- erfc ----------------
+__device__ __forceinline__ f2 erfc_a(float a) {    // erf(a), 0 <= a < 1, three FF levels
+  f2 T = mul_ff(a, a);
+  float p = polyf(T.x, kErfcA);
+  f2 in = add_f2_f(F2(kErfcAH[4], kErfcAH[5]), __fmul_rn(T.x, p));
+  in = add_f2f2(F2(kErfcAH[2], kErfcAH[3]), mul_f2f2(T, in));
+  in = add_f2f2(F2(kErfcAH[0], kErfcAH[1]), mul_f2f2(T, in));
+  return mul_f2_f(in, a);
+}
+__device__ __forceinline__ f2 erfc_L(float x) {    // log(erfc(x) e^(x^2)), 1 <= x <= 10.1
+  bool tail = x >= 3.95f;
+  float u = __fsub_rn(x, tail ? 7.0f : 2.5f);
+  float p = tail ? polyf(u, kErfcC) : polyf(u, kErfcB);
+  const float *h = tail ? kErfcCH : kErfcBH;
+  f2 in = add_f2_f(F2(h[2], h[3]), __fmul_rn(u, p));
+  return add_f2f2(F2(h[0], h[1]), mul_f2_f(in, u));
+}
+struct ErfcU10 {
+  static constexpr int NCLS = 4;
+  __device__ static int cls(float x) {
+    float a = fabsf(x);
+    return a < 1.0f ? 0 : (a < 3.95f ? 1 : (a <= 10.1f ? 2 : 3));
+  }
+  __device__ float operator()(float x) const {
+    float a = fabsf(x), y;
+    if (a < 1.0f) {
+      f2 e = erfc_a(a);
+      if (x > 0.0f) e = fneg(e);
+      f2 r = add_f_f2(1.0f, e);
+      y = __fadd_rn(r.x, r.y);
+    } else if (a <= 10.1f) {
+      f2 E = add_f2f2(mul_ff(-a, a), erfc_L(a));
+      float k;
+      f2 c = exp_parts(E, k);
+      if (x > 0.0f) {
+        y = scale2f(__fadd_rn(c.x, c.y), int_off(k));
+      } else if (a < 4.0f) {
+        c = scale_f2(c, pow2f(int_off(k)));
+        f2 r = add_f_f2(2.0f, fneg(c));
+        y = __fadd_rn(r.x, r.y);
+      } else {
+        y = 2.0f;
+      }
+    } else {
+      y = x > 0.0f ? 0.0f : 2.0f;
+    }
+    if (isnan_f(x)) y = from_fbits(QNAN32);
+    return canonf(y);
+  }
+};
+
+// ---------------- tan, sincos ----------------
+__device__ __forceinline__ f2 reduce_quarter(float x, int &q) {
+  uint32_t ab = fbits(x) & ABS32;
+  if (ab < B2P20) {
+    float Q = rintf(__fmul_rn(x, R_2_PIF));
+    q = q_of(Q);
+    return ab < B125 ? cw1(x, Q) : cw2(x, Q);
+  }
+  return ph(x, q);
+}
+struct QuarterPaths {
+  static constexpr int NCLS = 3;
+  __device__ static int cls(float x) {
+    uint32_t ab = fbits(x) & ABS32;
+    return ab < B125 ? 0 : (ab < B2P20 ? 1 : 2);
+  }
+};
+struct TanU10 : QuarterPaths {
+  __device__ float operator()(float x) const {
+    int q;
+    f2 s = reduce_quarter(x, q);
+    f2 t = sqr_f2(s);
+    float p = polyf(t.x, kTan10);
+    f2 w = add_f2_f_fast(F2(TAN_C1H, TAN_C1L), __fmul_rn(t.x, p));
+    w = mul_f2f2(s, mul_f2f2(t, w));
+    f2 r = add_f2f2_fast(s, w);
+    if (q & 1) r = div_f2f2(F2(-1.0f, 0.0f), r);
+    float y = __fadd_rn(r.x, r.y);
+    if (x == 0.0f) y = x;
+    return canonf(y);
+  }
+};
+struct TanU35 : QuarterPaths {
+  __device__ float operator()(float x) const {
+    int q;
+    f2 s = reduce_quarter(x, q);
+    float s1 = __fadd_rn(s.x, s.y), t = __fmul_rn(s1, s1);
+    float r = __fmaf_rn(__fmul_rn(s1, t), polyf(t, kTan35), s1);
+    if (q & 1) r = __fdiv_rn(-1.0f, r);
+    if (x == 0.0f) r = x;
+    return canonf(r);
+  }
+};
+__device__ __forceinline__ void sincos_out(int q, float sn, float cs, float x, float &os, float &oc) {
+  float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;
+  if (q == 1 || q == 2) b = -b;
+  if (q & 2) a = -a;
+  if (x == 0.0f) a = x;
+  os = canonf(a);
+  oc = canonf(b);
+}
+struct SinCosU10 : QuarterPaths {
+  __device__ void dual(float x, float &os, float &oc) const {
+    int q;
+    f2 s = reduce_quarter(x, q);
+    float sn = sin_poly_u10(s);
+    f2 t = sqr_f2(s);
+    float v = __fmul_rn(__fmul_rn(t.x, t.x), polyf(t.x, kCos));
+    f2 c = add_f_f2(1.0f, scale_f2(t, -0.5f));
+    c = add_f2_f_fast(c, v);
+    sincos_out(q, sn, __fadd_rn(c.x, c.y), x, os, oc);
+  }
+};
+struct SinCosU35 : QuarterPaths {
+  __device__ void dual(float x, float &os, float &oc) const {
+    int q;
+    f2 s = reduce_quarter(x, q);
+    float s1 = __fadd_rn(s.x, s.y), t = __fmul_rn(s1, s1);
+    float sn = sin_poly_u35(s1);
+    float cs = __fmaf_rn(__fmul_rn(t, t), polyf(t, kCos), __fmaf_rn(t, -0.5f, 1.0f));
+    sincos_out(q, sn, cs, x, os, oc);
+  }
+};
+
+// ---------------- asin, acos, atan, atan2 ----------------
+__device__ __forceinline__ f2 asin_ff(f2 u) {
+  f2 t = sqr_f2(u);
+  float p = polyf(t.x, kAsin10);
+  f2 w = add_f2_f_fast(F2(ASIN_C1H, ASIN_C1L), __fmul_rn(t.x, p));
+  w = mul_f2f2(u, mul_f2f2(t, w));
+  return add_f2f2_fast(u, w);
+}
+__device__ __forceinline__ float asin_f(float u) {
+  float t = __fmul_rn(u, u);
+  return __fmaf_rn(__fmul_rn(u, t), polyf(t, kAsin35), u);
+}
+__device__ __forceinline__ f2 half_sqrt(float v) { return v > 0.0f ? sqrt_f2(F2(v, 0.0f)) : F2(0.0f, 0.0f); }
+struct HalfPaths {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 0.5f; }
+};
+struct AsinU10 : HalfPaths {
+  __device__ float operator()(float x) const {
+    float a = fabsf(x);
+    f2 r;
+    if (a <= 0.5f) {
+      r = asin_ff(F2(a, 0.0f));
+    } else {
+      float v = a <= 1.0f ? __fmul_rn(__fsub_rn(1.0f, a), 0.5f) : 0.0f;
+      f2 A = asin_ff(half_sqrt(v));
+      r = add_f2f2(F2(PIO2HF, PIO2LF), scale_f2(A, -2.0f));
+    }
+    float y = __fadd_rn(r.x, r.y);
+    if (!(a <= 1.0f)) y = from_fbits(QNAN32);
+    return canonf(csign(y, fbits(x)));
+  }
+};
+struct AsinU35 : HalfPaths {
+  __device__ float operator()(float x) const {
+    float a = fabsf(x), y;
+    if (a <= 0.5f) y = asin_f(a);
+    else y = __fmaf_rn(-2.0f, asin_f(__fsqrt_rn(a <= 1.0f ? __fmul_rn(__fsub_rn(1.0f, a), 0.5f) : 0.0f)), PIO2HF);
+    if (!(a <= 1.0f)) y = from_fbits(QNAN32);
+    return canonf(csign(y, fbits(x)));
+  }
+};
+struct AcosU10 {
+  static constexpr int NCLS = 3;
+  __device__ static int cls(float x) { return fabsf(x) <= 0.5f ? 0 : (x > 0.0f ? 1 : 2); }
+  __device__ float operator()(float x) const {
+    float a = fabsf(x);
+    f2 r;
+    if (a <= 0.5f) {
+      f2 s = asin_ff(F2(a, 0.0f));
+      if (x < 0.0f) s = fneg(s);
+      r = add_f2f2(F2(PIO2HF, PIO2LF), fneg(s));
+    } else {
+      float v = a <= 1.0f ? __fmul_rn(__fsub_rn(1.0f, a), 0.5f) : 0.0f;
+      f2 A = scale_f2(asin_ff(half_sqrt(v)), 2.0f);
+      r = x > 0.0f ? A : add_f2f2(F2(PIHF, PILF), fneg(A));
+    }
+    float y = __fadd_rn(r.x, r.y);
+    if (!(a <= 1.0f)) y = from_fbits(QNAN32);
+    return canonf(y);
+  }
+};
+struct AcosU35 {
+  static constexpr int NCLS = 3;
+  __device__ static int cls(float x) { return AcosU10::cls(x); }
+  __device__ float operator()(float x) const {
+    float a = fabsf(x), y;
+    if (a <= 0.5f) {
+      y = __fsub_rn(PIO2HF, csign(asin_f(a), fbits(x)));
+    } else {
+      float A = __fmul_rn(2.0f, asin_f(__fsqrt_rn(a <= 1.0f ? __fmul_rn(__fsub_rn(1.0f, a), 0.5f) : 0.0f)));
+      y = x > 0.0f ? A : __fsub_rn(PIHF, A);
+    }
+    if (!(a <= 1.0f)) y = from_fbits(QNAN32);
+    return canonf(y);
+  }
+};
+__device__ __forceinline__ f2 atan_ff(f2 s) {
+  f2 t = sqr_f2(s);
+  float p = polyf(t.x, kAtan10);
+  f2 w = add_f2_f_fast(F2(ATAN_C1H, ATAN_C1L), __fmul_rn(t.x, p));
+  w = mul_f2f2(s, mul_f2f2(t, w));
+  return add_f2f2_fast(s, w);
+}
+__device__ __forceinline__ float atan_f(float s) {
+  float t = __fmul_rn(s, s);
+  return __fmaf_rn(__fmul_rn(s, t), polyf(t, kAtan35), s);
+}
+struct AtanPaths {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 1.0f; }
+};
+struct AtanU10 : AtanPaths {
+  __device__ float operator()(float x) const {
+    float a = fabsf(x);
+    bool big = a > 1.0f;
+    f2 s = big ? (isinf_f(a) ? F2(0.0f, 0.0f) : rec_f(a)) : F2(a, 0.0f);
+    f2 r = atan_ff(s);
+    if (big) r = add_f2f2(F2(PIO2HF, PIO2LF), fneg(r));
+    float y = __fadd_rn(r.x, r.y);
+    if (isnan_f(x)) y = from_fbits(QNAN32);
+    return canonf(csign(y, fbits(x)));
+  }
+};
+struct AtanU35 : AtanPaths {
+  __device__ float operator()(float x) const {
+    float a = fabsf(x);
+    float y = a > 1.0f ? __fsub_rn(PIO2HF, atan_f(__fdiv_rn(1.0f, a))) : atan_f(a);
+    if (isnan_f(x)) y = from_fbits(QNAN32);
+    return canonf(csign(y, fbits(x)));
+  }
+};
+template <bool U10>
+__device__ __forceinline__ float atan2_core(float y, float x) {
+  float ay = fabsf(y), ax = fabsf(x);
+  float mn = ay < ax ? ay : ax, mx = ay < ax ? ax : ay;
+  bool plain = mn < 0x1p-60f && mx >= 0x1p60f;
+  if (mx < 0x1p-60f || (mn < 0x1p-60f && mx < 0x1p60f)) { mn = __fmul_rn(mn, 0x1p64f); mx = __fmul_rn(mx, 0x1p64f); }
+  bool xneg = fbits(x) >> 31;
+  float r;
+  if (U10) {
+    f2 s = plain ? F2(__fdiv_rn(mn, mx), 0.0f) : div_f2f2(F2(mn, 0.0f), F2(mx, 0.0f));
+    f2 t = atan_ff(s);
+    if (ay > ax) t = add_f2f2(F2(PIO2HF, PIO2LF), fneg(t));
+    if (xneg) t = add_f2f2(F2(PIHF, PILF), fneg(t));
+    r = __fadd_rn(t.x, t.y);
+  } else {
+    float t = atan_f(__fdiv_rn(mn, mx));
+    if (ay > ax) t = __fsub_rn(PIO2HF, t);
+    if (xneg) t = __fsub_rn(PIHF, t);
+    r = t;
+  }
+  if (ay == 0.0f) r = xneg ? PIHF : 0.0f;
+  else if (ax == 0.0f || (isinf_f(ay) && !isinf_f(ax))) r = PIO2HF;
+  else if (isinf_f(ax)) r = isinf_f(ay) ? (xneg ? P3O4F : PIO4F) : (xneg ? PIHF : 0.0f);
+  r = csign(r, fbits(y));
+  if (isnan_f(x) || isnan_f(y)) r = from_fbits(QNAN32);
+  return canonf(r);
+}
+struct Atan2U10 { __device__ float operator()(float y, float x) const { return atan2_core<true>(y, x); } };
+struct Atan2U35 { __device__ float operator()(float y, float x) const { return atan2_core<false>(y, x); } };
+
+// ---------------- fmod, remainder ----------------
+constexpr int FMODF_MAXIT = 24;
+__device__ __forceinline__ float rdownf(float v) { return from_fbits(fbits(v) - 1u); }   // v > 0 finite
+__device__ __forceinline__ int ilogbf_n(float v) { return (int)((fbits(v) >> 23) & 0xFF) - 127; }
+__device__ __forceinline__ f2 fmodf_step(f2 r, float D, float rD) {
+  float q = truncf(__fmul_rn(rdownf(r.x), rD));
+  q = (__fmul_rn(3.0f, D) > r.x && r.x > D) ? 2.0f : q;
+  q = (__fmul_rn(2.0f, D) > r.x && r.x > D) ? 1.0f : q;
+  q = r.x == D ? (r.y >= 0.0f ? 1.0f : 0.0f) : q;
+  return norm_f2(add_f2f2(r, mul_ff(q, -D)));
+}
+__device__ __forceinline__ float fmodf_abs(float n, float d) {
+  bool sub = d < 0x1p-126f;
+  int kmin = sub ? 24 : 0;
+  float dmin = sub ? __fmul_rn(d, 0x1p24f) : d;
+  float rd0 = rdownf(__fdiv_rn(1.0f, dmin));
+  int ed = sub ? ilogbf_n(dmin) - 24 : ilogbf_n(d);
+  f2 r = F2(n, 0.0f);
+  for (int it = 0; it < FMODF_MAXIT && r.x >= dmin; it++) {
+    int j = ilogbf_n(r.x) - ed - 100;
+    if (j < kmin) j = kmin;
+    r = fmodf_step(r, scale_exact(d, j), scale_exact(rd0, kmin - j));
+  }
+  float ret;
+  if (sub) {
+    r = F2(__fmul_rn(r.x, 0x1p24f), __fmul_rn(r.y, 0x1p24f));
+    for (int k = 0; k < 4 && r.x >= dmin; k++) r = fmodf_step(r, dmin, rd0);
+    ret = __fmul_rn(r.x, 0x1p-24f);
+    if (__fadd_rn(r.x, r.y) == dmin) ret = 0.0f;
+  } else {
+    ret = r.x;
+    if (__fadd_rn(r.x, r.y) == d) ret = 0.0f;
+  }
+  return ret;
+}
+struct FmodF {
+  __device__ float operator()(float x, float y) const {
+    float n = fabsf(x), d = fabsf(y);
+    bool ok = !isinf_f(n) && !isnan_f(n) && d > 0.0f && !isinf_f(d);
+    float ret = fmodf_abs(ok ? n : 0.0f, ok ? d : 1.0f);
+    ret = csign(ret, fbits(x));
+    if (n < d) ret = x;
+    if (!(d > 0.0f) || isinf_f(n) || isnan_f(x) || isnan_f(y)) ret = from_fbits(QNAN32);
+    return canonf(ret);
+  }
+};
+struct RemainderF {
+  __device__ float operator()(float x, float y) const {
+    float n = fabsf(x), d = fabsf(y);
+    bool ok = !isinf_f(n) && !isnan_f(n) && d > 0.0f && !isinf_f(d);
+    float nn = ok ? n : 0.0f, dd = ok ? d : 1.0f;
+    float r2 = nn;
+    if (dd <= 0x1.fffffep126f) r2 = fmodf_abs(nn, __fmul_rn(2.0f, dd));
+    if (__fadd_rn(r2, r2) > dd) {
+      r2 = __fsub_rn(r2, dd);
+      if (__fadd_rn(r2, r2) >= dd) r2 = __fsub_rn(r2, dd);
+    }
+    float ret = (fbits(x) >> 31) ? -r2 : r2;
+    if (isinf_f(y) && !isinf_f(x) && !isnan_f(x)) ret = x;
+    if (!(d > 0.0f) || isinf_f(n) || isnan_f(x) || isnan_f(y)) ret = from_fbits(QNAN32);
+    return canonf(ret);
+  }
+};
+
+// ---------------- tgamma, lgamma ----------------
+__device__ __forceinline__ f2 lgf_r2(f2 e) {
+  float p = polyf(e.x, kLgR);
+  f2 in = add_f2_f(F2(kLgRH[2], kLgRH[3]), __fmul_rn(e.x, p));
+  in = add_f2f2(F2(kLgRH[0], kLgRH[1]), mul_f2f2(in, e));
+  return mul_f2f2(in, e);
+}
+__device__ __forceinline__ f2 lgf_m(f2 u) {
+  float p = polyf(u.x, kLgM);
+  f2 in = add_f2_f(F2(kLgMH[4], kLgMH[5]), __fmul_rn(u.x, p));
+  in = add_f2f2(F2(kLgMH[2], kLgMH[3]), mul_f2f2(in, u));
+  return add_f2f2(F2(kLgMH[0], kLgMH[1]), mul_f2f2(in, u));
+}
+__device__ __forceinline__ f2 lgf_stirling(f2 y) {
+  f2 ly = logk_ff(y);
+  f2 r = mul_f2f2(add_f2_f(y, -0.5f), ly);
+  r = add_f2f2(r, fneg(y));
+  r = add_f2f2(r, F2(LOG2PI_HF, LOG2PI_LF));
+  float w = __fdiv_rn(1.0f, __fmul_rn(y.x, y.x));
+  return add_f2_f(r, __fdiv_rn(polyf(w, kLgSt), y.x));
+}
+__device__ __forceinline__ f2 lgammaf_pos(f2 y) {
+  if (y.x >= 8.0f) return lgf_stirling(y);
+  if (y.x >= 1.75f && y.x < 2.5f) return lgf_r2(norm_f2(add_f2_f(y, -2.0f)));
+  if (y.x >= 1.25f && y.x < 1.75f) return lgf_m(norm_f2(add_f2_f(y, -1.5f)));
+  if (y.x >= 0.5f && y.x < 1.25f) {
+    f2 r = y.x < 0.75f ? lgf_m(norm_f2(add_f2_f(y, -0.5f))) : lgf_r2(norm_f2(add_f2_f(y, -1.0f)));
+    return add_f2f2(r, fneg(logk_ff(y)));
+  }
+  int n = (int)__fsub_rn(8.0f, floorf(y.x));
+  f2 P = y, z = y;
+  for (int i = 1; i < n; i++) {
+    z = add_f2_f(z, 1.0f);
+    P = mul_f2f2(P, z);
+  }
+  f2 s = lgf_stirling(add_f2_f(y, (float)n));
+  return add_f2f2(s, fneg(logk_ff(P)));
+}
+__device__ __forceinline__ f2 sinpif_ff(float x) {
+  float r = __fsub_rn(x, __fmul_rn(2.0f, rintf(__fmul_rn(0.5f, x))));
+  float s = r > 0.5f ? __fsub_rn(1.0f, r) : (r < -0.5f ? __fsub_rn(-1.0f, r) : r);
+  f2 T = mul_ff(s, s);
+  float p = polyf(T.x, kSpi);
+  f2 in = add_f2_f(F2(kSpiH[2], kSpiH[3]), __fmul_rn(T.x, p));
+  in = add_f2f2(F2(kSpiH[0], kSpiH[1]), mul_f2f2(T, in));
+  return mul_f2_f(in, s);
+}
+__device__ __forceinline__ f2 lgammaf_ff(float x, int &sign) {
+  sign = 1;
+  if (x > 0.0f) return lgammaf_pos(F2(x, 0.0f));
+  f2 sp = sinpif_ff(x);
+  bool negs = sp.x < 0.0f;
+  sign = negs ? -1 : 1;
+  f2 l = logk_ff(F2(fabsf(sp.x), negs ? -sp.y : sp.y));
+  f2 r = add_f2f2(F2(LOGPI_HF, LOGPI_LF), fneg(l));
+  return add_f2f2(r, fneg(lgammaf_pos(add_ff(1.0f, -x))));
+}
+__device__ __forceinline__ int gammaf_cls(float x) {
+  float a = fabsf(x);
+  if (!(a <= 0x1p124f) || a == 0.0f) return 7;
+  if (x < 0.0f) return a >= 7.0f ? 5 : 6;
+  if (x >= 8.0f) return 0;
+  if (x >= 1.75f && x < 2.5f) return 1;
+  if (x >= 1.25f && x < 1.75f) return 2;
+  if (x >= 0.5f && x < 1.25f) return 3;
+  return 4;
+}
+__device__ __forceinline__ bool neg_intf(float x) {
+  return x < 0.0f && (fabsf(x) >= 0x1p23f || x == rintf(x));
+}
+struct LgammaU10 {
+  static constexpr int NCLS = 8;
+  __device__ static int cls(float x) { return gammaf_cls(x); }
+  __device__ float operator()(float x) const {
+    if (isnan_f(x)) return from_fbits(QNAN32);
+    if (isinf_f(x) || x == 0.0f || neg_intf(x) || x > 0x1p124f) return from_fbits(INF);
+    int sign;
+    f2 L = lgammaf_ff(x, sign);
+    float y = __fadd_rn(L.x, L.y);
+    if ((fbits(y) & ABS32) >= INF) y = from_fbits(INF);
+    return canonf(y);
+  }
+};
+struct TgammaU10 {
+  static constexpr int NCLS = 8;
+  __device__ static int cls(float x) { return gammaf_cls(x); }
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    if (isnan_f(x) || bx == 0xFF800000u || neg_intf(x)) return from_fbits(QNAN32);
+    if (x == 0.0f) return csign(from_fbits(INF), bx);
+    if (x > 36.0f) return from_fbits(INF);
+    if (x < -42.0f) return sinpif_ff(x).x < 0.0f ? -0.0f : 0.0f;
+    int sign;
+    f2 L = lgammaf_ff(x, sign);
+    float k;
+    f2 o = exp_parts(L, k);
+    float y = scale2f(__fadd_rn(o.x, o.y), int_off(k));
+    return canonf(sign < 0 ? -y : y);
+  }
+};
+
+}  // namespace derived32
+}  // namespace sleefcu
+
+#ifndef SLEEFCU_FUNCTORS_ONLY
+using namespace sleefcu;
+
+#define UNARY32(NAME, F)                                                                    \
+  extern "C" sleefcu_status sleefcu_##NAME(const float *x, float *out, size_t n, sleefcu_stream s) { \
+    return launch_unary32<derived32::F>("sleefcu_" #NAME, x, out, n, s);                    \
+  }
+#define SORTED32(NAME, F)                                                                   \
+  extern "C" sleefcu_status sleefcu_##NAME(const float *x, float *out, size_t n, sleefcu_stream s) { \
+    return launch_sorted32<derived32::F>("sleefcu_" #NAME, x, out, n, s);                   \
+  }
+#define BINARY32(NAME, F)                                                                   \
+  extern "C" sleefcu_status sleefcu_##NAME(const float *x, const float *y, float *out, size_t n, \
+                                           sleefcu_stream s) {                              \
+    return launch_binary32<derived32::F>("sleefcu_" #NAME, x, y, out, n, s);                \
+  }
+#define DUAL32(NAME, F)                                                                     \
+  extern "C" sleefcu_status sleefcu_##NAME(const float *x, float *o1, float *o2, size_t n,  \
+                                           sleefcu_stream s) {                              \
+    return launch_dual32<derived32::F>("sleefcu_" #NAME, x, o1, o2, n, s);                  \
+  }
+SORTED32(tan_u10_f32, TanU10)
+SORTED32(tan_u35_f32, TanU35)
+DUAL32(sincos_u10_f32, SinCosU10)
+DUAL32(sincos_u35_f32, SinCosU35)
+SORTED32(asin_u10_f32, AsinU10)
+SORTED32(asin_u35_f32, AsinU35)
+SORTED32(acos_u10_f32, AcosU10)
+SORTED32(acos_u35_f32, AcosU35)
+SORTED32(atan_u10_f32, AtanU10)
+SORTED32(atan_u35_f32, AtanU35)
+BINARY32(atan2_u10_f32, Atan2U10)
+BINARY32(atan2_u35_f32, Atan2U35)
+UNARY32(exp2_u10_f32, Exp2U10)
+UNARY32(exp2_u35_f32, Exp2U35)
+UNARY32(exp10_u10_f32, Exp10U10)
+UNARY32(exp10_u35_f32, Exp10U35)
+UNARY32(expm1_u10_f32, Expm1U10)
+UNARY32(expm1_u35_f32, Expm1U10)
+UNARY32(log2_u10_f32, Log2U10)
+UNARY32(log2_u35_f32, Log2U35)
+UNARY32(log10_u10_f32, Log10U10)
+UNARY32(log10_u35_f32, Log10U35)
+BINARY32(pow_u10_f32, PowU10)
+BINARY32(pow_u35_f32, PowU10)
+UNARY32(cbrt_u10_f32, CbrtU10)
+UNARY32(cbrt_u35_f32, CbrtU35)
+SORTED32(sinh_u10_f32, SinhU10)
+SORTED32(sinh_u35_f32, SinhU10)
+SORTED32(cosh_u10_f32, CoshU10)
+SORTED32(cosh_u35_f32, CoshU10)
+SORTED32(asinh_u10_f32, AsinhU10)
+SORTED32(asinh_u35_f32, AsinhU10)
+SORTED32(acosh_u10_f32, AcoshU10)
+SORTED32(acosh_u35_f32, AcoshU10)
+UNARY32(atanh_u10_f32, AtanhU10)
+UNARY32(atanh_u35_f32, AtanhU10)
+SORTED32(erfc_u10_f32, ErfcU10)
+SORTED32(erfc_u35_f32, ErfcU10)
+BINARY32(fmod_u10_f32, FmodF)
+BINARY32(fmod_u35_f32, FmodF)
+BINARY32(remainder_u10_f32, RemainderF)
+BINARY32(remainder_u35_f32, RemainderF)
+SORTED32(tgamma_u10_f32, TgammaU10)
+SORTED32(tgamma_u35_f32, TgammaU10)
+SORTED32(lgamma_u10_f32, LgammaU10)
+SORTED32(lgamma_u35_f32, LgammaU10)
+#undef UNARY32
+#undef SORTED32
+#undef BINARY32
+#undef DUAL32
+#endif  // SLEEFCU_FUNCTORS_ONLY

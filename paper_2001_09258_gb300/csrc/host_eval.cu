@@ -42,16 +42,28 @@ const Entry kEntries[] = {
   HE_U(cos_u35_f32, float, 4)
   HE_U(tan_u10_f64, double, 8)
   HE_U(tan_u35_f64, double, 8)
+  HE_U(tan_u10_f32, float, 4)
+  HE_U(tan_u35_f32, float, 4)
   HE_SC(sincos_u10_f64, double, 8)
   HE_SC(sincos_u35_f64, double, 8)
+  HE_SC(sincos_u10_f32, float, 4)
+  HE_SC(sincos_u35_f32, float, 4)
   HE_U(asin_u10_f64, double, 8)
   HE_U(asin_u35_f64, double, 8)
+  HE_U(asin_u10_f32, float, 4)
+  HE_U(asin_u35_f32, float, 4)
   HE_U(acos_u10_f64, double, 8)
   HE_U(acos_u35_f64, double, 8)
+  HE_U(acos_u10_f32, float, 4)
+  HE_U(acos_u35_f32, float, 4)
   HE_U(atan_u10_f64, double, 8)
   HE_U(atan_u35_f64, double, 8)
+  HE_U(atan_u10_f32, float, 4)
+  HE_U(atan_u35_f32, float, 4)
   HE_B(atan2_u10_f64, double, 8)
   HE_B(atan2_u35_f64, double, 8)
+  HE_B(atan2_u10_f32, float, 4)
+  HE_B(atan2_u35_f32, float, 4)
   HE_U(exp_u10_f64, double, 8)
   HE_U(exp_u35_f64, double, 8)
   HE_U(exp_u10_f32, float, 4)
@@ -66,10 +78,16 @@ const Entry kEntries[] = {
   HE_U(log_u35_f32, float, 4)
   HE_B(pow_u10_f64, double, 8)
   HE_B(pow_u35_f64, double, 8)
+  HE_B(pow_u10_f32, float, 4)
+  HE_B(pow_u35_f32, float, 4)
   HE_B(fmod_u10_f64, double, 8)
   HE_B(fmod_u35_f64, double, 8)
+  HE_B(fmod_u10_f32, float, 4)
+  HE_B(fmod_u35_f32, float, 4)
   HE_B(remainder_u10_f64, double, 8)
   HE_B(remainder_u35_f64, double, 8)
+  HE_B(remainder_u10_f32, float, 4)
+  HE_B(remainder_u35_f32, float, 4)
   HE_U(log1p_u10_f64, double, 8)
   HE_U(log1p_u35_f64, double, 8)
   HE_U(log1p_u10_f32, float, 4)
@@ -96,32 +114,60 @@ const Entry kEntries[] = {
   HE_U(erf_u35_f16, void, 2)
   HE_U(exp2_u10_f64, double, 8)
   HE_U(exp2_u35_f64, double, 8)
+  HE_U(exp2_u10_f32, float, 4)
+  HE_U(exp2_u35_f32, float, 4)
   HE_U(exp10_u10_f64, double, 8)
   HE_U(exp10_u35_f64, double, 8)
+  HE_U(exp10_u10_f32, float, 4)
+  HE_U(exp10_u35_f32, float, 4)
   HE_U(expm1_u10_f64, double, 8)
   HE_U(expm1_u35_f64, double, 8)
+  HE_U(expm1_u10_f32, float, 4)
+  HE_U(expm1_u35_f32, float, 4)
   HE_U(log2_u10_f64, double, 8)
   HE_U(log2_u35_f64, double, 8)
+  HE_U(log2_u10_f32, float, 4)
+  HE_U(log2_u35_f32, float, 4)
   HE_U(log10_u10_f64, double, 8)
   HE_U(log10_u35_f64, double, 8)
+  HE_U(log10_u10_f32, float, 4)
+  HE_U(log10_u35_f32, float, 4)
   HE_U(cbrt_u10_f64, double, 8)
   HE_U(cbrt_u35_f64, double, 8)
+  HE_U(cbrt_u10_f32, float, 4)
+  HE_U(cbrt_u35_f32, float, 4)
   HE_U(sinh_u10_f64, double, 8)
   HE_U(sinh_u35_f64, double, 8)
+  HE_U(sinh_u10_f32, float, 4)
+  HE_U(sinh_u35_f32, float, 4)
   HE_U(cosh_u10_f64, double, 8)
   HE_U(cosh_u35_f64, double, 8)
+  HE_U(cosh_u10_f32, float, 4)
+  HE_U(cosh_u35_f32, float, 4)
   HE_U(asinh_u10_f64, double, 8)
   HE_U(asinh_u35_f64, double, 8)
+  HE_U(asinh_u10_f32, float, 4)
+  HE_U(asinh_u35_f32, float, 4)
   HE_U(acosh_u10_f64, double, 8)
   HE_U(acosh_u35_f64, double, 8)
+  HE_U(acosh_u10_f32, float, 4)
+  HE_U(acosh_u35_f32, float, 4)
   HE_U(atanh_u10_f64, double, 8)
   HE_U(atanh_u35_f64, double, 8)
-  HE_U(tgamma_u10_f64, double, 8)
-  HE_U(tgamma_u35_f64, double, 8)
-  HE_U(lgamma_u10_f64, double, 8)
-  HE_U(lgamma_u35_f64, double, 8)
+  HE_U(atanh_u10_f32, float, 4)
+  HE_U(atanh_u35_f32, float, 4)
   HE_U(erfc_u10_f64, double, 8)
   HE_U(erfc_u35_f64, double, 8)
+  HE_U(erfc_u10_f32, float, 4)
+  HE_U(erfc_u35_f32, float, 4)
+  HE_U(tgamma_u10_f64, double, 8)
+  HE_U(tgamma_u35_f64, double, 8)
+  HE_U(tgamma_u10_f32, float, 4)
+  HE_U(tgamma_u35_f32, float, 4)
+  HE_U(lgamma_u10_f64, double, 8)
+  HE_U(lgamma_u35_f64, double, 8)
+  HE_U(lgamma_u10_f32, float, 4)
+  HE_U(lgamma_u35_f32, float, 4)
 };
 #undef HE_U
 #undef HE_B

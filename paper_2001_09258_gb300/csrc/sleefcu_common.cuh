@@ -463,6 +463,57 @@ __global__ void __launch_bounds__(kBlock) k_unary32(const float *x, float *out, 
 }
 
 // FP32 divergence-sorted tiles (see k_sorted64)
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_binary32(const float *x, const float *y, float *out, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t nq = n >> 2;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    float4 *o4 = reinterpret_cast<float4 *>(out);
+    for (size_t i = tid; i < nq; i += stride) {
+      float4 a = __ldcs(x4 + i), b = __ldcs(y4 + i);
+      float4 r;
+      r.x = f(a.x, b.x);
+      r.y = f(a.y, b.y);
+      r.z = f(a.z, b.z);
+      r.w = f(a.w, b.w);
+      __stcs(o4 + i, r);
+    }
+    size_t rem = n & 3;
+    if (tid < rem) out[n - rem + tid] = f(x[n - rem + tid], y[n - rem + tid]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) out[i] = f(x[i], y[i]);
+  }
+}
+// one input, two outputs (sincos): the functor's dual(x, out1, out2)
+template <class F, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_dual32(const float *x, float *o1, float *o2, size_t n) {
+  F f;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    size_t nq = n >> 2;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float4 *a4 = reinterpret_cast<float4 *>(o1);
+    float4 *b4 = reinterpret_cast<float4 *>(o2);
+    for (size_t i = tid; i < nq; i += stride) {
+      float4 v = __ldcs(x4 + i), a, b;
+      f.dual(v.x, a.x, b.x);
+      f.dual(v.y, a.y, b.y);
+      f.dual(v.z, a.z, b.z);
+      f.dual(v.w, a.w, b.w);
+      __stcs(a4 + i, a);
+      __stcs(b4 + i, b);
+    }
+    size_t rem = n & 3;
+    if (tid < rem) f.dual(x[n - rem + tid], o1[n - rem + tid], o2[n - rem + tid]);
+  } else {
+    for (size_t i = tid; i < n; i += stride) f.dual(x[i], o1[i], o2[i]);
+  }
+}
 template <class F>
 __global__ void __launch_bounds__(kBlock) k_sorted32(const float *x, float *out, size_t n) {
   constexpr int NC = F::NCLS;
@@ -534,6 +585,37 @@ sleefcu_status launch_sorted32(const char *name, const float *x, float *out, siz
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted32<F>;
   k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, out, n);
+  return check_launch(name);
+}
+
+template <class F>
+sleefcu_status launch_binary32(const char *name, const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(y) && aligned16(out)) {
+    auto k = k_binary32<F, true>;
+    k<<<grid_for((const void *)k, (n + 3) / 4), kBlock, 0, st>>>(x, y, out, n);
+  } else {
+    auto k = k_binary32<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, y, out, n);
+  }
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_dual32(const char *name, const float *x, float *o1, float *o2, size_t n,
+                             sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(o1) && aligned16(o2)) {
+    auto k = k_dual32<F, true>;
+    k<<<grid_for((const void *)k, (n + 3) / 4), kBlock, 0, st>>>(x, o1, o2, n);
+  } else {
+    auto k = k_dual32<F, false>;
+    k<<<grid_for((const void *)k, n), kBlock, 0, st>>>(x, o1, o2, n);
+  }
   return check_launch(name);
 }
 

@@ -181,6 +181,12 @@ __device__ __forceinline__ f2 rec_f(float d) {
   float t = __fdiv_rn(1.0f, d);
   return F2(t, __fmul_rn(t, __fmaf_rn(-t, d, 1.0f)));
 }
+__device__ __forceinline__ f2 rec_f2(f2 d) {
+  float t = __fdiv_rn(1.0f, d.x);
+  float r = __fmaf_rn(-t, d.x, 1.0f);
+  r = __fmaf_rn(-t, d.y, r);
+  return F2(t, __fmul_rn(r, t));
+}
 __device__ __forceinline__ f2 sqrt_f2(f2 a) {
   float h = __fsqrt_rn(a.x);
   float r = __fadd_rn(__fmaf_rn(-h, h, a.x), a.y);

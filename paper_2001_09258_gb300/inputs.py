@@ -16,6 +16,7 @@ domains, Section 7, Table 3):
 """
 import hashlib
 import math
+import os
 
 import numpy as np
 
@@ -141,16 +142,49 @@ DOMAINS_F64 = {
 TRIG = ("sin", "cos", "tan", "sincos")
 # FP32: the same mixes scaled to the binary32 range
 DOMAINS_F32 = {
-    "sin": (-100.0, 100.0), "cos": (-100.0, 100.0), "exp": (-87.0, 88.0),
-    "log": (0.0, 3.4e38), "log1p": (-1.0, 3.4e38), "tanh": (-9.0, 9.0), "erf": (-4.0, 4.0),
+    "sin": (-100.0, 100.0), "cos": (-100.0, 100.0), "tan": (-100.0, 100.0), "sincos": (-100.0, 100.0),
+    "asin": (-1.0, 1.0), "acos": (-1.0, 1.0), "atan": (-700.0, 700.0), "atan2": (-100.0, 100.0),
+    "exp": (-87.0, 88.0), "exp2": (-150.0, 128.0), "exp10": (-45.0, 38.0), "expm1": (-87.0, 88.0),
+    "log": (0.0, 3.4e38), "log2": (0.0, 3.4e38), "log10": (0.0, 3.4e38), "log1p": (-1.0, 3.4e38),
+    "pow": (-30.0, 30.0), "cbrt": (-3.4e38, 3.4e38),
+    "sinh": (-89.0, 89.0), "cosh": (-89.0, 89.0), "tanh": (-9.0, 9.0),
+    "asinh": (-3.4e38, 3.4e38), "acosh": (1.0, 3.4e38), "atanh": (-1.0, 1.0),
+    "erf": (-4.0, 4.0), "erfc": (-4.0, 10.0), "tgamma": (-40.0, 35.0), "lgamma": (-1e3, 4e36),
+    "fmod": (-1e10, 1e10), "remainder": (-1e10, 1e10),
 }
 SPECIALS_F32_TAIL = (1e5, 3.4e38)
+
+
+_BLOCK = 1 << 22
+
+
+def _blocked(n, dtype, make):
+    """Arrays above 2^22 elements are built block by block, each block from
+    its own keyed streams (key + "#i"), on all host cores: the values depend
+    only on the keys, never on the thread count."""
+    if n <= _BLOCK:
+        return make(n, "")
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty(n, dtype=dtype)
+    nb = (n + _BLOCK - 1) // _BLOCK
+
+    def job(i):
+        lo = i * _BLOCK
+        m = min(_BLOCK, n - lo)
+        out[lo:lo + m] = make(m, f"#{i}")
+    with ThreadPoolExecutor(max_workers=min(nb, os.cpu_count() or 1)) as ex:
+        list(ex.map(job, range(nb)))
+    return out
 
 
 def workload(fn, n, key="c2", dtype=np.float64, operand=0):
     """The mixed workload of one function: 89% uniform over the main domain,
     10% log-uniform tail, 1% specials, interleaved by a seeded choice.
     dtype float32 uses the binary32 domains (trig tail up to 3.4e38)."""
+    return _blocked(n, dtype, lambda m, sfx: _workload_block(fn, m, key + sfx, dtype, operand))
+
+
+def _workload_block(fn, n, key, dtype, operand):
     f32 = dtype == np.float32
     a, b = (DOMAINS_F32 if f32 else DOMAINS_F64)[fn]
     k = f"{key}/{fn}/{operand}" + ("/f32" if f32 else "")
@@ -179,9 +213,8 @@ def stress(fn, n, key="c5", operand=0):
     with a random sign (every trig lane takes the Payne-Hanek path); the
     divisor of fmod/remainder log-uniform over [1e-300, 1e300], random sign."""
     k = f"{key}/{fn}/{operand}"
-    if operand == 0:
-        return loguniform(k, n, 1e5, 1.7976931348623157e308)
-    return loguniform(k, n, 1e-300, 1e300)
+    lo, hi = (1e5, 1.7976931348623157e308) if operand == 0 else (1e-300, 1e300)
+    return _blocked(n, np.float64, lambda m, sfx: loguniform(k + sfx, m, lo, hi))
 
 
 def to_bf16_bits(x32):
@@ -203,10 +236,12 @@ def activations(key, shape, fmt, sigma=3.0):
     """N(0, sigma) activations of the given shape as bf16 / binary16 bit
     patterns (Box-Muller in double, then binary32, then the 16-bit format)."""
     n = int(np.prod(shape))
-    u1 = (raw(key + "/u1", n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 + 2.0 ** -54
-    u2 = (raw(key + "/u2", n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
-    z = sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
-    x32 = z.astype(np.float32)
+
+    def block(m, sfx):
+        u1 = (raw(key + sfx + "/u1", m) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 + 2.0 ** -54
+        u2 = (raw(key + sfx + "/u2", m) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        return (sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)).astype(np.float32)
+    x32 = _blocked(n, np.float32, block)
     if fmt == "bf16":
         return to_bf16_bits(x32).reshape(shape)
     return x32.astype(np.float16).view(np.uint16).reshape(shape)
