@@ -504,6 +504,17 @@ def main():
         return
     avg = {name: statistics.mean(v) for name, v in per_fn_ms.items()}
     per_fn = {name: round(n / (avg[name] * 1e-3) / 1e9, 3) for name in names}
+    # per-entry-point roofline: algorithmic FP64 ops of each launch's path mix
+    per_roof = {}
+    for name in names:
+        fn = name.split("_")[0]
+        hx = host[fn]
+        st_ = None
+        if fn in ("fmod", "remainder"):
+            st_ = int(fmod_steps(sleefcu, torch, dev[fn][0], dev[fn][1], fn == "remainder", sp).sum())
+        o = opcounts.ops_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
+        per_roof[name] = {"ops_per_element": round(o / n, 2),
+                          "fp64_frac": round(o / (avg[name] * 1e-3) / peak_fp64, 4)}
     ext = None
     if not args.no_extras:
         del dev, outs
@@ -556,6 +567,7 @@ def main():
                                "(trig: Payne-Hanek arguments 1e5..1e300) / 1% specials",
                    "n_per_function": n, "entry_points": names, "l2": "inputs larger than L2 (no flush)"},
         "per_function_gelem_s": per_fn,
+        "per_function_roofline": per_roof,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -27,6 +27,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 namespace sleefcu {
@@ -185,10 +186,110 @@ struct Desc {
   int code, pad;
 };
 
+// functors with several reduction paths expose NCLS and cls(); their tiles
+// are evaluated in divergence-sorted sub-tiles (the single-array sorted
+// kernels' scheme, for any block size 128..512)
+template <class F, class = void> struct sortable { static constexpr bool value = false; };
+template <class F> struct sortable<F, decltype((void)F::NCLS)> { static constexpr bool value = true; };
+
+constexpr int kSubTile = 1024;         // elements per sorted sub-tile
+constexpr int kMaxEPT = 8;             // kSubTile / smallest block size
+struct SortSmem {
+  double x[kSubTile], y[kSubTile];     // inputs, then results (in place)
+  unsigned short idx[kSubTile];
+  int cnt[64], cur[64];
+};
+
+template <Kind K, class F>
+__device__ __forceinline__ void run_sorted(const Desc &D, long long b, long long e, SortSmem &S) {
+  using T = typename std::conditional<(K == U64 || K == B64 || K == SC64), double, float>::type;
+  constexpr bool BIN = (K == B64 || K == B32), DUAL = (K == SC64 || K == SC32);
+  F f;
+  const T *x = (const T *)D.x, *y = (const T *)D.y;
+  T *o = (T *)D.out, *o2 = (T *)D.out2;
+  T *sx = (T *)S.x, *sy = (T *)S.y;
+  const int tid = threadIdx.x, nt = blockDim.x, ept = kSubTile / nt;
+  const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
+  for (long long base = b; base < e; base += kSubTile) {
+    const int valid = (int)(e - base < kSubTile ? e - base : kSubTile);
+    if (tid < F::NCLS) S.cnt[tid] = 0;
+    __syncthreads();
+    int cl[kMaxEPT];
+#pragma unroll
+    for (int j = 0; j < kMaxEPT; j++) {
+      cl[j] = -1;
+      if (j < ept) {
+        int el = j * nt + tid;
+        T a = 0, c = 0;
+        if (el < valid) {
+          a = x[base + el];
+          if constexpr (BIN) {
+            c = y[base + el];
+            cl[j] = F::cls(a, c);
+          } else {
+            cl[j] = F::cls(a);
+          }
+        }
+        sx[el] = a;
+        if constexpr (BIN) sy[el] = c;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxEPT; j++) {
+      if (j < ept) {
+        unsigned m = __match_any_sync(0xffffffffu, cl[j]);
+        if ((int)lane == __ffs(m) - 1 && cl[j] >= 0) atomicAdd(&S.cnt[cl[j]], __popc(m));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int c = 0; c < F::NCLS; c++) { S.cur[c] = acc; acc += S.cnt[c]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kMaxEPT; j++) {
+      if (j < ept) {
+        unsigned m = __match_any_sync(0xffffffffu, cl[j]);
+        int leader = __ffs(m) - 1, p = 0;
+        if ((int)lane == leader && cl[j] >= 0) p = atomicAdd(&S.cur[cl[j]], __popc(m));
+        p = __shfl_sync(0xffffffffu, p, leader);
+        if (cl[j] >= 0) S.idx[p + __popc(m & lt)] = (unsigned short)(j * nt + tid);
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < valid; k += nt) {
+      int el = S.idx[k];
+      if constexpr (DUAL) {
+        T a, c;
+        f.dual(sx[el], a, c);
+        sx[el] = a;
+        sy[el] = c;
+      } else if constexpr (BIN) {
+        sx[el] = f(sx[el], sy[el]);
+      } else {
+        sx[el] = f(sx[el]);
+      }
+    }
+    __syncthreads();
+    for (int el = tid; el < valid; el += nt) {
+      o[base + el] = sx[el];
+      if constexpr (DUAL) o2[base + el] = sy[el];
+    }
+    __syncthreads();
+  }
+}
+
 // evaluate elements [b, e) of one array; threads of the CTA stride over them,
 // vec > 1 uses 16-byte accesses when the tile start is aligned
 template <Kind K, class F>
-__device__ __forceinline__ void run(const Desc &D, long long b, long long e, int vec) {
+__device__ __forceinline__ void run(const Desc &D, long long b, long long e, int vec, SortSmem &S) {
+  if constexpr (sortable<F>::value && K != BF && K != HF) {
+    if (kSubTile % blockDim.x == 0 && kSubTile / blockDim.x <= kMaxEPT) {   // blocks of 128..1024 threads
+      run_sorted<K, F>(D, b, e, S);
+      return;
+    }
+  }
   F f;
   const int tid = threadIdx.x, nt = blockDim.x;
   if constexpr (K == U64) {
@@ -251,6 +352,7 @@ __global__ void __launch_bounds__(512) k_batch(const Desc *__restrict__ d, const
                                                unsigned long long *ctr) {
   __shared__ long long s_t;
   __shared__ int s_i;
+  __shared__ SortSmem S;
   for (;;) {
     if (threadIdx.x == 0) {
       long long t = (long long)atomicAdd(ctr, 1ull);
@@ -274,7 +376,7 @@ __global__ void __launch_bounds__(512) k_batch(const Desc *__restrict__ d, const
     long long e = b + tile < D.n ? b + tile : D.n;
     switch (D.code) {
 #define SLEEFCU_BATCH_CASE(c, name, kind, F) \
-  case c: run<kind, F>(D, b, e, vec); break;
+  case c: run<kind, F>(D, b, e, vec, S); break;
       SLEEFCU_BATCH_TABLE(SLEEFCU_BATCH_CASE)
 #undef SLEEFCU_BATCH_CASE
       default: break;

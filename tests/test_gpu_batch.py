@@ -46,8 +46,8 @@ def check(items, host):
         want = oracle.apply(name, x, y)
         got = out.cpu().numpy()
         if out2 is not None:
-            assert np.array_equal(got.view(np.uint64), want[0].view(np.uint64)), name
-            assert np.array_equal(out2.cpu().numpy().view(np.uint64), want[1].view(np.uint64)), name
+            assert got.view(np.uint8).tobytes() == want[0].view(np.uint8).tobytes(), name
+            assert out2.cpu().numpy().view(np.uint8).tobytes() == want[1].view(np.uint8).tobytes(), name
         else:
             w = want.view(got.dtype) if want.dtype.itemsize == got.dtype.itemsize else want
             assert np.array_equal(got.view(np.uint8), w.view(np.uint8)), name
@@ -66,7 +66,8 @@ def test_mixed_batch_bitexact():
     check(items, host)
 
 
-@pytest.mark.parametrize("cfg", [(128, 512, 1, 1), (256, 4096, 2, 2), (512, 32768, 4, 2), (64, 64, 1, 1)])
+@pytest.mark.parametrize("cfg", [(128, 512, 1, 1), (256, 4096, 2, 2), (512, 32768, 4, 2), (64, 64, 1, 1),
+                                 (96, 960, 1, 2), (128, 1000, 3, 1)])
 def test_configs_and_graph(cfg):
     names = F64[::3] + F32[::2] + LOWP[::4]
     items, host = make_items(names, [1, 7, 1000, 4099, 65536, 3] * 10, "b2")
