@@ -192,6 +192,9 @@ struct Desc {
 template <class F, class = void> struct sortable { static constexpr bool value = false; };
 template <class F> struct sortable<F, decltype((void)F::NCLS)> { static constexpr bool value = true; };
 
+template <class F, class = void> struct sort_f32 { static constexpr bool value = false; };
+template <class F> struct sort_f32<F, decltype((void)F::SORT32)> { static constexpr bool value = F::SORT32; };
+
 constexpr int kSubTile = 1024;         // elements per sorted sub-tile
 constexpr int kMaxEPT = 8;             // kSubTile / smallest block size
 struct SortSmem {
@@ -284,7 +287,10 @@ __device__ __forceinline__ void run_sorted(const Desc &D, long long b, long long
 // vec > 1 uses 16-byte accesses when the tile start is aligned
 template <Kind K, class F>
 __device__ __forceinline__ void run(const Desc &D, long long b, long long e, int vec, SortSmem &S) {
-  if constexpr (sortable<F>::value && K != BF && K != HF) {
+  // FP64 functors with several paths always; binary32 ones only where the
+  // paths differ by an order of magnitude (gamma's eight classes)
+  if constexpr (sortable<F>::value && K != BF && K != HF &&
+                (K == U64 || K == B64 || K == SC64 || sort_f32<F>::value)) {
     if (kSubTile % blockDim.x == 0 && kSubTile / blockDim.x <= kMaxEPT) {   // blocks of 128..1024 threads
       run_sorted<K, F>(D, b, e, S);
       return;

@@ -876,6 +876,7 @@ __device__ __forceinline__ bool neg_intf(float x) {
 }
 struct LgammaU10 {
   static constexpr int NCLS = 8;
+  static constexpr bool SORT32 = true;
   __device__ static int cls(float x) { return gammaf_cls(x); }
   __device__ float operator()(float x) const {
     if (isnan_f(x)) return from_fbits(QNAN32);
@@ -889,6 +890,7 @@ struct LgammaU10 {
 };
 struct TgammaU10 {
   static constexpr int NCLS = 8;
+  static constexpr bool SORT32 = true;
   __device__ static int cls(float x) { return gammaf_cls(x); }
   __device__ float operator()(float x) const {
     uint32_t bx = fbits(x);
@@ -915,6 +917,9 @@ using namespace sleefcu;
   extern "C" sleefcu_status sleefcu_##NAME(const float *x, float *out, size_t n, sleefcu_stream s) { \
     return launch_unary32<derived32::F>("sleefcu_" #NAME, x, out, n, s);                    \
   }
+// divergence-sorted tiles only where the paths differ by an order of magnitude
+// (tgamma/lgamma's shift loop): for the other binary32 functions the sort's
+// bookkeeping costs more than the divergence it removes
 #define SORTED32(NAME, F)                                                                   \
   extern "C" sleefcu_status sleefcu_##NAME(const float *x, float *out, size_t n, sleefcu_stream s) { \
     return launch_sorted32<derived32::F>("sleefcu_" #NAME, x, out, n, s);                   \
@@ -929,16 +934,16 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_dual32<derived32::F>("sleefcu_" #NAME, x, o1, o2, n, s);                  \
   }
-SORTED32(tan_u10_f32, TanU10)
-SORTED32(tan_u35_f32, TanU35)
+UNARY32(tan_u10_f32, TanU10)
+UNARY32(tan_u35_f32, TanU35)
 DUAL32(sincos_u10_f32, SinCosU10)
 DUAL32(sincos_u35_f32, SinCosU35)
-SORTED32(asin_u10_f32, AsinU10)
-SORTED32(asin_u35_f32, AsinU35)
-SORTED32(acos_u10_f32, AcosU10)
-SORTED32(acos_u35_f32, AcosU35)
-SORTED32(atan_u10_f32, AtanU10)
-SORTED32(atan_u35_f32, AtanU35)
+UNARY32(asin_u10_f32, AsinU10)
+UNARY32(asin_u35_f32, AsinU35)
+UNARY32(acos_u10_f32, AcosU10)
+UNARY32(acos_u35_f32, AcosU35)
+UNARY32(atan_u10_f32, AtanU10)
+UNARY32(atan_u35_f32, AtanU35)
 BINARY32(atan2_u10_f32, Atan2U10)
 BINARY32(atan2_u35_f32, Atan2U35)
 UNARY32(exp2_u10_f32, Exp2U10)
@@ -955,18 +960,18 @@ BINARY32(pow_u10_f32, PowU10)
 BINARY32(pow_u35_f32, PowU10)
 UNARY32(cbrt_u10_f32, CbrtU10)
 UNARY32(cbrt_u35_f32, CbrtU35)
-SORTED32(sinh_u10_f32, SinhU10)
-SORTED32(sinh_u35_f32, SinhU10)
-SORTED32(cosh_u10_f32, CoshU10)
-SORTED32(cosh_u35_f32, CoshU10)
-SORTED32(asinh_u10_f32, AsinhU10)
-SORTED32(asinh_u35_f32, AsinhU10)
-SORTED32(acosh_u10_f32, AcoshU10)
-SORTED32(acosh_u35_f32, AcoshU10)
+UNARY32(sinh_u10_f32, SinhU10)
+UNARY32(sinh_u35_f32, SinhU10)
+UNARY32(cosh_u10_f32, CoshU10)
+UNARY32(cosh_u35_f32, CoshU10)
+UNARY32(asinh_u10_f32, AsinhU10)
+UNARY32(asinh_u35_f32, AsinhU10)
+UNARY32(acosh_u10_f32, AcoshU10)
+UNARY32(acosh_u35_f32, AcoshU10)
 UNARY32(atanh_u10_f32, AtanhU10)
 UNARY32(atanh_u35_f32, AtanhU10)
-SORTED32(erfc_u10_f32, ErfcU10)
-SORTED32(erfc_u35_f32, ErfcU10)
+UNARY32(erfc_u10_f32, ErfcU10)
+UNARY32(erfc_u35_f32, ErfcU10)
 BINARY32(fmod_u10_f32, FmodF)
 BINARY32(fmod_u35_f32, FmodF)
 BINARY32(remainder_u10_f32, RemainderF)

@@ -8,8 +8,8 @@
 // erf: |x| < 1: x (c0 + t (c1 + t P(t))) with the two leading terms in FF;
 //   1 <= |x| < 3.95: 1 - exp(-x^2 + L), L = log(erfc(x) e^(x^2)) a polynomial
 //   in |x| - 2.475, the exponent and the exponential in FF.
-// Every lane takes the same path (plain 16-byte vectorized kernels) except
-// erf, whose two regions are grouped in divergence-sorted tiles.
+// Plain 16-byte vectorized kernels (for binary32 the divergence-sorted tiles
+// cost about what they save).
 #include "explog32_core.cuh"
 
 // ---------------- bf16 / f16 forms ----------------
@@ -113,10 +113,10 @@ UNARY32(log1p_u35_f32, Log1pU35)
 UNARY32(tanh_u10_f32, TanhU10)
 UNARY32(tanh_u35_f32, TanhU35)
 extern "C" sleefcu_status sleefcu_erf_u10_f32(const float *x, float *out, size_t n, sleefcu_stream s) {
-  return launch_sorted32<explog32::ErfU10>("sleefcu_erf_u10_f32", x, out, n, s);
+  return launch_unary32<explog32::ErfU10>("sleefcu_erf_u10_f32", x, out, n, s);
 }
 extern "C" sleefcu_status sleefcu_erf_u35_f32(const float *x, float *out, size_t n, sleefcu_stream s) {
-  return launch_sorted32<explog32::ErfU35>("sleefcu_erf_u35_f32", x, out, n, s);
+  return launch_unary32<explog32::ErfU35>("sleefcu_erf_u35_f32", x, out, n, s);
 }
 
 #define LOWP(NAME, F)                                                                       \
