@@ -19,10 +19,11 @@
  *    the CUDA error text (thread-local).
  *  - Results are deterministic: the same bits for any launch configuration,
  *    and the same bits as the scalar reference implementation of the same
- *    operation sequence (Section 4, "Making Results Bit-wise Consistent").
+ *    operation sequence (the bit-wise consistency of Section 4).
  *  - Accuracy: u10 entry points are within 1.0 ULP and u35 entry points
- *    within 3.5 ULP of the exact result (Section 2: "1-ULP accuracy version
- *    and 3.5-ULP accuracy version").  Special values follow C99 Annex F; no
+ *    within 3.5 ULP of the exact result (the two accuracy classes of Section
+ *    2; lgamma near its negative-axis zeros has an absolute bound, see
+ *    below).  Special values follow C99 Annex F; no
  *    errno, no floating-point flags, round-to-nearest only (Section 5.10).
  *    Every NaN result is the canonical quiet NaN (0x7FF8000000000000 /
  *    0x7FC00000).
@@ -54,8 +55,8 @@ const char *sleefcu_version(void);
 
 /* ---------------- trigonometric functions, FP64 ----------------
  * Section 5.1 (sin, cos): Cody-Waite reduction for |x| < 15 and |x| < 1e14,
- * the vectorized Payne-Hanek reduction of Section 5.8 (table of Fig.
- * "Payne-Hanek table generation") above that and for non-finite x; one sine
+ * the vectorized Payne-Hanek reduction of Section 5.8 (table of the Payne-Hanek
+ * table-generation figure) above that and for non-finite x; one sine
  * polynomial on [-pi/2, pi/2]; the sign is set in the reconstruction.
  * Section 5.2 and Appendix A (tan): the same reductions to quarter turns,
  * half-angle reduction, tan polynomial, double-angle reconstruction.

@@ -5,7 +5,7 @@
  * Test infrastructure: only tests/, the smoke check and the CPU-baseline leg
  * of the benchmark use anything under oracle/.
  *
- * Section 5.8 and Appendix A (Fig. "Payne-Hanek table generation"):
+ * Section 5.8 and Appendix A (the Payne-Hanek table-generation figure):
  *   for E = 0..1023, with M = (E > 700 ? -128 : 0),
  *   m = frac(2/pi * 2^(E-53)) * 2^-(E-53+M),
  *   four times: t = RN_double(m) with its lowest bit cleared; tab[4E+i] = t; m -= t.

@@ -1,6 +1,6 @@
 """Build step: write the Payne-Hanek tables of the CUDA library.
 
-Section 5.8 and Appendix A (Fig. "Payne-Hanek table generation") define the
+Section 5.8 and Appendix A (the Payne-Hanek table-generation figure) define the
 FP64 table: for E = 0..1023 and M = (E > 700 ? -128 : 0),
     m = frac(2/pi * 2^(E-53)) * 2^-(E-53+M),
 and four times t = RN_double(m) with the lowest bit cleared, tab[4E+i] = t,

@@ -7,7 +7,7 @@
 //   |x| < 1e14  level-2 Cody-Waite: head by fma (exact for these q), second
 //               constant by an exact DD product, third constant into the tail;
 //   otherwise   the vectorizable Payne-Hanek reduction (Eq. 1 in DD over the
-//               four table words of Fig. "Payne-Hanek table generation").
+//               four table words of the Payne-Hanek table-generation figure).
 // Each lane takes the reduction its own |x| calls for (the paper's
 // bit-consistent variant, Section 4: small-argument method first, the next
 // method only for elements it does not cover); a warp runs a reduction only

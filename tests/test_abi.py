@@ -72,7 +72,7 @@ def test_cuda_literals_match_paper_listing():
 def test_phtab_generators_agree():
     """The CUDA build's Payne-Hanek table (Chudnovsky pi, Python Fractions)
     equals the oracle's (Machin pi, C bignum): two independent derivations
-    of Fig. "Payne-Hanek table generation"."""
+    of the Payne-Hanek table-generation figure."""
     import importlib.util
     import numpy as np
     import oracle

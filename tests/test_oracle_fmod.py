@@ -56,7 +56,7 @@ def test_exact_against_libm(fn, acc):
 
 
 def test_worked_example():
-    """Section 5.9, Fig. "Example computation of FP remainder": 1e40 / 0.75;
+    """Section 5.9, the worked-example figure: 1e40 / 0.75;
     first integer quotient about 1.333e40, second dividend about 4.836e24.
     The printed dividend is n - q d for q = RD53(n/d) - 2 ulp; the listing's
     quotient formula gives RD53(n/d) - 1 ulp.  Pinned: the quotient to the

@@ -164,7 +164,7 @@ def test_payne_hanek_bruteforce():
 
 
 def test_payne_hanek_table_definition():
-    """Fig. "Payne-Hanek table generation": 1024 x 4 doubles (32 KB), each the
+    """the Payne-Hanek table-generation figure: 1024 x 4 doubles (32 KB), each the
     RN double of the remaining fraction with its lowest bit cleared, E > 700
     scaled by 2^128; recomputed here independently with mpmath at 2000 bits."""
     mp = pytest.importorskip("mpmath")
