@@ -158,26 +158,32 @@ def launch(sleefcu, name, ins, outs, stream_ptr):
         raise RuntimeError(f"{name}: {sleefcu.last_error()}")
 
 
-def fp64_pipe_peak(sleefcu, torch, device):
-    """Measured FP64 FMA-pipe throughput (ops/s) with the library's probe."""
+def pipe_peak(sleefcu, torch, device, pipe="fp64"):
+    """Measured FMA-pipe throughput (ops/s) with the library's probe kernels
+    (8 independent FMA chains per thread, 8 blocks of 256 per SM)."""
     props = torch.cuda.get_device_properties(device)
     blocks = props.multi_processor_count * 8
-    out = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    dt, probe, iters = ((torch.float64, sleefcu.lib().sleefcu_probe_dfma, 2048) if pipe == "fp64"
+                        else (torch.float32, sleefcu.lib().sleefcu_probe_ffma, 16384))
+    out = torch.empty(blocks * 256, dtype=dt, device=device)
     st = torch.cuda.current_stream(device)
     sp = ctypes.c_void_p(st.cuda_stream)
-    iters = 2048
     for _ in range(2):
-        sleefcu.lib().sleefcu_probe_dfma(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
+        probe(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
     best = None
     for _ in range(5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
-        sleefcu.lib().sleefcu_probe_dfma(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
+        probe(ctypes.c_void_p(out.data_ptr()), blocks, iters, sp)
         b.record(st)
         b.synchronize()
         ms = a.elapsed_time(b)
         best = ms if best is None else min(best, ms)
     return blocks * 256.0 * iters * 8 / (best * 1e-3)
+
+
+def fp64_pipe_peak(sleefcu, torch, device):
+    return pipe_peak(sleefcu, torch, device, "fp64")
 
 
 def time_calls(torch, st, fn, reps=5):
@@ -196,8 +202,10 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
     """FP32 family (2^28 floats) and bf16/f16 activation forms ([8192, 28672]),
     each with its speedup over the plain FP64 / FP32 form of the function."""
     from paper_2001_09258_gb300 import inputs as I
+    from paper_2001_09258_gb300 import opcounts
     import numpy as np
     hbm = peaks.get("hbm_gbs")
+    peak_fp32 = pipe_peak(sleefcu, torch, device, "fp32")
     f32 = {}
     cache = {}
     for name in [e for e in sleefcu.entry_points() if e.endswith("_f32")]:
@@ -215,8 +223,11 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
         nbytes = 4 * (len(ins) + len(outs))
         acc = name.split("_")[1]
         base = per_fn_f64.get(f"{fn}_{acc}_f64")
+        ope = opcounts.ops_per_element_f32(name)
         f32[name] = {"gelem_s": round(g, 2), "hbm_gbs": round(nbytes * n32 / (ms * 1e-3) / 1e9, 1),
                      "hbm_frac": round(nbytes * n32 / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                     "ops_per_element": round(ope, 2),
+                     "fp32_frac": round(ope * g * 1e9 / peak_fp32, 4),
                      "speedup_vs_f64": round(g / base, 2) if base else None}
         del outs
     low = {}
@@ -231,11 +242,18 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
         ms = time_calls(torch, st, lambda: f(x.data_ptr(), o.data_ptr(), n16, sp))
         g = n16 / (ms * 1e-3) / 1e9
         base = f32.get(f"{fn}_{acc}_f32", {}).get("gelem_s")
+        ope = opcounts.ops_per_element_f32(name)
         low[name] = {"gelem_s": round(g, 2), "hbm_gbs": round(4 * n16 / (ms * 1e-3) / 1e9, 1),
                      "hbm_frac": round(4 * n16 / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                     "ops_per_element": round(ope, 2),
+                     "fp32_frac": round(ope * g * 1e9 / peak_fp32, 4),
                      "speedup_vs_f32": round(g / base, 2) if base else None}
         del x, o
     return {"fp32_family": {"n": n32, "workload": "same mixes scaled to binary32 (trig tail to 3.4e38)",
+                            "fp32_pipe_peak_tops": round(peak_fp32 / 1e12, 3),
+                            "fp32_frac_note": "algorithmic binary32 ops per element (oracle counting build, "
+                                              "mean over the workload) x Gelem/s / measured FFMA peak "
+                                              "(sleefcu_probe_ffma)",
                             "entry_points": f32},
             "bf16_f16_forms": {"shape": list(shape), "inputs": "N(0,3) rounded to the 16-bit format",
                                "entry_points": low}}
@@ -513,7 +531,9 @@ def main():
         if fn in ("fmod", "remainder"):
             st_ = int(fmod_steps(sleefcu, torch, dev[fn][0], dev[fn][1], fn == "remainder", sp).sum())
         o = opcounts.ops_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
+        dv, sq = opcounts.div_sqrt_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
         per_roof[name] = {"ops_per_element": round(o / n, 2),
+                          "div_per_element": round(dv / n, 3), "sqrt_per_element": round(sq / n, 3),
                           "fp64_frac": round(o / (avg[name] * 1e-3) / peak_fp64, 4)}
     ext = None
     if not args.no_extras:
@@ -532,6 +552,7 @@ def main():
         steps = int(fmod_steps(sleefcu, torch, dx[0], dx[1], dom.startswith("remainder"), sp).sum())
         del dx
     ops = opcounts.ops_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None, steps)
+    dv, sq = opcounts.div_sqrt_per_launch(dom, hx[0], hx[1] if len(hx) > 1 else None, steps)
     achieved = ops / (avg[dom] * 1e-3)
     roof = {"kernel": dom, "bound": "alu", "pipe": "fp64",
             "achieved": round(achieved / 1e12, 5), "peak": round(peak_fp64 / 1e12, 5),
@@ -539,7 +560,11 @@ def main():
             "frac": round(achieved / peak_fp64, 4),
             "peak_source": "measured in this run with sleefcu_probe_dfma (8 independent FMA chains "
                            "per thread, all SMs)",
-            "ops_per_element": round(ops / n, 3), "traffic": None}
+            "ops_per_element": round(ops / n, 3), "div_per_element": round(dv / n, 3),
+            "sqrt_per_element": round(sq / n, 3),
+            "ops_source": "oracle counting build, per path class (paper_2001_09258_gb300/opcounts.json), "
+                          "weighted by this launch's path mix",
+            "traffic": None}
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:

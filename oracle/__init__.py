@@ -112,3 +112,67 @@ def ph_table():
     ib = np.empty(1024, dtype=np.uint8)
     lib().oracle_ph_table_copy(tab.ctypes.data, ib.ctypes.data)
     return tab, ib
+
+
+# ---- counting build (oracle/counting): operation tallies of the same sources ----
+COUNT_CATS = ("add", "mul", "fma", "div", "sqrt", "rnd", "cmp", "cvt", "scl")
+ALGO_CATS = ("add", "mul", "fma", "div", "sqrt", "rnd")
+_clib = None
+
+
+def count_lib():
+    global _clib
+    if _clib is None:
+        _clib = ctypes.CDLL(_build.build_count())
+        _clib.oracle_count_apply.restype = ctypes.c_int
+        _clib.oracle_count_apply.argtypes = [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]
+        _clib.oracle_count_ph.restype = None
+        _clib.oracle_count_ph.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+        _clib.oracle_count_ncat.restype = ctypes.c_int
+        assert _clib.oracle_count_ncat() == len(COUNT_CATS)
+    return _clib
+
+
+def _tally_dict(t):
+    t = t.reshape(2, len(COUNT_CATS))
+    return {p: dict(zip(COUNT_CATS, (int(v) for v in t[i]))) for i, p in enumerate(("f64", "f32"))}
+
+
+def count(name, x, y=None):
+    """Run the counting build of `name` over x (and y) on one thread.
+    Returns (outputs as apply() returns them, tallies) with tallies =
+    {"f64": {category: total}, "f32": {...}} summed over all elements."""
+    k = kind(name)
+    if k == 0:
+        raise KeyError(f"oracle has no function {name!r}")
+    dt = np.float64 if k < 10 else (np.float32 if k < 20 else np.uint16)
+    x = np.ascontiguousarray(x, dtype=dt)
+    out = np.empty_like(x)
+    out2 = np.empty_like(x) if k in (K_SC64, K_SC32) else None
+    yp = None
+    if k in (K_B64, K_B32):
+        y = np.ascontiguousarray(y, dtype=dt)
+        assert y.size == x.size
+        yp = y.ctypes.data
+    t = np.zeros(2 * len(COUNT_CATS), dtype=np.uint64)
+    rc = count_lib().oracle_count_apply(name.encode(), x.ctypes.data, yp, out.ctypes.data,
+                                        out2.ctypes.data if out2 is not None else None, x.size,
+                                        t.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_count_apply({name}) failed: {rc}")
+    return ((out, out2) if out2 is not None else out), _tally_dict(t)
+
+
+def count_ph(x):
+    """Tallies of the binary64 Payne-Hanek reduction alone over x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.zeros(2 * len(COUNT_CATS), dtype=np.uint64)
+    count_lib().oracle_count_ph(x.ctypes.data, x.size, t.ctypes.data)
+    return _tally_dict(t)
+
+
+def algo_ops(tally, prec="f64"):
+    """Algorithmic operation count: add + mul + fma + div + sqrt + rnd."""
+    return sum(tally[prec][c] for c in ALGO_CATS)

@@ -26,9 +26,9 @@
 #define L2LF 0x1.7f7d1cp-20f
 
 static float pow2if(int k) { return ldexpf(1.0f, k); }
-static float scale2f(float y, int k) {
+static float scale2f(float y, int k) {   /* as scale2 of the FP64 file */
   int k1 = k / 2, k2 = k - k1;
-  return (y * pow2if(k1)) * pow2if(k2);
+  return ldexpf(ldexpf(y, k1), k2);
 }
 
 /* ---------------- exp ---------------- */

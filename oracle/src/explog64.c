@@ -26,13 +26,12 @@
 #define L2H 0x1.62e42fefa3800p-1     /* ln2 to 42 bits: e*L2H is exact for |e| < 2^11 */
 #define L2L 0x1.ef35793c76730p-45    /* RN(ln2 - L2H) */
 
-/* 2^k for integer k in [-1022, 1023] */
-static double pow2i(int k) { return ldexp(1.0, k); }
-
-/* y * 2^k in two multiplications (each factor a normal power of two) */
+/* y * 2^k in two steps, y * 2^k1 then * 2^k2 with both factors normal
+ * powers of two, so that the result is rounded once even when it is
+ * subnormal; each step is an exponent operation (ldexp, correctly rounded) */
 static double scale2(double y, int k) {
   int k1 = k / 2, k2 = k - k1;
-  return (y * pow2i(k1)) * pow2i(k2);
+  return ldexp(ldexp(y, k1), k2);
 }
 double oracle_scale2(double y, int k) { return scale2(y, k); }
 

@@ -29,7 +29,8 @@
 extern const float *oracle_ph_tabf(void);
 extern const uint8_t *oracle_ph_ibitf(void);
 
-/* Payne-Hanek in FF: s in [-pi/4, pi/4] and the quarter-turn count */
+/* Payne-Hanek in FF: s in [-pi/4, pi/4] and the quarter-turn count mod 4
+ * (the steps of the FP64 form, in float-float) */
 ff_t oracle_ph_reduce_ff(float d, int *qo) {
   const float *tab = oracle_ph_tabf();
   float df = isfinite(d) ? d : 0.0f;
@@ -41,16 +42,16 @@ ff_t oracle_ph_reduce_ff(float d, int *qo) {
   int q = 0;
   for (int i = 0; i < 4; i++) {
     ff_t y = ffmul_f2_f_f(u, tab[ex * 4 + i]);
-    x = ffadd2_f2_f2_f2(x, y);
-    float r = rintf(4 * x.x);
-    q += (int)(r - 4 * rintf(x.x));
-    x.x -= r * 0.25f;
+    x = i == 0 ? y : ffadd2_f2_f2_f2(x, y);
+    float r = rintf(ldexpf(x.x, 2));
+    q += low2_of_integralf(r);
+    x.x = fmaf(r, -0.25f, x.x);
     x = ffnormalize_f2_f2(x);
   }
   x = ffmul_f2_f2_f2(x, ff(TWOPIF_H, TWOPIF_L));
   q += 2 * (int)(fbits(df) & oracle_ph_ibitf()[ex] & 1);
   if (!isfinite(d)) x.x = NAN;
-  *qo = q;
+  *qo = q & 3;
   return x;
 }
 

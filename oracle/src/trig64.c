@@ -31,9 +31,15 @@ extern const double *oracle_ph_tab(void);
 extern const uint8_t *oracle_ph_ibit(void);
 
 /* Section 5.8 / Appendix A: returns 2 pi * rfrac-reduced turns as a DD in
- * [-pi/4, pi/4] and the quarter-turn count in *q (only q mod 4 is used).
+ * [-pi/4, pi/4] and the quarter-turn count mod 4 in *q.
  * The table drops M*I(E)/2 turns; a half turn is put back through q when the
- * mantissa and I(E) are both odd. */
+ * mantissa and I(E) are both odd.
+ * Each of the four steps of Eq. (ph0) adds M*F_i(E) (the first to zero, so
+ * the product itself), takes r = round(4 x.hi) quarter turns off the head
+ * (x.hi - r/4, exact, one fma) and renormalizes.  Only q mod 4 is used by
+ * the callers, and the paper's per-step increment r - 4 round(x.hi) is r
+ * mod 4, so q takes the two low bits of the integer r; 4 x.hi is an exact
+ * exponent step. */
 dd_t oracle_ph_reduce_dd(double d, int *qo) {
   const double *tab = oracle_ph_tab();
   double df = isfinite(d) ? d : 0.0;
@@ -45,16 +51,16 @@ dd_t oracle_ph_reduce_dd(double d, int *qo) {
   int q = 0;
   for (int i = 0; i < 4; i++) {
     dd_t y = ddmul_d2_d_d(u, tab[ex * 4 + i]);
-    x = ddadd2_d2_d2_d2(x, y);
-    double r = rint(4 * x.x);
-    q += (int)(r - 4 * rint(x.x));
-    x.x -= r * 0.25;
+    x = i == 0 ? y : ddadd2_d2_d2_d2(x, y);
+    double r = rint(ldexp(x.x, 2));
+    q += low2_of_integral(r);
+    x.x = fma(r, -0.25, x.x);
     x = ddnormalize_d2_d2(x);
   }
   x = ddmul_d2_d2_d2(x, dd(TWOPI_H, TWOPI_L));
   q += 2 * (int)(dbits(df) & oracle_ph_ibit()[ex] & 1);
   if (!isfinite(d)) x.x = NAN;
-  *qo = q;
+  *qo = q & 3;
   return x;
 }
 
