@@ -283,10 +283,77 @@ __device__ __forceinline__ void run_sorted(const Desc &D, long long b, long long
   }
 }
 
+// binary32 functors with a deferred rare path (DEFER, as in k_defer32): per
+// sub-tile, every lane runs the main path (deferred lanes on the stand-in
+// argument), the deferred arguments are queued in shared memory and, after a
+// barrier, evaluated densely and written over the stand-in results
+template <Kind K, class F>
+__device__ __forceinline__ void run_deferred(const Desc &D, long long b, long long e, SortSmem &S) {
+  constexpr bool DUAL = (K == SC32);
+  F f;
+  const float *x = (const float *)D.x;
+  float *o = (float *)D.out, *o2 = (float *)D.out2;
+  float *qx = (float *)S.x;
+  const int tid = threadIdx.x, nt = blockDim.x, ept = kSubTile / nt;
+  const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
+  for (long long base = b; base < e; base += kSubTile) {
+    const int valid = (int)(e - base < kSubTile ? e - base : kSubTile);
+    if (tid == 0) S.cnt[0] = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 0; j < ept; j++) {
+      const int el = j * nt + tid;
+      const bool in = el < valid;
+      float v = in ? x[base + el] : 0.0f;
+      const bool r = in && F::defer(v);
+      const unsigned m = __ballot_sync(0xffffffffu, r);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        int p = 0;
+        if ((int)lane == leader) p = atomicAdd(&S.cnt[0], __popc(m));
+        p = __shfl_sync(0xffffffffu, p, leader);
+        if (r) {
+          qx[p + __popc(m & lt)] = v;
+          S.idx[p + __popc(m & lt)] = (unsigned short)el;
+        }
+      }
+      if (r) v = F::kStandIn;
+      if constexpr (DUAL) {
+        float a, c;
+        f.dual(v, a, c);
+        if (in) {
+          o[base + el] = a;
+          o2[base + el] = c;
+        }
+      } else {
+        const float a = f(v);
+        if (in) o[base + el] = a;
+      }
+    }
+    __syncthreads();
+    const int q = S.cnt[0];
+    for (int k = tid; k < q; k += nt) {
+      const long long g = base + S.idx[k];
+      if constexpr (DUAL) {
+        f.dual(qx[k], o[g], o2[g]);
+      } else {
+        o[g] = f(qx[k]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // evaluate elements [b, e) of one array; threads of the CTA stride over them,
 // vec > 1 uses 16-byte accesses when the tile start is aligned
 template <Kind K, class F>
 __device__ __forceinline__ void run(const Desc &D, long long b, long long e, int vec, SortSmem &S) {
+  if constexpr ((K == U32 || K == SC32) && has_defer<F>::value) {
+    if (kSubTile % blockDim.x == 0 && kSubTile / blockDim.x <= kMaxEPT) {   // blocks of 128..1024 threads
+      run_deferred<K, F>(D, b, e, S);
+      return;
+    }
+  }
   // FP64 functors with several paths always; binary32 ones only where the
   // paths differ by an order of magnitude (gamma's eight classes)
   if constexpr (sortable<F>::value && K != BF && K != HF &&

@@ -540,6 +540,10 @@ struct QuarterPaths {
     uint32_t ab = fbits(x) & ABS32;
     return ab < B125 ? 0 : (ab < B2P20 ? 1 : 2);
   }
+  // deferred Payne-Hanek path, as for sin and cos
+  static constexpr bool DEFER = true;
+  static constexpr float kStandIn = 1.5f;
+  __device__ static bool defer(float x) { return (fbits(x) & ABS32) >= B2P20; }
 };
 struct TanU10 : QuarterPaths {
   __device__ float operator()(float x) const {

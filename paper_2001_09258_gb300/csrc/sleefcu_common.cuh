@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 #include <stddef.h>
 #include "../../include/sleefcu.h"
 #include "sleefcu_dd.cuh"
@@ -565,11 +566,119 @@ __global__ void __launch_bounds__(kBlock) k_sorted32(const float *x, float *out,
   }
 }
 
+// Binary32 kernel with a deferred rare path.  A functor that declares
+// DEFER has one expensive path that ordinary data takes rarely (the
+// Payne-Hanek reduction of the trigonometric functions); in a plain kernel
+// every warp holding one such lane runs that path with the others idle.
+// Here the main pass evaluates every lane on one path: a lane with
+// F::defer(x) runs on the stand-in argument F::kStandIn (a main-path value)
+// and its true argument and position go to a shared-memory queue (one
+// ballot and one atomic per warp); after a barrier the block evaluates the
+// queue densely and overwrites those outputs.  Each output is still F(x) of
+// its own argument, so results do not depend on the grouping.  Blocks take
+// chunks of kDeferChunk elements (two 16-byte vectors per thread).
+constexpr int kDeferVec = 2;
+constexpr int kDeferChunk = kBlock * 4 * kDeferVec;
+
+template <class F, class = void>
+struct has_defer : std::false_type {};
+template <class F>
+struct has_defer<F, std::void_t<decltype(F::DEFER)>> : std::bool_constant<F::DEFER> {};
+
+template <class F, int NOUT>
+__device__ __forceinline__ void defer_eval(const F &f, float v, float &a, float &b) {
+  if constexpr (NOUT == 1) {
+    a = f(v);
+    (void)b;
+  } else {
+    f.dual(v, a, b);
+  }
+}
+
+template <class F, int NOUT>
+__global__ void __launch_bounds__(kBlock) k_defer32(const float *x, float *o1, float *o2, size_t n) {
+  __shared__ float qx[kDeferChunk];
+  __shared__ unsigned short qi[kDeferChunk];
+  __shared__ int qn;
+  F f;
+  const int tid = threadIdx.x;
+  const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
+  const size_t nq = n >> 2;
+  const size_t per = (size_t)kBlock * kDeferVec;
+  const size_t nchunks = (nq + per - 1) / per;
+  const float4 *x4 = reinterpret_cast<const float4 *>(x);
+  float4 *a4 = reinterpret_cast<float4 *>(o1);
+  float4 *b4 = reinterpret_cast<float4 *>(o2);
+  for (size_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    if (tid == 0) qn = 0;
+    __syncthreads();
+    const size_t q0 = c * per;
+#pragma unroll 1
+    for (int v = 0; v < kDeferVec; v++) {
+      const int local = v * kBlock + tid;               // 16-byte vector within the chunk
+      const size_t qv = q0 + local;
+      const bool in = qv < nq;
+      float4 t = in ? __ldcs(x4 + qv) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const bool r = in && F::defer(e[k]);
+        const unsigned m = __ballot_sync(0xffffffffu, r);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int b = 0;
+          if ((int)lane == leader) b = atomicAdd(&qn, __popc(m));
+          b = __shfl_sync(0xffffffffu, b, leader);
+          if (r) {
+            qx[b + __popc(m & lt)] = e[k];
+            qi[b + __popc(m & lt)] = (unsigned short)(local * 4 + k);
+          }
+        }
+        if (r) e[k] = F::kStandIn;
+      }
+      float4 ra, rb;
+      defer_eval<F, NOUT>(f, e[0], ra.x, rb.x);
+      defer_eval<F, NOUT>(f, e[1], ra.y, rb.y);
+      defer_eval<F, NOUT>(f, e[2], ra.z, rb.z);
+      defer_eval<F, NOUT>(f, e[3], ra.w, rb.w);
+      if (in) {
+        __stcs(a4 + qv, ra);
+        if constexpr (NOUT == 2) __stcs(b4 + qv, rb);
+      }
+    }
+    __syncthreads();
+    const int m = qn;
+    for (int k = tid; k < m; k += kBlock) {
+      const size_t g = q0 * 4 + qi[k];
+      float a, b;
+      defer_eval<F, NOUT>(f, qx[k], a, b);
+      o1[g] = a;
+      if constexpr (NOUT == 2) o2[g] = b;
+    }
+    __syncthreads();
+  }
+  const size_t rem = n & 3;
+  if (blockIdx.x == 0 && (size_t)tid < rem) {
+    const size_t g = n - rem + tid;
+    float a, b;
+    defer_eval<F, NOUT>(f, x[g], a, b);
+    o1[g] = a;
+    if constexpr (NOUT == 2) o2[g] = b;
+  }
+}
+
 template <class F>
 sleefcu_status launch_unary32(const char *name, const float *x, float *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   cudaStream_t st = (cudaStream_t)s;
+  if constexpr (has_defer<F>::value) {
+    if (aligned16(x) && aligned16(out)) {
+      auto k = k_defer32<F, 1>;
+      k<<<grid_for((const void *)k, (n + 3) / 4 / kDeferVec), kBlock, 0, st>>>(x, out, out, n);
+      return check_launch(name);
+    }
+  }
   if (aligned16(x) && aligned16(out)) {
     auto k = k_unary32<F, true>;
     k<<<grid_for((const void *)k, (n + 3) / 4), kBlock, 0, st>>>(x, out, n);
@@ -609,6 +718,13 @@ sleefcu_status launch_dual32(const char *name, const float *x, float *o1, float 
   if (n == 0) return SLEEFCU_OK;
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   cudaStream_t st = (cudaStream_t)s;
+  if constexpr (has_defer<F>::value) {
+    if (aligned16(x) && aligned16(o1) && aligned16(o2)) {
+      auto k = k_defer32<F, 2>;
+      k<<<grid_for((const void *)k, (n + 3) / 4 / kDeferVec), kBlock, 0, st>>>(x, o1, o2, n);
+      return check_launch(name);
+    }
+  }
   if (aligned16(x) && aligned16(o1) && aligned16(o2)) {
     auto k = k_dual32<F, true>;
     k<<<grid_for((const void *)k, (n + 3) / 4), kBlock, 0, st>>>(x, o1, o2, n);

@@ -127,6 +127,11 @@ struct Paths {
     if (COS && ab < B1) return 3;
     return ab < B125 ? 0 : (ab < B2P20 ? 1 : 2);
   }
+  // the Payne-Hanek path (|x| >= 2^20 or non-finite) is deferred by the
+  // plain binary32 kernel; 1.5 stands in for it on the Cody-Waite path
+  static constexpr bool DEFER = true;
+  static constexpr float kStandIn = 1.5f;
+  __device__ static bool defer(float x) { return (fbits(x) & ABS32) >= B2P20; }
 };
 
 struct SinU10 : Paths<false> {

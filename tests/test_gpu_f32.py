@@ -49,3 +49,37 @@ def test_c3_workload_2p24(name):
 def test_c3_full_size_2p28(name):
     """2^28 floats of the FP32 bench workload, every output compared."""
     check(name, I.workload(name.split("_")[0], 1 << 28, dtype=F))
+
+
+DEFERRED = ["sin_u10_f32", "sin_u35_f32", "cos_u10_f32", "cos_u35_f32", "tan_u10_f32", "tan_u35_f32",
+            "sincos_u10_f32", "sincos_u35_f32"]
+
+
+def _deferral_cases():
+    """Arrays for the deferred Payne-Hanek queue of the binary32 trig kernels:
+    no deferred lane, every lane deferred, a scattered tenth, whole 2048-element
+    chunks of each kind back to back, and deferred lanes on chunk edges; sizes
+    around the chunk and the 16-byte vector."""
+    cw = I.uniform("dq/cw", 20000, -100, 100).astype(F)
+    ph = I.loguniform("dq/ph", 20000, 1.1e6, 3.4e38).astype(F)
+    pick = (I.raw("dq/pick", 20000) % np.uint64(10)) == 0
+    mix = np.where(pick, ph, cw)
+    blocks = np.concatenate([cw[:2048], ph[:2048], cw[2048:4096], ph[2048:4096], cw[4096:4100]])
+    edges = cw[:6151].copy()
+    for i in (0, 3, 2047, 2048, 4095, 4096, 6143, 6150):
+        edges[i] = ph[i]
+    spec = I.specials_f32()
+    return {"none": cw[:8195], "all": ph[:8195], "tenth": mix, "blocks": blocks, "edges": edges,
+            "specials": np.concatenate([spec, cw[:61]]), "n1": ph[:1], "n5": mix[:5], "n2049": mix[:2049]}
+
+
+@pytest.mark.parametrize("name", DEFERRED)
+@pytest.mark.parametrize("case", ["none", "all", "tenth", "blocks", "edges", "specials", "n1", "n5", "n2049"])
+def test_deferred_payne_hanek_queue(name, case):
+    x = _deferral_cases()[case]
+    got, want = gpu_call(name, x), oracle.apply(name, x)
+    if isinstance(want, tuple):
+        assert_bitexact(got[0], want[0], x, name + "/sin")
+        assert_bitexact(got[1], want[1], x, name + "/cos")
+    else:
+        assert_bitexact(got, want, x, name)
