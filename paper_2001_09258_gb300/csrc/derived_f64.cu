@@ -128,18 +128,18 @@ struct Exp10U35 {
 
 // ---------------- expm1 ----------------
 __device__ __forceinline__ double expm1_out(double x, double y) {
-  bool inr = x > -40.0 && x < 710.0;
-  if (x == 0.0) y = x;
-  if (!inr) y = x >= 710.0 ? from_bits(INF) : (x <= -40.0 ? -1.0 : from_bits(QNAN64));
+  bool inr = gt_c(x, -40.0) && lt_c(x, 710.0);
+  if (eq_0(x)) y = x;
+  if (!inr) y = ge_c(x, 710.0) ? from_bits(INF) : (le_c(x, -40.0) ? -1.0 : from_bits(QNAN64));
   return canon(y);
 }
 struct Expm1U10 {
   __device__ double operator()(double x) const {
-    double xc = (x > -40.0 && x < 710.0) ? x : 0.0;
+    double xc = (gt_c(x, -40.0) && lt_c(x, 710.0)) ? x : 0.0;
     double k;
     d2 s = expk_s(D2(xc, 0.0), k);
     double y;
-    if (k > 1000.0) {
+    if (int_of(k) > 1000) {
       d2 e = add_d_d2_fast(1.0, s);
       y = scale2(__dadd_rn(e.x, e.y), int_of(k));
     } else {
@@ -151,11 +151,11 @@ struct Expm1U10 {
 };
 struct Expm1U35 {
   __device__ double operator()(double x) const {
-    double xc = (x > -40.0 && x < 710.0) ? x : 0.0;
+    double xc = (gt_c(x, -40.0) && lt_c(x, 710.0)) ? x : 0.0;
     double k;
     double v = em1_u35(xc, k);
     double y;
-    if (k > 1000.0) {
+    if (int_of(k) > 1000) {
       y = scale2(__dadd_rn(1.0, v), int_of(k));
     } else {
       double p = pow2i(int_of(k));
@@ -213,14 +213,16 @@ struct Log10U35 {
   }
 };
 __device__ __forceinline__ double log1p_out(double x, double y) {
-  if (x == -1.0) return from_bits(0xFFF0000000000000ull);
-  if (x < -1.0 || x != x) return from_bits(QNAN64);
-  if (bits(x) == INF) return from_bits(INF);
-  if (x == 0.0) return x;
+  uint64_t b = bits(x), ab = b & ABS64;
+  if (b == (SIGN | ONE)) return from_bits(0xFFF0000000000000ull);       // x = -1
+  if (((b >> 63) && ab > ONE) || ab > EXP64) return from_bits(QNAN64);  // x < -1 or NaN
+  if (b == INF) return from_bits(INF);
+  if (ab == 0) return x;
   return canon(y);
 }
 __device__ __forceinline__ double log1p_arg(double x) {
-  return (x > -1.0 && (bits(x) & ABS64) <= DMAX) ? x : 0.0;
+  uint64_t b = bits(x), ab = b & ABS64;
+  return (!((b >> 63) && ab >= ONE) && ab <= DMAX) ? x : 0.0;           // -1 < x < inf
 }
 struct Log1pU10 {
   __device__ double operator()(double x) const {
@@ -243,7 +245,7 @@ __device__ __forceinline__ double cbrt_core(double x) {
   bool fin = ab - 1 < INF - 1;                     // finite and non-zero
   double a0 = fin ? from_bits(ab) : 1.0;
   int off = 0;
-  if (a0 < 0x1p-1022) { a0 = __dmul_rn(a0, 0x1p54); off = 18; }
+  if (bits(a0) < 0x0010000000000000ull) { a0 = __dmul_rn(a0, 0x1p54); off = 18; }   // a0 > 0
   uint64_t b0 = bits(a0);
   int e = (int)(b0 >> 52) - 1023;
   int q = e >= 0 ? e / 3 : -((2 - e) / 3);
@@ -286,7 +288,7 @@ struct SinhU10 {
     double k;
     d2 s = expk_s(D2(ac, 0.0), k);
     double y;
-    if (ac > 22.0) {
+    if (bits(ac) > 0x4036000000000000ull) {   // ac > 22
       d2 e = add_d_d2_fast(1.0, s);
       y = scale2(__dadd_rn(e.x, e.y), int_of(k) - 1);
     } else {
@@ -310,7 +312,7 @@ struct CoshU10 {
     d2 s = expk_s(D2(ac, 0.0), k);
     d2 e = add_d_d2_fast(1.0, s);
     double y;
-    if (ac > 22.0) {
+    if (bits(ac) > 0x4036000000000000ull) {   // ac > 22
       y = scale2(__dadd_rn(e.x, e.y), int_of(k) - 1);
     } else {
       d2 E = scale_d2(e, pow2i(int_of(k)));
@@ -344,7 +346,7 @@ struct SinhU35 {
     double k;
     double v = em1_u35(ac, k);
     double y;
-    if (ac > 22.0) {
+    if (bits(ac) > 0x4036000000000000ull) {   // ac > 22
       y = scale2(__dadd_rn(1.0, v), int_of(k) - 1);
     } else {
       double p = pow2i(int_of(k));
@@ -365,7 +367,7 @@ struct CoshU35 {
     double k;
     double v = em1_u35(ac, k);
     double y;
-    if (ac > 22.0) {
+    if (bits(ac) > 0x4036000000000000ull) {   // ac > 22
       y = scale2(__dadd_rn(1.0, v), int_of(k) - 1);
     } else {
       double E = __dmul_rn(__dadd_rn(1.0, v), pow2i(int_of(k)));
@@ -397,7 +399,7 @@ struct AsinhU10 {
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x), ab = bx & ABS64;
     double ac = ab <= DMAX ? from_bits(ab) : 1.0;
-    bool big = ac > 0x1p500;
+    bool big = bits(ac) > 0x5F30000000000000ull;   // ac > 2^500
     d2 arg;
     if (big) {
       arg = D2(ac, 0.0);
@@ -418,9 +420,9 @@ struct AcoshU10 {
   __device__ static int cls(double x) { return cls_500(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
-    bool inr = x >= 1.0 && bx <= DMAX;
+    bool inr = bx >= ONE && bx <= DMAX;              // 1 <= x < inf
     double xc = inr ? x : 1.0;
-    bool big = xc > 0x1p500;
+    bool big = bits(xc) > 0x5F30000000000000ull;   // xc > 2^500
     d2 arg;
     if (big) {
       arg = D2(xc, 0.0);
@@ -431,7 +433,7 @@ struct AcoshU10 {
     d2 r = log_dd(arg);
     if (big) r = add_d2d2(r, D2(L2A, L2B));
     double y = __dadd_rn(r.x, r.y);
-    if (xc == 1.0) y = 0.0;
+    if (bits(xc) == ONE) y = 0.0;
     if (!inr) y = bx == INF ? from_bits(INF) : from_bits(QNAN64);
     return canon(y);
   }
@@ -508,10 +510,14 @@ __device__ __forceinline__ d2 erf_s(double a) {
   in = add_d2d2(D2(kErfH[2], kErfH[3]), mul_d2d2(T, in));
   return add_d2d2(D2(kErfH[0], kErfH[1]), mul_d2d2(T, in));
 }
-__device__ __forceinline__ int erfc_iv(double a) { return a < 2.0 ? 0 : (a < 4.0 ? 1 : 2); }
+// interval bounds as bit patterns: a >= 0 (or +NaN), so the order of the
+// bits is the order of the values
+constexpr uint64_t BE1 = 0x3FF0000000000000ull, BE2 = 0x4000000000000000ull, BE4 = 0x4010000000000000ull;
+constexpr uint64_t BE6 = 0x4018000000000000ull, BE8 = 0x4020000000000000ull, BE275 = 0x403B800000000000ull;
+__device__ __forceinline__ int erfc_iv(double a) { return bits(a) < BE2 ? 0 : (bits(a) < BE4 ? 1 : 2); }
 // F(a) = erfc(a) e^(a^2) as a DD, 1 <= a <= 27.5
 __device__ __forceinline__ d2 erfc_F(double a) {
-  if (a < 8.0) {
+  if (bits(a) < BE8) {
     int i = erfc_iv(a);
     double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
     double p = poly_p<22>(u, kErfcFP[i]);
@@ -539,17 +545,17 @@ __device__ __forceinline__ double scale2_two(double y, int k) {
 struct ErfU10 {
   static constexpr int NCLS = 5;
   __device__ static int cls(double x) {
-    double a = from_bits(bits(x) & ABS64);
-    return a < 1.0 ? 0 : (a < 2.0 ? 1 : (a < 4.0 ? 2 : (a < 6.0 ? 3 : 4)));
+    uint64_t a = bits(x) & ABS64;
+    return a < BE1 ? 0 : (a < BE2 ? 1 : (a < BE4 ? 2 : (a < BE6 ? 3 : 4)));
   }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     double a = from_bits(bx & ABS64);
     double y;
-    if (a < 1.0) {
+    if (bits(a) < BE1) {
       d2 e = mul_d2_d(erf_s(a), a);
       y = __dadd_rn(e.x, e.y);
-    } else if (a < 6.0) {
+    } else if (bits(a) < BE6) {
       double k;
       d2 c = erfc_core(a, k);
       c = scale_d2(c, pow2i(int_of(k)));
@@ -565,24 +571,24 @@ struct ErfU10 {
 struct ErfcU10 {
   static constexpr int NCLS = 6;
   __device__ static int cls(double x) {
-    double a = from_bits(bits(x) & ABS64);
-    return a < 1.0 ? 0 : (a < 2.0 ? 1 : (a < 4.0 ? 2 : (a < 8.0 ? 3 : (a <= 27.5 ? 4 : 5))));
+    uint64_t a = bits(x) & ABS64;
+    return a < BE1 ? 0 : (a < BE2 ? 1 : (a < BE4 ? 2 : (a < BE8 ? 3 : (a <= BE275 ? 4 : 5))));
   }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     double a = from_bits(bx & ABS64);
     double y;
-    if (a < 1.0) {
+    if (bits(a) < BE1) {
       d2 e = mul_d2_d(erf_s(a), a);
-      if (x > 0.0) e = neg_d2(e);
+      if (gt_0(x)) e = neg_d2(e);
       d2 r = add_d_d2(1.0, e);
       y = __dadd_rn(r.x, r.y);
-    } else if (a <= 27.5) {
+    } else if (bits(a) <= BE275) {
       double k;
       d2 c = erfc_core(a, k);
-      if (x > 0.0) {
+      if (gt_0(x)) {
         y = scale2_two(__dadd_rn(c.x, c.y), int_of(k));
-      } else if (a < 8.0) {
+      } else if (bits(a) < BE8) {
         c = scale_d2(c, pow2i(int_of(k)));
         d2 r = add_d_d2(2.0, neg_d2(c));
         y = __dadd_rn(r.x, r.y);
@@ -590,7 +596,7 @@ struct ErfcU10 {
         y = 2.0;
       }
     } else {
-      y = x > 0.0 ? 0.0 : 2.0;
+      y = gt_0(x) ? 0.0 : 2.0;
     }
     if (is_nan_b(bx)) y = from_bits(QNAN64);
     return canon(y);
@@ -603,10 +609,10 @@ struct ErfU35 {
     uint64_t bx = bits(x);
     double a = from_bits(bx & ABS64);
     double y;
-    if (a < 1.0) {
+    if (bits(a) < BE1) {
       double t = __dmul_rn(a, a);
       y = __dmul_rn(a, __fma_rn(t, __fma_rn(t, poly(t, kErfP), kErfH[2]), kErfH[0]));
-    } else if (a < 6.0) {
+    } else if (bits(a) < BE6) {
       int i = erfc_iv(a);
       double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
       double F = __fma_rn(u, __fma_rn(u, poly_p<22>(u, kErfcFP[i]), kErfcFH[i][2]), kErfcFH[i][0]);

@@ -114,10 +114,10 @@ __device__ __forceinline__ double expk(d2 Y) {
 // with z = 2(m-1)/(m+1) in DD (Section 5.5 on a DD argument)
 __device__ __forceinline__ d2 logm_u10(d2 a, int &e) {
   int off = 0;
-  if (a.x < 0x1p-1022) { a = scale_d2(a, 0x1p64); off = 64; }
+  if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
   int ex = (int)(bits(a.x) >> 52) - 1023;
   d2 m = scale_d2(a, pow2_any(-ex));
-  if (m.x >= 1.5) { m = scale_d2(m, 0.5); ex++; }
+  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
   d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
   d2 den = add_d_d2(1.0, m);
   d2 z = div_d2d2(num, den);
@@ -130,10 +130,10 @@ __device__ __forceinline__ d2 logm_u10(d2 a, int &e) {
 // the same in double for the 3.5-ULP forms (z rounded once)
 __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   int off = 0;
-  if (a.x < 0x1p-1022) { a = scale_d2(a, 0x1p64); off = 64; }
+  if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
   int ex = (int)(bits(a.x) >> 52) - 1023;
   d2 m = scale_d2(a, pow2_any(-ex));
-  if (m.x >= 1.5) { m = scale_d2(m, 0.5); ex++; }
+  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
   double num = __dmul_rn(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
   double z = __ddiv_rn(num, __dadd_rn(1.0, m.x));
   double t = __dmul_rn(z, z);
@@ -146,10 +146,10 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
 // in DD
 __device__ __forceinline__ d2 logk_dd(d2 y) {
   int off = 0;
-  if (y.x < 0x1p-1022) { y = scale_d2(y, 0x1p64); off = 64; }
+  if (lt_c(y.x, 0x1p-1022)) { y = scale_d2(y, 0x1p64); off = 64; }
   int ex = (int)(bits(y.x) >> 52) - 1023;
   d2 m = scale_d2(y, pow2_any(-ex));
-  if (m.x >= 1.5) { m = scale_d2(m, 0.5); ex++; }
+  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
   d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
   d2 z = div_d2d2(num, add_d_d2(1.0, m));
   d2 t = sqr_d2(z);

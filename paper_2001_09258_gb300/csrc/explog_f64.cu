@@ -119,8 +119,8 @@ struct PowU10 {
     bool xneg = (bx >> 63) && ax != 0 && !xnan;    // x < 0
     uint64_t a = (ax - 1) < DMAX ? ax : 0x3FF0000000000000ull;
     double yc = yfin ? y : 0.0;
-    bool yint = yfin && (y == trunc(y));
-    bool yodd = yint && ay < 0x4340000000000000ull && (((uint64_t)(int64_t)y) & 1);   // |y| < 2^53
+    bool yint = yfin && integral_b(ay);
+    bool yodd = yfin && odd_int_b(ay);
     double r = expk(mul_d2_d(logk(a), yc));
     if (xneg && yodd) r = -r;
     if (xneg && xfin && yfin && !yint) r = from_bits(QNAN64);

@@ -48,6 +48,15 @@ static __constant__ double kSpP[11] = {
 
 __device__ __forceinline__ d2 neg(d2 a) { return D2(-a.x, -a.y); }
 
+// bounds as bit patterns; the comparisons below are on positive values (or
+// on |x|), whose bit order is their value order, so they run on the
+// integer pipe
+constexpr uint64_t G05 = 0x3FE0000000000000ull, G075 = 0x3FE8000000000000ull, G125 = 0x3FF4000000000000ull;
+constexpr uint64_t G175 = 0x3FFC000000000000ull, G25 = 0x4004000000000000ull, G7 = 0x401C000000000000ull;
+constexpr uint64_t G8 = 0x4020000000000000ull, G172 = 0x4065800000000000ull, G190 = 0x4067C00000000000ull;
+constexpr uint64_t G1015 = 0x7F60000000000000ull, G52 = 0x4330000000000000ull;
+
+
 // lgamma(2 + e), -0.25 <= e < 0.5
 __device__ __forceinline__ d2 lg_r2(d2 e) {
   double p = poly_p<16>(e.x, kLgR2P);
@@ -73,26 +82,27 @@ __device__ __forceinline__ d2 lg_stirling(d2 y) {
 }
 // lgamma of a DD y > 0
 __device__ __forceinline__ d2 lgamma_pos(d2 y) {
-  if (y.x >= 8.0) return lg_stirling(y);
-  if (y.x >= 1.75 && y.x < 2.5) return lg_r2(norm_d2(add_d2_d(y, -2.0)));
-  if (y.x >= 1.25 && y.x < 1.75) return lg_m(norm_d2(add_d2_d(y, -1.5)));
-  if (y.x >= 0.5 && y.x < 1.25) {
-    d2 r = y.x < 0.75 ? lg_m(norm_d2(add_d2_d(y, -0.5))) : lg_r2(norm_d2(add_d2_d(y, -1.0)));
+  const uint64_t b = bits(y.x);                       // y.x > 0 and finite
+  if (b >= G8) return lg_stirling(y);
+  if (b >= G175 && b < G25) return lg_r2(norm_d2(add_d2_d(y, -2.0)));
+  if (b >= G125 && b < G175) return lg_m(norm_d2(add_d2_d(y, -1.5)));
+  if (b >= G05 && b < G125) {
+    d2 r = b < G075 ? lg_m(norm_d2(add_d2_d(y, -0.5))) : lg_r2(norm_d2(add_d2_d(y, -1.0)));
     return add_d2d2(r, neg(logk_dd(y)));
   }
-  int n = (int)__dsub_rn(8.0, floor(y.x));           // y + n in [8, 9)
+  int n = int_of(__dsub_rn(8.0, floor(y.x)));         // y + n in [8, 9)
   d2 P = y, z = y;
   for (int i = 1; i < n; i++) {
     z = add_d2_d(z, 1.0);
     P = mul_d2d2(P, z);
   }
-  d2 s = lg_stirling(add_d2_d(y, (double)n));
+  d2 s = lg_stirling(add_d2_d(y, dbl_of(n)));
   return add_d2d2(s, neg(logk_dd(P)));
 }
 // sin(pi x) as a DD, |x| < 2^52
 __device__ __forceinline__ d2 sinpi_dd(double x) {
   double r = __dsub_rn(x, __dmul_rn(2.0, rint(__dmul_rn(0.5, x))));
-  double s = r > 0.5 ? __dsub_rn(1.0, r) : (r < -0.5 ? __dsub_rn(-1.0, r) : r);
+  double s = okey(r) > okey(0.5) ? __dsub_rn(1.0, r) : (okey(r) < okey(-0.5) ? __dsub_rn(-1.0, r) : r);
   d2 T = mul_dd(s, s);
   double p = poly_p<11>(T.x, kSpP);
   d2 in = add_d2_d(D2(kSpH[0], kSpH[1]), __dmul_rn(T.x, p));
@@ -102,9 +112,9 @@ __device__ __forceinline__ d2 sinpi_dd(double x) {
 // log-gamma as a DD, sign of gamma (finite x, not a non-positive integer)
 __device__ __forceinline__ d2 lgamma_dd(double x, int &sign) {
   sign = 1;
-  if (x > 0.0) return lgamma_pos(D2(x, 0.0));
+  if (gt_0(x)) return lgamma_pos(D2(x, 0.0));
   d2 sp = sinpi_dd(x);
-  bool negs = sp.x < 0.0;
+  bool negs = lt_0(sp.x);
   sign = negs ? -1 : 1;
   d2 l = logk_dd(D2(fabs(sp.x), negs ? -sp.y : sp.y));
   d2 r = add_d2d2(D2(LOGPI_H, LOGPI_L), neg(l));
@@ -113,17 +123,18 @@ __device__ __forceinline__ d2 lgamma_dd(double x, int &sign) {
 }
 // path class for the sorted tiles
 __device__ __forceinline__ int gamma_cls(double x) {
-  double a = fabs(x);
-  if (!(a <= 0x1p1015) || a == 0.0) return 7;
-  if (x < 0.0) return a >= 7.0 ? 5 : 6;
-  if (x >= 8.0) return 0;
-  if (x >= 1.75 && x < 2.5) return 1;
-  if (x >= 1.25 && x < 1.75) return 2;
-  if (x >= 0.5 && x < 1.25) return 3;
+  const uint64_t a = bits(x) & ABS64;
+  if (a > G1015 || a == 0) return 7;                  // also inf and NaN
+  if (bits(x) >> 63) return a >= G7 ? 5 : 6;
+  if (a >= G8) return 0;
+  if (a >= G175 && a < G25) return 1;
+  if (a >= G125 && a < G175) return 2;
+  if (a >= G05 && a < G125) return 3;
   return 4;
 }
-__device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (all |x| >= 2^52 are)
-  return x < 0.0 && (fabs(x) >= 0x1p52 || x == rint(x));
+__device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (-inf included)
+  const uint64_t a = bits(x) & ABS64;
+  return (bits(x) >> 63) && a - 1 < EXP64 && (a >= G52 || integral_b(a));
 }
 
 struct LgammaU10 {
@@ -132,7 +143,8 @@ struct LgammaU10 {
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     if (is_nan_b(bx)) return from_bits(QNAN64);
-    if ((bx & ABS64) == INF || x == 0.0 || neg_int(x) || x > 0x1p1015) return from_bits(INF);
+    if ((bx & ABS64) == INF || (bx & ABS64) == 0 || neg_int(x) || (!(bx >> 63) && bx > G1015))
+      return from_bits(INF);
     int sign;
     d2 L = lgamma_dd(x, sign);
     double y = __dadd_rn(L.x, L.y);
@@ -146,9 +158,9 @@ struct TgammaU10 {
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     if (is_nan_b(bx) || bx == (INF | SIGN) || neg_int(x)) return from_bits(QNAN64);
-    if (x == 0.0) return from_bits(INF | (bx & SIGN));
-    if (x > 172.0) return from_bits(INF);
-    if (x < -190.0) return sinpi_dd(x).x < 0.0 ? -0.0 : 0.0;
+    if ((bx & ABS64) == 0) return from_bits(INF | (bx & SIGN));
+    if (!(bx >> 63) && bx > G172) return from_bits(INF);
+    if ((bx >> 63) && (bx & ABS64) > G190) return lt_0(sinpi_dd(x).x) ? -0.0 : 0.0;
     int sign;
     d2 L = lgamma_dd(x, sign);
     double y = expk(L);

@@ -30,6 +30,39 @@ __device__ __forceinline__ float canonf(float y) {
   return (fbits(y) & ABS32) > EXP32 ? from_fbits(QNAN32) : y;
 }
 
+// Comparisons of a double with a constant on the integer pipe: on GB300 an
+// FP64 comparison occupies an FP64-pipe slot like an FMA.  okey() increases
+// with the value over all non-NaN doubles (-0 sorts just below +0); with a
+// non-zero constant c each helper returns the IEEE result for every x, NaNs
+// included.
+__device__ __forceinline__ long long okey(double d) {
+  long long b = (long long)bits(d);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ bool not_nan(double d) { return (bits(d) & ABS64) <= EXP64; }
+__device__ __forceinline__ bool lt_c(double x, double c) { return not_nan(x) && okey(x) < okey(c); }
+__device__ __forceinline__ bool le_c(double x, double c) { return not_nan(x) && okey(x) <= okey(c); }
+__device__ __forceinline__ bool gt_c(double x, double c) { return not_nan(x) && okey(x) > okey(c); }
+__device__ __forceinline__ bool ge_c(double x, double c) { return not_nan(x) && okey(x) >= okey(c); }
+// x < 0, x > 0 and x == 0 with IEEE semantics (signed zeros equal, NaN false)
+__device__ __forceinline__ bool lt_0(double x) { return (bits(x) >> 63) && (bits(x) & ABS64) - 1 < EXP64; }
+__device__ __forceinline__ bool gt_0(double x) { return !(bits(x) >> 63) && bits(x) - 1 < EXP64; }
+__device__ __forceinline__ bool eq_0(double x) { return (bits(x) & ABS64) == 0; }
+
+// a finite |x|, given as its bits, is an integer / an odd integer
+__device__ __forceinline__ bool integral_b(uint64_t ab) {
+  int e = (int)(ab >> 52) - 1023;
+  if (e >= 52) return true;
+  if (e < 0) return ab == 0;
+  return (ab & ((1ull << (52 - e)) - 1)) == 0;
+}
+__device__ __forceinline__ bool odd_int_b(uint64_t ab) {
+  int e = (int)(ab >> 52) - 1023;
+  if (e < 0 || e > 52) return false;
+  uint64_t m = (ab & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  return integral_b(ab) && ((m >> (52 - e)) & 1);
+}
+
 // For an integer-valued double k (|k| < 2^63 or a multiple of 4 above),
 // k mod 4 in two's complement, computed on the integer pipe.
 __device__ __forceinline__ int low2_of_int(double k) {
