@@ -421,6 +421,16 @@ sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size
  * several host threads on one device are serialized. */
 sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk);
 
+/* The same for `count` host arrays in one call: the chunks of all items go
+ * through one pipeline in item order, so the copy in of an item's first
+ * chunk overlaps the kernels of the previous item's last ones (a loop of
+ * sleefcu_eval_host calls drains the pipeline at every item).  Every item
+ * is checked before any work starts: EINVAL for a null items with count > 0
+ * or a null pointer with n > 0, EUNSUPPORTED for an unknown (fn, dtype, ulp);
+ * count == 0 returns OK.  Synchronous like sleefcu_eval_host; same staging
+ * buffers. */
+sleefcu_status sleefcu_eval_host_many(const sleefcu_batch_item *items, size_t count, size_t chunk);
+
 /* ---------------- diagnostics (not part of the method) ----------------
  * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
  * each run 8 independent chains of `iters` fused multiply-adds in FP64

@@ -177,6 +177,7 @@ def _batch_lib():
         L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.sleefcu_batch_launch_static.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_void_p]
         L.sleefcu_eval_host.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t]
+        L.sleefcu_eval_host_many.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_size_t]
         L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
         L.sleefcu_batch_destroy.restype = None
         L._batch_ready = True
@@ -216,6 +217,22 @@ def eval_host(name, x, y=None, out=None, out2=None, chunk=0):
     item = BatchItem(FN_IDS[fn], DTYPE_IDS[prec], int(acc[1:]), 0, ptr(x), ptr(y), ptr(out), ptr(out2), n)
     _check(_batch_lib().sleefcu_eval_host(ctypes.byref(item), chunk), "eval_host")
     return out
+
+
+def eval_host_many(items, chunk=0):
+    """sleefcu_eval_host_many on (entry point name, x, y, out, out2) items of
+    host numpy arrays (y / out2 None where unused): one overlapped pipeline
+    over all items; returns when every out holds its results."""
+    import numpy as np
+    arr = (BatchItem * max(len(items), 1))()
+    ptr = lambda a: None if a is None else a.ctypes.data
+    for i, (name, x, y, out, out2) in enumerate(items):
+        if not isinstance(x, np.ndarray):
+            raise SleefcuError("eval_host_many: pass numpy arrays")
+        fn, acc, prec = name.split("_")
+        arr[i] = BatchItem(FN_IDS[fn], DTYPE_IDS[prec], int(acc[1:]), 0, ptr(x), ptr(y), ptr(out), ptr(out2),
+                           x.size)
+    _check(_batch_lib().sleefcu_eval_host_many(arr, len(items), chunk), "eval_host_many")
 
 
 class Batch:

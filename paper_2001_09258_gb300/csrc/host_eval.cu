@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 namespace {
 using namespace sleefcu;
@@ -236,58 +237,92 @@ sleefcu_status prepare(Stage &st, size_t bytes) {
   }
   return SLEEFCU_OK;
 }
-}  // namespace
 
-extern "C" sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk) {
-  if (!item) { set_error("sleefcu_eval_host: null descriptor"); return SLEEFCU_EINVAL; }
-  const Entry *en = find(*item);
-  if (!en) {
-    set_error("sleefcu_eval_host: unsupported (fn %u, dtype %u, ulp %u)", item->fn, item->dtype, item->ulp);
-    return SLEEFCU_EUNSUPPORTED;
+// every item's entry and pointers, before any work
+sleefcu_status check_items(const sleefcu_batch_item *items, size_t count, const Entry **ens) {
+  for (size_t i = 0; i < count; i++) {
+    const sleefcu_batch_item &it = items[i];
+    const Entry *en = find(it);
+    if (!en) {
+      set_error("sleefcu_eval_host: item %zu unsupported (fn %u, dtype %u, ulp %u)", i, it.fn, it.dtype, it.ulp);
+      return SLEEFCU_EUNSUPPORTED;
+    }
+    if (it.n && (!it.x || !it.out || (en->nin == 2 && !it.y) || (en->nout == 2 && !it.out2))) {
+      set_error("sleefcu_eval_host: item %zu: null pointer with n = %zu", i, (size_t)it.n);
+      return SLEEFCU_EINVAL;
+    }
+    ens[i] = en;
   }
-  size_t n = item->n;
-  if (n == 0) return SLEEFCU_OK;
-  if (!item->x || !item->out || (en->nin == 2 && !item->y) || (en->nout == 2 && !item->out2)) {
-    set_error("sleefcu_eval_host: null pointer with n = %zu", n);
-    return SLEEFCU_EINVAL;
-  }
+  return SLEEFCU_OK;
+}
+
+// the chunks of items[0..count) through one three-stream pipeline
+sleefcu_status run_pipeline(const sleefcu_batch_item *items, const Entry *const *ens, size_t count, size_t chunk) {
   if (chunk == 0) chunk = (size_t)1 << 22;
   chunk = (chunk + 7) & ~(size_t)7;            // 16-byte aligned chunk starts for 2-byte elements
+  size_t cbytes = 0;
+  for (size_t i = 0; i < count; i++) {
+    size_t m = items[i].n < chunk ? items[i].n : chunk;
+    if (m * (size_t)ens[i]->esz > cbytes) cbytes = m * (size_t)ens[i]->esz;
+  }
+  if (cbytes == 0) return SLEEFCU_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
   if (dev < 0 || dev >= kMaxDev) { set_error("sleefcu_eval_host: device %d unsupported", dev); return SLEEFCU_EUNSUPPORTED; }
   std::lock_guard<std::mutex> lock(g_mu[dev]);
   Stage &st = g_stage[dev];
-  const size_t esz = (size_t)en->esz, cbytes = (chunk < n ? chunk : n) * esz;
   sleefcu_status rc = prepare(st, cbytes);
   if (rc != SLEEFCU_OK) return rc;
-  const size_t nchunks = (n + chunk - 1) / chunk;
-  for (size_t c = 0; c < nchunks; c++) {
-    const int b = (int)(c % kDepth);
-    const size_t off = c * chunk, m = (n - off < chunk) ? n - off : chunk, bytes = m * esz;
-    if (c >= (size_t)kDepth && (e = cudaStreamWaitEvent(st.in, st.freed[b], 0)) != cudaSuccess)
-      return cuda_fail("wait", e);
-    if ((e = cudaMemcpyAsync(st.buf[b][0], (const char *)item->x + off * esz, bytes, cudaMemcpyHostToDevice,
-                             st.in)) != cudaSuccess)
-      return cuda_fail("copy in", e);
-    if (en->nin == 2 && (e = cudaMemcpyAsync(st.buf[b][1], (const char *)item->y + off * esz, bytes,
-                                             cudaMemcpyHostToDevice, st.in)) != cudaSuccess)
-      return cuda_fail("copy in", e);
-    if ((e = cudaEventRecord(st.loaded[b], st.in)) != cudaSuccess) return cuda_fail("record", e);
-    if ((e = cudaStreamWaitEvent(st.run, st.loaded[b], 0)) != cudaSuccess) return cuda_fail("wait", e);
-    rc = en->f(st.buf[b][0], st.buf[b][1], st.buf[b][2], st.buf[b][3], m, (sleefcu_stream)st.run);
-    if (rc != SLEEFCU_OK) return rc;
-    if ((e = cudaEventRecord(st.done[b], st.run)) != cudaSuccess) return cuda_fail("record", e);
-    if ((e = cudaStreamWaitEvent(st.out, st.done[b], 0)) != cudaSuccess) return cuda_fail("wait", e);
-    if ((e = cudaMemcpyAsync((char *)item->out + off * esz, st.buf[b][2], bytes, cudaMemcpyDeviceToHost,
-                             st.out)) != cudaSuccess)
-      return cuda_fail("copy out", e);
-    if (en->nout == 2 && (e = cudaMemcpyAsync((char *)item->out2 + off * esz, st.buf[b][3], bytes,
-                                              cudaMemcpyDeviceToHost, st.out)) != cudaSuccess)
-      return cuda_fail("copy out", e);
-    if ((e = cudaEventRecord(st.freed[b], st.out)) != cudaSuccess) return cuda_fail("record", e);
+  size_t c = 0;                                // chunks issued so far, over all items
+  for (size_t i = 0; i < count; i++) {
+    const sleefcu_batch_item &it = items[i];
+    const Entry *en = ens[i];
+    const size_t n = it.n, esz = (size_t)en->esz;
+    for (size_t off = 0; off < n; off += chunk, c++) {
+      const int b = (int)(c % kDepth);
+      const size_t m = (n - off < chunk) ? n - off : chunk, bytes = m * esz;
+      if (c >= (size_t)kDepth && (e = cudaStreamWaitEvent(st.in, st.freed[b], 0)) != cudaSuccess)
+        return cuda_fail("wait", e);
+      if ((e = cudaMemcpyAsync(st.buf[b][0], (const char *)it.x + off * esz, bytes, cudaMemcpyHostToDevice,
+                               st.in)) != cudaSuccess)
+        return cuda_fail("copy in", e);
+      if (en->nin == 2 && (e = cudaMemcpyAsync(st.buf[b][1], (const char *)it.y + off * esz, bytes,
+                                               cudaMemcpyHostToDevice, st.in)) != cudaSuccess)
+        return cuda_fail("copy in", e);
+      if ((e = cudaEventRecord(st.loaded[b], st.in)) != cudaSuccess) return cuda_fail("record", e);
+      if ((e = cudaStreamWaitEvent(st.run, st.loaded[b], 0)) != cudaSuccess) return cuda_fail("wait", e);
+      rc = en->f(st.buf[b][0], st.buf[b][1], st.buf[b][2], st.buf[b][3], m, (sleefcu_stream)st.run);
+      if (rc != SLEEFCU_OK) return rc;
+      if ((e = cudaEventRecord(st.done[b], st.run)) != cudaSuccess) return cuda_fail("record", e);
+      if ((e = cudaStreamWaitEvent(st.out, st.done[b], 0)) != cudaSuccess) return cuda_fail("wait", e);
+      if ((e = cudaMemcpyAsync((char *)it.out + off * esz, st.buf[b][2], bytes, cudaMemcpyDeviceToHost,
+                               st.out)) != cudaSuccess)
+        return cuda_fail("copy out", e);
+      if (en->nout == 2 && (e = cudaMemcpyAsync((char *)it.out2 + off * esz, st.buf[b][3], bytes,
+                                                cudaMemcpyDeviceToHost, st.out)) != cudaSuccess)
+        return cuda_fail("copy out", e);
+      if ((e = cudaEventRecord(st.freed[b], st.out)) != cudaSuccess) return cuda_fail("record", e);
+    }
   }
   if ((e = cudaStreamSynchronize(st.out)) != cudaSuccess) return cuda_fail("synchronize", e);
   return SLEEFCU_OK;
+}
+}  // namespace
+
+extern "C" sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk) {
+  if (!item) { set_error("sleefcu_eval_host: null descriptor"); return SLEEFCU_EINVAL; }
+  const Entry *en = nullptr;
+  sleefcu_status rc = check_items(item, 1, &en);
+  if (rc != SLEEFCU_OK) return rc;
+  return run_pipeline(item, &en, 1, chunk);
+}
+
+extern "C" sleefcu_status sleefcu_eval_host_many(const sleefcu_batch_item *items, size_t count, size_t chunk) {
+  if (count == 0) return SLEEFCU_OK;
+  if (!items) { set_error("sleefcu_eval_host_many: null items with count = %zu", count); return SLEEFCU_EINVAL; }
+  std::vector<const Entry *> ens(count);
+  sleefcu_status rc = check_items(items, count, ens.data());
+  if (rc != SLEEFCU_OK) return rc;
+  return run_pipeline(items, ens.data(), count, chunk);
 }

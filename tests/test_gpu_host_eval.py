@@ -47,3 +47,38 @@ def test_eval_host_pinned_and_errors():
     assert np.array_equal(o.numpy().view(np.uint64), oracle.apply("exp_u35_f64", x.numpy()).view(np.uint64))
     with pytest.raises(sleefcu.SleefcuError):
         sleefcu.eval_host("pow_u10_f64", x.numpy(), None, o.numpy())          # missing y
+
+
+def test_eval_host_many_one_pipeline():
+    """sleefcu_eval_host_many over items of every signature and precision,
+    ragged sizes and chunk counts, an empty item: each result equals the
+    oracle's bit for bit."""
+    names = NAMES + ["atan2_u35_f64", "sincos_u10_f32"]
+    sizes = [100003, 1, 0, 70001, 4096, 33, 250000, 5, 8193, 777, 12345]
+    items, wants = [], []
+    for i, name in enumerate(names):
+        n = sizes[i % len(sizes)]
+        x, y = operands(name, n, f"hm/{i}")
+        out = np.empty_like(x)
+        out2 = np.empty_like(x) if sleefcu.FUNCS[name.split("_")[0]] == "sc" else None
+        items.append((name, x, y, out, out2))
+        wants.append(oracle.apply(name, x, y) if n else None)
+    sleefcu.eval_host_many(items, chunk=8192)
+    for (name, x, y, out, out2), want in zip(items, wants):
+        if x.size == 0:
+            continue
+        if out2 is not None:
+            assert out.tobytes() == want[0].tobytes() and out2.tobytes() == want[1].tobytes(), name
+        else:
+            w = want.view(out.dtype) if want.dtype.itemsize == out.dtype.itemsize else want
+            assert out.view(np.uint8).tobytes() == w.view(np.uint8).tobytes(), name
+
+
+def test_eval_host_many_checks_every_item_first():
+    x = I.workload("exp", 1000, key="hm/e")
+    o = np.full_like(x, 7.0)
+    bad = [("exp_u10_f64", x, None, o, None), ("pow_u10_f64", x, None, np.empty_like(x), None)]
+    with pytest.raises(sleefcu.SleefcuError):
+        sleefcu.eval_host_many(bad)
+    assert np.all(o == 7.0)                       # nothing ran
+    sleefcu.eval_host_many([])
