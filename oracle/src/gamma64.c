@@ -66,8 +66,9 @@ static dd_t lg_stirling(dd_t y) {
   dd_t r = ddmul_d2_d2_d2(ddadd2_d2_d2_d(y, -0.5), ly);
   r = ddadd2_d2_d2_d2(r, dd(-y.x, -y.y));
   r = ddadd2_d2_d2_d2(r, dd(LOG2PI_H, LOG2PI_L));
-  double w = 1.0 / (y.x * y.x);
-  return ddadd2_d2_d2_d(r, poly_d(w, LG_ST, 10) / y.x);
+  double ry = 1.0 / y.x;                      /* one reciprocal gives w = 1/y^2 and G(w)/y */
+  double w = ry * ry;
+  return ddadd2_d2_d2_d(r, poly_d(w, LG_ST, 10) * ry);
 }
 
 /* lgamma of a DD y > 0 (finite, y.x < 2^1014) */

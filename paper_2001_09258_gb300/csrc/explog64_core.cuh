@@ -72,6 +72,23 @@ __device__ __forceinline__ double pow2_any(int k) {
   return k >= -1022 ? pow2i(k) : from_bits(1ull << (k + 1074));
 }
 
+// a DD with a normal positive head, scaled by 2^-ex (ex its head's
+// exponent): the head's significand in [1, 2) is taken from the bits, the
+// tail (possibly zero or subnormal) is multiplied; then halved if the head
+// is >= 1.5 (ex incremented).  Same values as scaling both parts by
+// multiplications, one or two FP64 operations fewer.
+__device__ __forceinline__ d2 log_mantissa(d2 a, int &ex) {
+  ex = (int)(bits(a.x) >> 52) - 1023;
+  uint64_t hb = (bits(a.x) & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  double t = __dmul_rn(a.y, pow2_any(-ex));
+  if (hb >= 0x3FF8000000000000ull) {
+    hb -= 0x0010000000000000ull;
+    t = __dmul_rn(t, 0.5);
+    ex++;
+  }
+  return D2(from_bits(hb), t);
+}
+
 // 2^k (1 + r + rl) with the 1-ULP polynomial, |r| <= ln2/2: the residual rl
 // joins the polynomial part and 1 + r is a DD, so the last addition is the
 // only rounding of order one ulp (Section 5.6)
@@ -115,9 +132,8 @@ __device__ __forceinline__ double expk(d2 Y) {
 __device__ __forceinline__ d2 logm_u10(d2 a, int &e) {
   int off = 0;
   if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
-  int ex = (int)(bits(a.x) >> 52) - 1023;
-  d2 m = scale_d2(a, pow2_any(-ex));
-  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
+  int ex;
+  d2 m = log_mantissa(a, ex);
   d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
   d2 den = add_d_d2(1.0, m);
   d2 z = div_d2d2(num, den);
@@ -131,9 +147,8 @@ __device__ __forceinline__ d2 logm_u10(d2 a, int &e) {
 __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   int off = 0;
   if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
-  int ex = (int)(bits(a.x) >> 52) - 1023;
-  d2 m = scale_d2(a, pow2_any(-ex));
-  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
+  int ex;
+  d2 m = log_mantissa(a, ex);
   double num = __dmul_rn(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
   double z = __ddiv_rn(num, __dadd_rn(1.0, m.x));
   double t = __dmul_rn(z, z);
@@ -147,9 +162,8 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
 __device__ __forceinline__ d2 logk_dd(d2 y) {
   int off = 0;
   if (lt_c(y.x, 0x1p-1022)) { y = scale_d2(y, 0x1p64); off = 64; }
-  int ex = (int)(bits(y.x) >> 52) - 1023;
-  d2 m = scale_d2(y, pow2_any(-ex));
-  if (ge_c(m.x, 1.5)) { m = scale_d2(m, 0.5); ex++; }
+  int ex;
+  d2 m = log_mantissa(y, ex);
   d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
   d2 z = div_d2d2(num, add_d_d2(1.0, m));
   d2 t = sqr_d2(z);

@@ -77,8 +77,9 @@ __device__ __forceinline__ d2 lg_stirling(d2 y) {
   d2 r = mul_d2d2(add_d2_d(y, -0.5), ly);
   r = add_d2d2(r, neg(y));
   r = add_d2d2(r, D2(LOG2PI_H, LOG2PI_L));
-  double w = __ddiv_rn(1.0, __dmul_rn(y.x, y.x));
-  return add_d2_d(r, __ddiv_rn(poly(w, kLgSt), y.x));
+  double ry = __ddiv_rn(1.0, y.x);            // one reciprocal: w = 1/y^2 and G(w)/y
+  double w = __dmul_rn(ry, ry);
+  return add_d2_d(r, __dmul_rn(poly(w, kLgSt), ry));
 }
 // lgamma of a DD y > 0
 __device__ __forceinline__ d2 lgamma_pos(d2 y) {
