@@ -519,7 +519,7 @@ def main():
         e2e = {"value": round(total_el / (e_ms * 1e-3) / 1e9, 4), "unit": "Gelem/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "sleefcu_eval_host_many (one call per step over the 60 pinned host arrays, "
-                      "3 chunks of 2^22 in flight)",
+                      "up to 6 chunks of 2^22 in flight)",
                "timer": "host clock around whole steps"}
 
     if rank != 0:

@@ -409,13 +409,13 @@ sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size
  * The end-to-end form of every entry point: item describes one array exactly
  * as for the batched launch, but x, y, out, out2 are HOST pointers.  The
  * library streams the arrays through device buffers it owns in chunks of
- * `chunk` elements (0: 4,194,304), keeping three chunks in flight: copy in
- * of chunk i+1, the entry point's kernel on chunk i and copy out of chunk
- * i-1 run concurrently on three library streams.  Results equal the device
+ * `chunk` elements (0: 4,194,304), keeping up to six chunks in flight:
+ * copies in, the entry point's kernels and copies out run concurrently on
+ * three library streams.  Results equal the device
  * entry point's bit for bit.  The call is synchronous: it returns when out
  * (and out2) hold every result.  Host arrays should be page-locked
  * (cudaHostAlloc / cudaHostRegister) for the copies to overlap; pageable
- * memory works at lower speed.  The staging buffers (3 x 4 x chunk x element
+ * memory works at lower speed.  The staging buffers (6 x 4 x chunk x element
  * size bytes of device memory) and streams are created on the first call
  * per device and kept; ENOMEM if they cannot be allocated.  Calls from
  * several host threads on one device are serialized. */

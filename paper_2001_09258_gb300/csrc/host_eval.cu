@@ -1,8 +1,8 @@
 // Evaluation from and to host memory: the end-to-end form of every entry
 // point.  A caller whose arrays live in host memory hands the library one
 // descriptor; the library streams it through device buffers it owns, in
-// chunks, with the copy in of chunk i+1, the kernel on chunk i and the copy
-// out of chunk i-1 in flight at once on three streams (the per-element work
+// chunks, with copies in, kernels and copies out of up to six chunks in
+// flight at once on three streams (the per-element work
 // is the same entry point, so every result equals the device call's bit for
 // bit).  Staging buffers and streams are created on the first call per
 // device and reused; the call returns when every result is in host memory.
@@ -190,7 +190,11 @@ const Entry *find(const sleefcu_batch_item &it) {
   return nullptr;
 }
 
-constexpr int kDepth = 3;                      // chunks in flight
+// chunks in flight: deep enough that the copy engines run ahead through
+// items whose kernels are slow and the kernels through items whose copies
+// are slow (a fast FP64 function moves its 16 bytes per element faster than
+// the host link carries them, a slow one leaves the link idle)
+constexpr int kDepth = 6;
 constexpr int kMaxDev = 64;
 struct Stage {
   bool ready = false;

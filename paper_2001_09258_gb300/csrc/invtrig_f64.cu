@@ -64,6 +64,11 @@ __device__ __forceinline__ d2 asin_core_u10(double ax, bool big) {
   double corr = __dmul_rn(__dmul_rn(u.x, t), poly(t, kAsinU10));
   return add_d2_d_fast(u, corr);
 }
+// a square root the compiler cannot hoist out of its branch: inlined, the
+// 3.5-ULP asin/acos had both arms if-converted, so every lane paid for the
+// square root (ncu: 33 FP64 instructions per element on either path)
+static __device__ __noinline__ double sqrt_branch(double t) { return __dsqrt_rn(t); }
+
 __device__ __forceinline__ double asin_core_u35(double ax, bool big) {
   double u, t;
   if (!big) {
@@ -71,7 +76,7 @@ __device__ __forceinline__ double asin_core_u35(double ax, bool big) {
     t = __dmul_rn(ax, ax);
   } else {
     t = __dmul_rn(__dsub_rn(1.0, ax), 0.5);
-    u = __dsqrt_rn(t);
+    u = sqrt_branch(t);
   }
   return __fma_rn(__dmul_rn(u, t), poly(t, kAsinU10), u);
 }
