@@ -23,9 +23,10 @@
  *                  [8, 9), the product in DD
  * y < 0 (not an integer): reflection, lgamma(y) = log pi - log|sin(pi y)| -
  * lgamma(1 - y), sin(pi y) from y reduced exactly to [-1/2, 1/2] and an odd
- * polynomial with DD leading terms.  tgamma(y) = sign * exp(L) with L the DD
- * log-gamma (so only its absolute error matters) and the sign of sin(pi y)
- * for y < 0.  Near the zeros of lgamma on the negative axis the reflection
+ * polynomial with DD leading terms.  tgamma(y) = exp(L) with L the DD
+ * log-gamma for y > 0 (so only its absolute error matters); for y < 0 the
+ * reflection in linear form, pi / (sin(pi y) e^g) with g = lgamma(1 - y)
+ * (one DD logarithm fewer than through L).  Near the zeros of lgamma on the negative axis the reflection
  * cancels, as in every libm: the relative error there is reported
  * separately (absolute error bound).  Both u35 entry points run the u10
  * algorithm. */
@@ -131,7 +132,6 @@ double oracle_lgamma_u10_f64(double x) {
 
 double oracle_tgamma_u10_f64(double x) {
   double a = fabs(x);
-  int sign;
   if (isnan(x) || x == -INFINITY || (x < 0 && (a >= 0x1p52 || x == rint(x)))) return canon_nan();
   if (x == 0) return copysign(INFINITY, x);
   if (x > 172) return INFINITY;
@@ -140,9 +140,23 @@ double oracle_tgamma_u10_f64(double x) {
     dd_t sp = sinpi_dd(x);
     return sp.x < 0 ? -0.0 : 0.0;
   }
-  dd_t L = lgamma_dd(x, &sign);
-  double y = oracle_exp_dd(L);
-  return canon(sign < 0 ? -y : y);
+  if (x > 0) return canon(oracle_exp_dd(lgamma_pos(dd(x, 0.0))));
+  /* x < 0: the reflection in linear form, gamma(x) = pi / (sin(pi x) gamma(1-x))
+   * with gamma(1-x) = e^g, g = lgamma(1-x) > -0.13: e^-g = 2^k (1 + s) from the
+   * DD exp core, pi (1 + s) / |sin(pi x)| in DD, then 2^k applied once */
+  /* |x| < 2^-900: sin(pi x) is pi x to far below an ulp; it is formed from
+   * x 2^200 (exact) so that it keeps full precision where pi x would be
+   * subnormal, and the quotient gets 2^-200 back with 2^k */
+  int up = fabs(x) < 0x1p-900 ? 200 : 0;
+  dd_t sp = up ? ddmul_d2_d2_d(dd(PI_H, PI_L), ldexp(x, 200)) : sinpi_dd(x);
+  int neg = sp.x < 0;
+  dd_t d = dd(fabs(sp.x), neg ? -sp.y : sp.y);
+  dd_t g = lgamma_pos(ddadd2_d2_d_d(1.0, -x));
+  double k;
+  dd_t e = ddadd_d2_d_d2(1.0, oracle_expk_s(dd(-g.x, -g.y), &k));
+  dd_t q = dddiv_d2_d2_d2(ddmul_d2_d2_d2(dd(PI_H, PI_L), e), d);
+  double y = oracle_scale2(q.x + q.y, (int)k + up);   /* +inf when it overflows */
+  return canon(neg ? -y : y);
 }
 
 double oracle_lgamma_u35_f64(double x) { return oracle_lgamma_u10_f64(x); }

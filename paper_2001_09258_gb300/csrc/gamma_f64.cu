@@ -153,6 +153,18 @@ struct LgammaU10 {
     return canon(y);
   }
 };
+// y 2^k for a positive normal y: the exponent field when the result is
+// normal, +inf above, two multiplications by normal powers of two (one
+// rounding) below
+__device__ __forceinline__ double scale2_any(double y, int k) {
+  const int e = (int)(bits(y) >> 52) - 1023 + k;
+  if (e > 1023) return from_bits(INF);
+  if (e >= -1022) return from_bits(bits(y) + ((uint64_t)(int64_t)k << 52));
+  const int k1 = k / 2, k2 = k - k1;
+  return __dmul_rn(__dmul_rn(y, pow2i(k1)), pow2i(k2));
+}
+constexpr uint64_t G2M900 = 0x07B0000000000000ull;   // 2^-900
+
 struct TgammaU10 {
   static constexpr int NCLS = 8;
   __device__ static int cls(double x) { return gamma_cls(x); }
@@ -162,10 +174,21 @@ struct TgammaU10 {
     if ((bx & ABS64) == 0) return from_bits(INF | (bx & SIGN));
     if (!(bx >> 63) && bx > G172) return from_bits(INF);
     if ((bx >> 63) && (bx & ABS64) > G190) return lt_0(sinpi_dd(x).x) ? -0.0 : 0.0;
-    int sign;
-    d2 L = lgamma_dd(x, sign);
-    double y = expk(L);
-    return canon(sign < 0 ? -y : y);
+    if (gt_0(x)) return canon(expk(lgamma_pos(D2(x, 0.0))));
+    // x < 0: the reflection in linear form, gamma(x) = pi / (sin(pi x) e^g)
+    // with g = lgamma(1 - x), e^-g = 2^k (1 + s) from the DD exp core; for
+    // |x| < 2^-900 sin(pi x) = pi x is formed from x 2^200 (full precision
+    // where pi x would be subnormal) and 2^-200 rejoins 2^k
+    const int up = (bx & ABS64) < G2M900 ? 200 : 0;
+    d2 sp = up ? mul_d2_d(D2(PI_H, PI_L), __dmul_rn(x, 0x1p200)) : sinpi_dd(x);
+    const bool negs = lt_0(sp.x);
+    d2 d = D2(fabs(sp.x), negs ? -sp.y : sp.y);
+    d2 g = lgamma_pos(add_dd(1.0, -x));
+    double k;
+    d2 e = add_d_d2_fast(1.0, expk_s(D2(-g.x, -g.y), k));
+    d2 q = div_d2d2(mul_d2d2(D2(PI_H, PI_L), e), d);
+    double y = scale2_any(__dadd_rn(q.x, q.y), int_of(k) + up);
+    return canon(negs ? -y : y);
   }
 };
 

@@ -170,7 +170,8 @@ def test_erf_identities():
 GAMMA_SETS = {
     "tgamma": lambda: [U("t1", N, -170, 171.6), U("t2", N, 0, 3), L("t3", N, 1e-300, 1e-3), U("t4", N, -5, 0),
                        U("t5", N, 160, 171.62), U("t6", N, -190, -170), L("t7", N, 5e-324, 1e-300, signed=False),
-                       U("t8", N, 0.99, 2.01)],
+                       U("t8", N, 0.99, 2.01), -L("t9", N, 5e-324, 1e-290, signed=False),
+                       U("t10", N, -1.0001, -0.9999)],
     "lgamma": lambda: [U("l1", N, 0, 1000), U("l2", N, 0, 3), L("l3", N, 1e-300, 2.5e305, signed=False),
                        U("l4", N, 0.99, 1.01), U("l5", N, 1.99, 2.01), U("l6", N, 1.2, 1.8), U("l7", N, 2.4, 8.5),
                        U("l9", N, 0.5, 0.8), L("l10", N, 5e-324, 1e-300, signed=False)],
