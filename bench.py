@@ -378,11 +378,12 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
             "speedup_vs_single_launch_graph": round(ms_single_graph / ms_graph, 2)}
 
 
-def cpu_baseline(names, n_sample, rank):
-    """The oracle as it stands, on the host cores, on a bounded sample."""
+def cpu_baseline(names, n_sample, rank, threads=None):
+    """The oracle as it stands, on the host cores (all of them unless
+    `threads` is given), on a bounded sample."""
     import oracle
     from paper_2001_09258_gb300 import inputs as I
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     total_el, total_s = 0, 0.0
     for name in names:
         fn = name.split("_")[0]
@@ -583,9 +584,12 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         el, s, thr = cpu_baseline(names, args.cpu_sample, rank)
+        el1, s1, _ = cpu_baseline(names, max(1024, args.cpu_sample // 16), rank, threads=1)
         cpu = {"value": round(el / s / 1e9, 6), "unit": "Gelem/s", "cores": thr, "kind": "oracle",
                "sample": f"{args.cpu_sample} elements of each entry point's workload array "
-                         f"({len(names)} entry points)"}
+                         f"({len(names)} entry points)",
+               "single_core_value": round(el1 / s1 / 1e9, 6),
+               "single_core_sample": f"{max(1024, args.cpu_sample // 16)} elements per entry point, one thread"}
     line = {
         "metric": "Gelem/s (full FP64 C99 set, u10+u35) at max-ULP <=1.0/3.5",
         "value": round(value, 4), "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps,
