@@ -113,7 +113,7 @@ static inline dd_t ddrec_d2_d2(dd_t d) {
 static inline dd_t ddsqrt_d2_d2(dd_t d) {
   double h = sqrt(d.x);
   double r = fma(-h, h, d.x) + d.y;
-  return dd(h, r / (h + h));
+  return dd(h, r * (1.0 / (h + h)));
 }
 
 /* ---- float-float (FP32 analogues) ---- */

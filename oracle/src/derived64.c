@@ -320,7 +320,7 @@ double oracle_sinh_u35_f64(double x) {
   } else {
     double p = ldexp(1.0, (int)k);
     double em = fma(p, v, p - 1.0);
-    y = 0.5 * (em + em / (em + 1.0));
+    y = 0.5 * (em + em * (1.0 / (em + 1.0)));
   }
   if (a < TWO_M28) y = a;
   if (!(a <= 711)) y = isnan(x) ? NAN : INFINITY;
@@ -350,7 +350,7 @@ double oracle_tanh_u35_f64(double x) {
   double v = em1_u35(ac + ac, &k);
   double p = ldexp(1.0, (int)k);
   double em = fma(p, v, p - 1.0);
-  double y = em / (em + 2.0);
+  double y = em * (1.0 / (em + 2.0));
   if (a < TWO_M28) y = a;
   if (!(a <= 20)) y = isnan(x) ? NAN : 1.0;
   return canon(copysign(y, x));

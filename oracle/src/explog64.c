@@ -117,7 +117,7 @@ double oracle_log_u35_f64(double x) {
   double a = (x > 0 && x <= 0x1.fffffffffffffp1023) ? x : 1.0;
   int e;
   double m = log_reduce(a, &e);
-  double z = (2.0 * (m - 1.0)) / (1.0 + m);
+  double z = (2.0 * (m - 1.0)) * (1.0 / (1.0 + m));
   double t = z * z;
   double lm = fma(z * t, poly_d(t, LOG_U35, 7), z);
   double y = fma((double)e, L2A, lm);
@@ -152,7 +152,7 @@ double oracle_logm_u35(dd_t a, int *ep) {
   dd_t m = ddscale_d2_d2_d(a, ldexp(1.0, -ex));
   if (m.x >= 1.5) { m = ddscale_d2_d2_d(m, 0.5); ex++; }
   double num = 2.0 * ((m.x - 1.0) + m.y);
-  double z = num / (1.0 + m.x);
+  double z = num * (1.0 / (1.0 + m.x));
   double t = z * z;
   *ep = ex - off;
   return fma(z * t, poly_d(t, LOG_U35, 7), z);

@@ -32,7 +32,7 @@ static const double ATAN_U35[19] = { ATAN_U35_COEFFS };
 static dd_t sqrt_dd(double t) {
   double h = sqrt(t);
   double r = fma(-h, h, t);
-  double lo = r / (h + h);
+  double lo = r * (1.0 / (h + h));
   return dd(h, h > 0 ? lo : 0.0);
 }
 
@@ -160,7 +160,7 @@ double oracle_atan2_u35_f64(double a, double b) {
   if (!(den > 0 && den <= 0x1.fffffffffffffp1023) || !(num <= den)) { num = 0.0; den = 1.0; }
   if (den < 0x1p-1000) { num *= 0x1p600; den *= 0x1p600; }      /* keep 1/den finite */
   if (den > 0x1p1000) { num *= 0x1p-600; den *= 0x1p-600; }     /* keep 1/den normal */
-  double r = atan_core_u35(num / den);
+  double r = atan_core_u35(num * (1.0 / den));
   if (swap) r = PIO2H - r;
   if (b < 0) r = PIH - r;
   double y = copysign(r, a);

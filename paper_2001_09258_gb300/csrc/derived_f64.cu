@@ -351,7 +351,7 @@ struct SinhU35 {
     } else {
       double p = pow2i(int_of(k));
       double em = __fma_rn(p, v, __dsub_rn(p, 1.0));
-      y = __dmul_rn(0.5, __dadd_rn(em, __ddiv_rn(em, __dadd_rn(em, 1.0))));
+      y = __dmul_rn(0.5, __dadd_rn(em, __dmul_rn(em, __ddiv_rn(1.0, __dadd_rn(em, 1.0)))));
     }
     if (ab < BM28) y = from_bits(ab);
     if (ab > B711) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
@@ -385,7 +385,7 @@ struct TanhU35 {
     double v = em1_u35(__dadd_rn(ac, ac), k);
     double p = pow2i(int_of(k));
     double em = __fma_rn(p, v, __dsub_rn(p, 1.0));
-    double y = __ddiv_rn(em, __dadd_rn(em, 2.0));
+    double y = __dmul_rn(em, __ddiv_rn(1.0, __dadd_rn(em, 2.0)));
     if (ab < BM28) y = from_bits(ab);
     if (ab > B20) y = is_nan_b(bx) ? from_bits(QNAN64) : 1.0;
     return canon(copysign_b(y, bx));

@@ -150,7 +150,7 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   int ex;
   d2 m = log_mantissa(a, ex);
   double num = __dmul_rn(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
-  double z = __ddiv_rn(num, __dadd_rn(1.0, m.x));
+  double z = __dmul_rn(num, __ddiv_rn(1.0, __dadd_rn(1.0, m.x)));
   double t = __dmul_rn(z, z);
   e = ex - off;
   return __fma_rn(__dmul_rn(z, t), poly(t, kLogU35), z);

@@ -87,7 +87,7 @@ struct LogU35 {
     uint64_t a = (b - 1) < DMAX ? b : 0x3FF0000000000000ull;
     int e;
     double m = log_reduce(a, e);
-    double z = __ddiv_rn(__dmul_rn(2.0, __dsub_rn(m, 1.0)), __dadd_rn(1.0, m));
+    double z = __dmul_rn(__dmul_rn(2.0, __dsub_rn(m, 1.0)), __ddiv_rn(1.0, __dadd_rn(1.0, m)));
     double t = __dmul_rn(z, z);
     double lm = __fma_rn(__dmul_rn(z, t), poly(t, kLogU35), z);
     return canon(log_special(b, __fma_rn(dbl_of(e), L2A, lm)));

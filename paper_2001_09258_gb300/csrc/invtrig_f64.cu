@@ -47,7 +47,7 @@ __device__ __forceinline__ double copysign_b(double v, uint64_t sgn_src) {
 __device__ __forceinline__ d2 sqrt_dd(double t) {
   double h = __dsqrt_rn(t);
   double r = __fma_rn(-h, h, t);
-  double lo = __ddiv_rn(r, __dadd_rn(h, h));
+  double lo = __dmul_rn(r, __ddiv_rn(1.0, __dadd_rn(h, h)));
   return D2(h, (bits(h) & ABS64) != 0 ? lo : 0.0);
 }
 
@@ -233,7 +233,7 @@ struct Atan2U35 {
     double fn = from_bits(num), fd = from_bits(den);
     if (den < 0x0170000000000000ull) { fn = __dmul_rn(fn, 0x1p600); fd = __dmul_rn(fd, 0x1p600); }
     if (den > 0x7E70000000000000ull) { fn = __dmul_rn(fn, 0x1p-600); fd = __dmul_rn(fd, 0x1p-600); }
-    double r = atan_core_u35(__ddiv_rn(fn, fd));
+    double r = atan_core_u35(__dmul_rn(fn, __ddiv_rn(1.0, fd)));
     if (swap) r = __dsub_rn(PIO2H, r);
     bool bneg = (bb >> 63) && ab != 0 && ab <= INF;
     if (bneg) r = __dsub_rn(PIH, r);

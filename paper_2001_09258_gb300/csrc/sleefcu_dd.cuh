@@ -107,7 +107,7 @@ __device__ __forceinline__ d2 rec_d2(d2 d) {
 __device__ __forceinline__ d2 sqrt_d2(d2 a) {
   double h = __dsqrt_rn(a.x);
   double r = __dadd_rn(__fma_rn(-h, h, a.x), a.y);
-  return D2(h, __ddiv_rn(r, __dadd_rn(h, h)));
+  return D2(h, __dmul_rn(r, __ddiv_rn(1.0, __dadd_rn(h, h))));
 }
 
 // ---- FF (binary32) ----

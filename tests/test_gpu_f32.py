@@ -52,16 +52,26 @@ def test_c3_full_size_2p28(name):
 
 
 DEFERRED = ["sin_u10_f32", "sin_u35_f32", "cos_u10_f32", "cos_u35_f32", "tan_u10_f32", "tan_u35_f32",
-            "sincos_u10_f32", "sincos_u35_f32"]
+            "sincos_u10_f32", "sincos_u35_f32", "sinh_u10_f32", "cosh_u35_f32", "asinh_u10_f32", "acosh_u10_f32"]
+# (arguments of the main path, arguments of the deferred path) per function
+DEFER_SETS = {
+    "trig": (lambda n: I.uniform("dq/cw", n, -100, 100), lambda n: I.loguniform("dq/ph", n, 1.1e6, 3.4e38)),
+    "hyp": (lambda n: I.uniform("dq/hb", n, 12.5, 89.0) * np.where(I.raw("dq/hs", n) & np.uint64(1), 1, -1),
+            lambda n: I.uniform("dq/hs2", n, -12.0, 12.0)),
+    "ainv": (lambda n: I.loguniform("dq/ab", n, 2.4e18, 3.3e38, signed=False),
+             lambda n: I.loguniform("dq/as", n, 1.0, 1e18, signed=False)),
+}
 
 
-def _deferral_cases():
-    """Arrays for the deferred Payne-Hanek queue of the binary32 trig kernels:
-    no deferred lane, every lane deferred, a scattered tenth, whole 2048-element
-    chunks of each kind back to back, and deferred lanes on chunk edges; sizes
-    around the chunk and the 16-byte vector."""
-    cw = I.uniform("dq/cw", 20000, -100, 100).astype(F)
-    ph = I.loguniform("dq/ph", 20000, 1.1e6, 3.4e38).astype(F)
+def _deferral_cases(fn):
+    """Arrays for the deferred queue of the binary32 kernels: no deferred
+    lane, every lane deferred, a scattered tenth, whole 2048-element chunks of
+    each kind back to back, and deferred lanes on chunk edges; sizes around
+    the chunk and the 16-byte vector."""
+    kind = "trig" if fn in ("sin", "cos", "tan", "sincos") else ("hyp" if fn in ("sinh", "cosh") else "ainv")
+    main, rare = DEFER_SETS[kind]
+    cw = main(20000).astype(F)
+    ph = rare(20000).astype(F)
     pick = (I.raw("dq/pick", 20000) % np.uint64(10)) == 0
     mix = np.where(pick, ph, cw)
     blocks = np.concatenate([cw[:2048], ph[:2048], cw[2048:4096], ph[2048:4096], cw[4096:4100]])
@@ -75,8 +85,8 @@ def _deferral_cases():
 
 @pytest.mark.parametrize("name", DEFERRED)
 @pytest.mark.parametrize("case", ["none", "all", "tenth", "blocks", "edges", "specials", "n1", "n5", "n2049"])
-def test_deferred_payne_hanek_queue(name, case):
-    x = _deferral_cases()[case]
+def test_deferred_queue(name, case):
+    x = _deferral_cases(name.split("_")[0])[case]
     got, want = gpu_call(name, x), oracle.apply(name, x)
     if isinstance(want, tuple):
         assert_bitexact(got[0], want[0], x, name + "/sin")
