@@ -309,10 +309,6 @@ __device__ __forceinline__ float exph_big(float a) {    // e^a / 2 for 12 < a <=
 struct SinhU10 {
   static constexpr int NCLS = 2;
   __device__ static int cls(float x) { return fabsf(x) > 12.0f; }
-  // the DD-style path of |x| <= 12 (and non-finite lanes) is deferred by the plain kernel
-  static constexpr bool DEFER = true;
-  static constexpr float kStandIn = 20.0f;
-  __device__ static bool defer(float x) { return !((fbits(x) & ABS32) > 0x41400000u && (fbits(x) & ABS32) <= 0x42B30000u); }
   __device__ float operator()(float x) const {
     uint32_t bx = fbits(x);
     float a = fabsf(x);
@@ -334,10 +330,6 @@ struct SinhU10 {
 struct CoshU10 {
   static constexpr int NCLS = 2;
   __device__ static int cls(float x) { return fabsf(x) > 12.0f; }
-  // as for sinh: |x| <= 12 and non-finite lanes are deferred
-  static constexpr bool DEFER = true;
-  static constexpr float kStandIn = 20.0f;
-  __device__ static bool defer(float x) { return !((fbits(x) & ABS32) > 0x41400000u && (fbits(x) & ABS32) <= 0x42B30000u); }
   __device__ float operator()(float x) const {
     float a = fabsf(x);
     float ac = a <= 89.5f ? a : 0.0f;

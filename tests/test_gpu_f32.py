@@ -52,12 +52,10 @@ def test_c3_full_size_2p28(name):
 
 
 DEFERRED = ["sin_u10_f32", "sin_u35_f32", "cos_u10_f32", "cos_u35_f32", "tan_u10_f32", "tan_u35_f32",
-            "sincos_u10_f32", "sincos_u35_f32", "sinh_u10_f32", "cosh_u35_f32", "asinh_u10_f32", "acosh_u10_f32"]
+            "sincos_u10_f32", "sincos_u35_f32", "asinh_u10_f32", "asinh_u35_f32", "acosh_u10_f32"]
 # (arguments of the main path, arguments of the deferred path) per function
 DEFER_SETS = {
     "trig": (lambda n: I.uniform("dq/cw", n, -100, 100), lambda n: I.loguniform("dq/ph", n, 1.1e6, 3.4e38)),
-    "hyp": (lambda n: I.uniform("dq/hb", n, 12.5, 89.0) * np.where(I.raw("dq/hs", n) & np.uint64(1), 1, -1),
-            lambda n: I.uniform("dq/hs2", n, -12.0, 12.0)),
     "ainv": (lambda n: I.loguniform("dq/ab", n, 2.4e18, 3.3e38, signed=False),
              lambda n: I.loguniform("dq/as", n, 1.0, 1e18, signed=False)),
 }
@@ -68,7 +66,7 @@ def _deferral_cases(fn):
     lane, every lane deferred, a scattered tenth, whole 2048-element chunks of
     each kind back to back, and deferred lanes on chunk edges; sizes around
     the chunk and the 16-byte vector."""
-    kind = "trig" if fn in ("sin", "cos", "tan", "sincos") else ("hyp" if fn in ("sinh", "cosh") else "ainv")
+    kind = "trig" if fn in ("sin", "cos", "tan", "sincos") else "ainv"
     main, rare = DEFER_SETS[kind]
     cw = main(20000).astype(F)
     ph = rare(20000).astype(F)
