@@ -544,6 +544,7 @@ __device__ __forceinline__ double scale2_two(double y, int k) {
 
 struct ErfU10 {
   static constexpr int NCLS = 5;
+  static constexpr int SORT_EPT = 8;    // 2048-element tiles
   __device__ static int cls(double x) {
     uint64_t a = bits(x) & ABS64;
     return a < BE1 ? 0 : (a < BE2 ? 1 : (a < BE4 ? 2 : (a < BE6 ? 3 : 4)));
@@ -570,6 +571,7 @@ struct ErfU10 {
 };
 struct ErfcU10 {
   static constexpr int NCLS = 6;
+  static constexpr int SORT_EPT = 8;    // 2048-element tiles
   __device__ static int cls(double x) {
     uint64_t a = bits(x) & ABS64;
     return a < BE1 ? 0 : (a < BE2 ? 1 : (a < BE4 ? 2 : (a < BE8 ? 3 : (a <= BE275 ? 4 : 5))));
@@ -604,6 +606,7 @@ struct ErfcU10 {
 };
 struct ErfU35 {
   static constexpr int NCLS = 5;
+  static constexpr int SORT_EPT = 8;    // 2048-element tiles
   __device__ static int cls(double x) { return ErfU10::cls(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);

@@ -140,6 +140,7 @@ __device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (-
 
 struct LgammaU10 {
   static constexpr int NCLS = 8;
+  static constexpr int SORT_EPT = 16;   // 4096-element tiles: eight classes, several of them small
   __device__ static int cls(double x) { return gamma_cls(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
@@ -167,6 +168,7 @@ constexpr uint64_t G2M900 = 0x07B0000000000000ull;   // 2^-900
 
 struct TgammaU10 {
   static constexpr int NCLS = 8;
+  static constexpr int SORT_EPT = 16;   // 4096-element tiles: eight classes, several of them small
   __device__ static int cls(double x) { return gamma_cls(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);

@@ -218,12 +218,19 @@ __global__ void __launch_bounds__(kBlock) k_dual64(const double *x, double *o1, 
 constexpr int kSortEPT = 4;
 constexpr int kSortTile = kBlock * kSortEPT;
 
-template <int NC>
-__device__ __forceinline__ void sort_scatter(const int (&cl)[kSortEPT], int *cnt, int *cur,
-                                             unsigned short *sidx, int tid) {
+// elements per thread of a functor's sorted tiles: F::SORT_EPT where the
+// functor sets it (many classes, some small: a larger tile leaves fewer warps
+// straddling two classes), else kSortEPT
+template <class F, class = void>
+struct sort_ept { static constexpr int value = kSortEPT; };
+template <class F>
+struct sort_ept<F, std::void_t<decltype(F::SORT_EPT)>> { static constexpr int value = F::SORT_EPT; };
+
+template <int NC, int EPT>
+__device__ __forceinline__ void sort_scatter(const int (&cl)[EPT], int *cur, unsigned short *sidx, int tid) {
   const unsigned lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
-  for (int j = 0; j < kSortEPT; j++) {
+  for (int j = 0; j < EPT; j++) {
     if constexpr (NC > 4) {
       // many classes: the lanes of one class find each other with a match
       // instead of one ballot per class
@@ -246,13 +253,12 @@ __device__ __forceinline__ void sort_scatter(const int (&cl)[kSortEPT], int *cnt
       }
     }
   }
-  (void)cnt;
 }
 
-template <int NC>
-__device__ __forceinline__ void sort_count(const int (&cl)[kSortEPT], int *cnt, int tid) {
+template <int NC, int EPT>
+__device__ __forceinline__ void sort_count(const int (&cl)[EPT], int *cnt, int tid) {
   const unsigned lane = tid & 31;
-  for (int j = 0; j < kSortEPT; j++) {
+  for (int j = 0; j < EPT; j++) {
     if constexpr (NC > 4) {
       unsigned m = __match_any_sync(0xffffffffu, cl[j]);
       if ((int)lane == __ffs(m) - 1 && cl[j] >= 0) atomicAdd(&cnt[cl[j]], __popc(m));
@@ -266,63 +272,63 @@ __device__ __forceinline__ void sort_count(const int (&cl)[kSortEPT], int *cnt, 
   }
 }
 
-// unary (NOUT = 1) or one-input-two-output (NOUT = 2) sorted kernel
+// unary (NOUT = 1) or one-input-two-output (NOUT = 2) sorted kernel; each
+// result overwrites its staged argument (a sorted position belongs to one
+// thread), the second output of NOUT = 2 has its own buffer
 template <class F, int NOUT>
 __global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1, double *o2, size_t n) {
-  constexpr int NC = F::NCLS;
-  __shared__ double sx[kSortTile];
-  __shared__ double so[NOUT][kSortTile];
-  __shared__ unsigned short sidx[kSortTile];
+  constexpr int NC = F::NCLS, EPT = sort_ept<F>::value, TILE = kBlock * EPT;
+  __shared__ double sx[TILE];
+  __shared__ double so2[NOUT == 2 ? TILE : 1];
+  __shared__ unsigned short sidx[TILE];
   __shared__ int cnt[NC], cur[NC];
   F f;
   const int tid = threadIdx.x;
-  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const size_t ntiles = (n + TILE - 1) / TILE;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const size_t base = tile * kSortTile;
-    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    const size_t base = tile * TILE;
+    const int valid = (int)((n - base) < (size_t)TILE ? (n - base) : (size_t)TILE);
     if (tid < NC) cnt[tid] = 0;
     __syncthreads();
-    double xv[kSortEPT];
-    int cl[kSortEPT];
+    int cl[EPT];
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
+      double v = 0.0;
+      cl[j] = -1;
       if (e < valid) {
-        xv[j] = __ldcs(x + base + e);
-        cl[j] = F::cls(xv[j]);
-      } else {
-        xv[j] = 0.0;
-        cl[j] = -1;
+        v = __ldcs(x + base + e);
+        cl[j] = F::cls(v);
       }
-      sx[e] = xv[j];
+      sx[e] = v;
     }
-    sort_count<NC>(cl, cnt, tid);
+    sort_count<NC, EPT>(cl, cnt, tid);
     __syncthreads();
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
     }
     __syncthreads();
-    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    sort_scatter<NC, EPT>(cl, cur, sidx, tid);
     __syncthreads();
     for (int k = tid; k < valid; k += kBlock) {
       int e = sidx[k];
       if constexpr (NOUT == 1) {
-        so[0][e] = f(sx[e]);
+        sx[e] = f(sx[e]);
       } else {
         double a, b;
         f.dual(sx[e], a, b);
-        so[0][e] = a;
-        so[NOUT - 1][e] = b;
+        sx[e] = a;
+        so2[e] = b;
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
       if (e < valid) {
-        __stcs(o1 + base + e, so[0][e]);
-        if constexpr (NOUT == 2) __stcs(o2 + base + e, so[NOUT - 1][e]);
+        __stcs(o1 + base + e, sx[e]);
+        if constexpr (NOUT == 2) __stcs(o2 + base + e, so2[e]);
       }
     }
     __syncthreads();
@@ -360,14 +366,14 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
       sx[e] = a;
       sy[e] = b;
     }
-    sort_count<NC>(cl, cnt, tid);
+    sort_count<NC, kSortEPT>(cl, cnt, tid);
     __syncthreads();
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
     }
     __syncthreads();
-    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    sort_scatter<NC, kSortEPT>(cl, cur, sidx, tid);
     __syncthreads();
     for (int k = tid; k < valid; k += kBlock) {
       int e = sidx[k];
@@ -443,7 +449,8 @@ sleefcu_status launch_sorted64(const char *name, const double *x, double *out, s
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted64<F, 1>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n);
+  constexpr int EPT = sort_ept<F>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n);
   return check_launch(name);
 }
 template <class F>
@@ -452,7 +459,8 @@ sleefcu_status launch_sorted64_dual(const char *name, const double *x, double *o
   if (n == 0) return SLEEFCU_OK;
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted64<F, 2>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n);
+  constexpr int EPT = sort_ept<F>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n);
   return check_launch(name);
 }
 template <class F>
@@ -576,14 +584,14 @@ __global__ void __launch_bounds__(kBlock) k_sorted32(const float *x, float *out,
       }
       sx[e] = v;
     }
-    sort_count<NC>(cl, cnt, tid);
+    sort_count<NC, kSortEPT>(cl, cnt, tid);
     __syncthreads();
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
     }
     __syncthreads();
-    sort_scatter<NC>(cl, cnt, cur, sidx, tid);
+    sort_scatter<NC, kSortEPT>(cl, cur, sidx, tid);
     __syncthreads();
     for (int k = tid; k < valid; k += kBlock) {
       int e = sidx[k];
