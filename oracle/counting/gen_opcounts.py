@@ -80,6 +80,9 @@ def classes(fn, x, y=None):
         c = {"st": pos & (x >= 8), "r2": pos & (x >= 1.75) & (x < 2.5), "m": pos & (x >= 1.25) & (x < 1.75),
              "lo": pos & (x >= 0.5) & (x < 1.25)}
         c["sh"] = pos & ~(c["st"] | c["r2"] | c["m"] | c["lo"])
+        if fn == "lgamma":                         # Stirling without its two smallest terms
+            c["stb"] = c["st"] & (x >= 2.0 ** 60)
+            c["st"] = c["st"] & ~(x >= 2.0 ** 60)
         c["rs"] = neg & (x < -7)
         c["rn"] = neg & (x >= -7)
         rest = np.ones_like(pos)

@@ -66,6 +66,9 @@ static dd_t lg_stirling(dd_t y) {
   dd_t ly = oracle_logk_dd(y);
   dd_t r = ddmul_d2_d2_d2(ddadd2_d2_d2_d(y, -0.5), ly);
   r = ddadd2_d2_d2_d2(r, dd(-y.x, -y.y));
+  /* from 2^60 on, log(2 pi)/2 + G(1/y^2)/y < 0.92 is under 2^-12 ulp of
+   * (y - 1/2) log y - y (ulp >= 2^13) and is left out */
+  if (y.x >= 0x1p60) return r;
   r = ddadd2_d2_d2_d2(r, dd(LOG2PI_H, LOG2PI_L));
   double ry = 1.0 / y.x;                      /* one reciprocal gives w = 1/y^2 and G(w)/y */
   double w = ry * ry;

@@ -889,6 +889,7 @@ __device__ __forceinline__ bool neg_intf(float x) {
 struct LgammaU10 {
   static constexpr int NCLS = 8;
   static constexpr bool SORT32 = true;
+  static constexpr int SORT_EPT = 16;   // 4096-element tiles (eight classes)
   __device__ static int cls(float x) { return gammaf_cls(x); }
   __device__ float operator()(float x) const {
     if (isnan_f(x)) return from_fbits(QNAN32);
@@ -903,6 +904,7 @@ struct LgammaU10 {
 struct TgammaU10 {
   static constexpr int NCLS = 8;
   static constexpr bool SORT32 = true;
+  static constexpr int SORT_EPT = 16;   // 4096-element tiles (eight classes)
   __device__ static int cls(float x) { return gammaf_cls(x); }
   __device__ float operator()(float x) const {
     uint32_t bx = fbits(x);

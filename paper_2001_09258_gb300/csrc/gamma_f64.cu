@@ -54,7 +54,7 @@ __device__ __forceinline__ d2 neg(d2 a) { return D2(-a.x, -a.y); }
 constexpr uint64_t G05 = 0x3FE0000000000000ull, G075 = 0x3FE8000000000000ull, G125 = 0x3FF4000000000000ull;
 constexpr uint64_t G175 = 0x3FFC000000000000ull, G25 = 0x4004000000000000ull, G7 = 0x401C000000000000ull;
 constexpr uint64_t G8 = 0x4020000000000000ull, G172 = 0x4065800000000000ull, G190 = 0x4067C00000000000ull;
-constexpr uint64_t G1015 = 0x7F60000000000000ull, G52 = 0x4330000000000000ull;
+constexpr uint64_t G1015 = 0x7F60000000000000ull, G52 = 0x4330000000000000ull, G60 = 0x43B0000000000000ull;
 
 
 // lgamma(2 + e), -0.25 <= e < 0.5
@@ -76,6 +76,9 @@ __device__ __forceinline__ d2 lg_stirling(d2 y) {
   d2 ly = logk_dd(y);
   d2 r = mul_d2d2(add_d2_d(y, -0.5), ly);
   r = add_d2d2(r, neg(y));
+  // from 2^60 on, log(2 pi)/2 + G(1/y^2)/y < 0.92 is under 2^-12 ulp of the
+  // rest (ulp >= 2^13) and is left out (those lanes sort into their own class)
+  if (bits(y.x) >= G60) return r;
   r = add_d2d2(r, D2(LOG2PI_H, LOG2PI_L));
   double ry = __ddiv_rn(1.0, y.x);            // one reciprocal: w = 1/y^2 and G(w)/y
   double w = __dmul_rn(ry, ry);
@@ -139,9 +142,13 @@ __device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (-
 }
 
 struct LgammaU10 {
-  static constexpr int NCLS = 8;
-  static constexpr int SORT_EPT = 16;   // 4096-element tiles: eight classes, several of them small
-  __device__ static int cls(double x) { return gamma_cls(x); }
+  static constexpr int NCLS = 9;
+  static constexpr int SORT_EPT = 16;   // 4096-element tiles: nine classes, several of them small
+  // class 8: x >= 2^60, Stirling's form without its two smallest terms
+  __device__ static int cls(double x) {
+    const int c = gamma_cls(x);
+    return (c == 0 && bits(x) >= G60) ? 8 : c;
+  }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);
     if (is_nan_b(bx)) return from_bits(QNAN64);

@@ -558,50 +558,48 @@ __global__ void __launch_bounds__(kBlock) k_dual32(const float *x, float *o1, fl
 }
 template <class F>
 __global__ void __launch_bounds__(kBlock) k_sorted32(const float *x, float *out, size_t n) {
-  constexpr int NC = F::NCLS;
-  __shared__ float sx[kSortTile];
-  __shared__ float so[kSortTile];
-  __shared__ unsigned short sidx[kSortTile];
+  constexpr int NC = F::NCLS, EPT = sort_ept<F>::value, TILE = kBlock * EPT;
+  __shared__ float sx[TILE];                   // arguments, then results in place
+  __shared__ unsigned short sidx[TILE];
   __shared__ int cnt[NC], cur[NC];
   F f;
   const int tid = threadIdx.x;
-  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const size_t ntiles = (n + TILE - 1) / TILE;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const size_t base = tile * kSortTile;
-    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    const size_t base = tile * TILE;
+    const int valid = (int)((n - base) < (size_t)TILE ? (n - base) : (size_t)TILE);
     if (tid < NC) cnt[tid] = 0;
     __syncthreads();
-    int cl[kSortEPT];
+    int cl[EPT];
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
       float v = 0.0f;
+      cl[j] = -1;
       if (e < valid) {
         v = __ldcs(x + base + e);
         cl[j] = F::cls(v);
-      } else {
-        cl[j] = -1;
       }
       sx[e] = v;
     }
-    sort_count<NC, kSortEPT>(cl, cnt, tid);
+    sort_count<NC, EPT>(cl, cnt, tid);
     __syncthreads();
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
     }
     __syncthreads();
-    sort_scatter<NC, kSortEPT>(cl, cur, sidx, tid);
+    sort_scatter<NC, EPT>(cl, cur, sidx, tid);
     __syncthreads();
     for (int k = tid; k < valid; k += kBlock) {
       int e = sidx[k];
-      so[e] = f(sx[e]);
+      sx[e] = f(sx[e]);
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
-      if (e < valid) __stcs(out + base + e, so[e]);
+      if (e < valid) __stcs(out + base + e, sx[e]);
     }
     __syncthreads();
   }
@@ -734,7 +732,8 @@ sleefcu_status launch_sorted32(const char *name, const float *x, float *out, siz
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted32<F>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, out, n);
+  constexpr int EPT = sort_ept<F>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, n);
   return check_launch(name);
 }
 

@@ -99,6 +99,9 @@ def path_mix(name, x, y=None, steps=None):
         if fn == "tgamma":
             rs, rn = rs & (x >= -190), rn
         c = {"st": st, "r2": r2, "m": m, "lo": lo, "sh": sh, "rs": rs, "rn": rn}
+        if fn == "lgamma":                         # x >= 2^60: the shorter Stirling form
+            c["stb"] = st & (x >= 2.0 ** 60)
+            c["st"] = st & ~(x >= 2.0 ** 60)
         out = {k: int(v.sum()) for k, v in c.items()}
         out["sp"] = int(ax.size - sum(out.values()))
         return out
