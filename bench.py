@@ -161,6 +161,26 @@ def launch(sleefcu, name, ins, outs, stream_ptr):
 E2E_CHUNK = 1 << 24          # elements per host-pipeline chunk of the end-to-end step
 
 
+def measured_pipe_counts():
+    """FP64 instructions per element measured by ncu for each FP64 entry point
+    (profiles/fp64_inst.json), or None when the kernel sources have changed
+    since the capture (the file records a hash of the CUDA sources)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fp64_inst.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2001_09258_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        fp = os.path.join(csrc, f)
+        if os.path.isfile(fp):
+            h.update(f.encode())
+            h.update(open(fp, "rb").read())
+    return rec.get("per_entry_point") if h.hexdigest()[:16] == rec.get("csrc_sha") else None
+
+
 def pipe_peak(sleefcu, torch, device, pipe="fp64"):
     """Measured FMA-pipe throughput (ops/s) with the library's probe kernels
     (8 independent FMA chains per thread, 8 blocks of 256 per SM)."""
@@ -534,6 +554,7 @@ def main():
     per_fn = {name: round(n / (avg[name] * 1e-3) / 1e9, 3) for name in names}
     # per-entry-point roofline: algorithmic FP64 ops of each launch's path mix
     per_roof = {}
+    pipe_counts = measured_pipe_counts()
     for name in names:
         fn = name.split("_")[0]
         hx = host[fn]
@@ -545,6 +566,8 @@ def main():
         per_roof[name] = {"ops_per_element": round(o / n, 2),
                           "div_per_element": round(dv / n, 3), "sqrt_per_element": round(sq / n, 3),
                           "fp64_frac": round(o / (avg[name] * 1e-3) / peak_fp64, 4)}
+        if pipe_counts and name in pipe_counts:
+            per_roof[name]["fp64_inst_per_element"] = pipe_counts[name]["fp64_inst"]
     ext = None
     if not args.no_extras:
         del dev, outs
@@ -574,6 +597,9 @@ def main():
             "sqrt_per_element": round(sq / n, 3),
             "ops_source": "oracle counting build, per path class (paper_2001_09258_gb300/opcounts.json), "
                           "weighted by this launch's path mix",
+            "fp64_inst_per_element": (pipe_counts or {}).get(dom, {}).get("fp64_inst"),
+            "fp64_inst_source": "ncu sm__sass_thread_inst_executed_op_fp64_pred_on on the C2 mix "
+                                "(profiles/fp64_inst.json; null when the kernels changed since)",
             "traffic": None}
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
