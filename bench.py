@@ -346,6 +346,31 @@ def stress(sleefcu, torch, device, st, sp, n5, peak_fp64):
                                  "[1e-300, 1e300]", "entry_points": out}
 
 
+def fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64, n=1 << 22):
+    """Section 7.1's remainder workload: throughput of fmod u10 as the
+    quotient size r grows from 1 to 1e25 (d uniform in [1, 100], dividend
+    uniform in [0.95 r d, 1.05 r d]); per r the Gelem/s, the long-division
+    steps per element counted by the kernel's own loop, and the FP64-pipe
+    fraction.  The steps grow by one every 52 bits of quotient, so the
+    throughput falls in steps."""
+    from paper_2001_09258_gb300 import inputs as I
+    from paper_2001_09258_gb300 import opcounts
+    pts = []
+    for e in range(0, 26):
+        r = 10.0 ** e
+        hx, hy = I.fmod_sweep(r, n)
+        ins = [torch.from_numpy(hx).to(device), torch.from_numpy(hy).to(device)]
+        outs = [torch.empty_like(ins[0])]
+        ms = time_calls(torch, st, lambda: launch(sleefcu, "fmod_u10_f64", ins, outs, sp), reps=5)
+        steps = int(fmod_steps(sleefcu, torch, ins[0], ins[1], False, sp).sum())
+        ops = opcounts.ops_per_launch("fmod_u10_f64", hx, hy, steps)
+        pts.append({"r": r, "gelem_s": round(n / (ms * 1e-3) / 1e9, 3), "steps_per_element": round(steps / n, 3),
+                    "fp64_frac": round(ops / (ms * 1e-3) / peak_fp64, 4)})
+        del ins, outs
+    return {"n": n, "workload": "d uniform [1, 100], x uniform [0.95 r d, 1.05 r d] (Section 7.1)",
+            "points": pts}
+
+
 def batched(sleefcu, torch, device, st, sp, narrays=4096):
     """4096 arrays, lengths log-uniform in [1, 2^20], each assigned an FP64 or
     FP32 entry point uniformly at random: one autotuned persistent launch (plain
@@ -577,6 +602,8 @@ def main():
         ext["batched"] = batched(sleefcu, torch, device, st, sp)
         torch.cuda.empty_cache()
         ext["stress"] = stress(sleefcu, torch, device, st, sp, args.n5, peak_fp64)
+        torch.cuda.empty_cache()
+        ext["fmod_sweep"] = fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64)
     dom = max(names, key=lambda nm: avg[nm])
     hx = host[dom.split("_")[0]]
     steps = None

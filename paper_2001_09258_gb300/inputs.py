@@ -217,6 +217,14 @@ def stress(fn, n, key="c5", operand=0):
     return _blocked(n, np.float64, lambda m, sfx: loguniform(k + sfx, m, lo, hi))
 
 
+def fmod_sweep(r, n, key="sweep"):
+    """The remainder workload of Section 7.1: d uniform in [1, 100] and the
+    dividend uniform in [0.95 r d, 1.05 r d], for a quotient size r."""
+    d = uniform(f"{key}/{r:g}/d", n, 1.0, 100.0)
+    u = uniform(f"{key}/{r:g}/u", n, 0.95, 1.05)
+    return u * (r * d), d
+
+
 def to_bf16_bits(x32):
     """binary32 -> bf16 bit patterns, round-to-nearest-even (input preparation)."""
     b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)

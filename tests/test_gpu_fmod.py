@@ -53,3 +53,12 @@ def test_large_argument_stress_sample():
     y = I.loguniform("c5/fy", 1 << 21, 1e-300, 1e300)
     for name in ("fmod_u10_f64", "remainder_u10_f64"):
         check(name, x, y)
+
+
+@pytest.mark.parametrize("name", ["fmod_u10_f64", "remainder_u10_f64"])
+@pytest.mark.parametrize("r", [1.0, 1e8, 1e16, 1e25])
+def test_section71_sweep_workload(name, r):
+    """The remainder workload of Section 7.1 (d in [1, 100], dividend in
+    [0.95 r d, 1.05 r d]) at several quotient sizes: bit-exact."""
+    x, y = I.fmod_sweep(r, 20001)
+    assert_bitexact(gpu_call(name, x, y), oracle.apply(name, x, y), x, f"{name}/r={r:g}")
