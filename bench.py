@@ -371,6 +371,34 @@ def fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64, n=1 << 22):
             "points": pts}
 
 
+def masked(sleefcu, torch, device, st, sp, n=1 << 26):
+    """The masked entry points (the paper's whole-function opmask) on the C2
+    arrays with a tenth and a half of the elements selected: time against
+    the unmasked call, which evaluates every element."""
+    from paper_2001_09258_gb300 import inputs as I
+    import numpy as np
+    out = {}
+    for name in ("sin_u10_f64", "tgamma_u10_f64", "pow_u10_f64"):
+        fn = name.split("_")[0]
+        ins = [torch.from_numpy(I.workload(fn, n, key="c2/rank0", operand=k)).to(device)
+               for k in range(2 if sleefcu.FUNCS[fn] == "b" else 1)]
+        o = torch.empty_like(ins[0])
+        full = time_calls(torch, st, lambda: launch(sleefcu, name, ins, [o], sp), reps=3)
+        rec = {"unmasked_ms": round(full, 3)}
+        r = torch.from_numpy(I.raw("c2/mask", n) % np.uint64(10)).to(device)
+        for label, keep in (("tenth", 1), ("half", 5)):
+            m = (r < keep).to(torch.uint8)
+            y = ins[1] if len(ins) > 1 else None
+            ms = time_calls(torch, st, lambda: sleefcu.call_masked(name, ins[0], m, y=y, out=o, stream=st), reps=3)
+            sel = keep / 10
+            rec[label] = {"ms": round(ms, 3), "time_vs_unmasked": round(ms / full, 3),
+                          "selected_gelem_s": round(sel * n / (ms * 1e-3) / 1e9, 3)}
+        out[name] = rec
+        del ins, o
+        torch.cuda.empty_cache()
+    return {"n": n, "workload": "C2 arrays, mask bytes from a seeded stream", "entry_points": out}
+
+
 def batched(sleefcu, torch, device, st, sp, narrays=4096):
     """4096 arrays, lengths log-uniform in [1, 2^20], each assigned an FP64 or
     FP32 entry point uniformly at random: one autotuned persistent launch (plain
@@ -604,6 +632,8 @@ def main():
         ext["stress"] = stress(sleefcu, torch, device, st, sp, args.n5, peak_fp64)
         torch.cuda.empty_cache()
         ext["fmod_sweep"] = fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64)
+        torch.cuda.empty_cache()
+        ext["masked"] = masked(sleefcu, torch, device, st, sp)
     dom = max(names, key=lambda nm: avg[nm])
     hx = host[dom.split("_")[0]]
     steps = None

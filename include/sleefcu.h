@@ -218,6 +218,135 @@ sleefcu_status sleefcu_tgamma_u35_f64(const double *x, double *out, size_t n, sl
 sleefcu_status sleefcu_lgamma_u10_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 sleefcu_status sleefcu_lgamma_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
 
+/* ---------------- masked FP64 entry points ----------------
+ * The paper's whole-function opmask (Section 4): each FP64 entry point also
+ * takes a mask of n bytes in device memory and evaluates only the elements
+ * whose mask byte is non-zero; the other outputs are left as they are.  The
+ * selected elements of each tile are gathered (and grouped by reduction
+ * path) before they are evaluated, so the work scales with the number of
+ * selected elements.  Results equal the unmasked entry point's bit for bit;
+ * argument rules as for those (mask included). */
+sleefcu_status sleefcu_sin_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_sin_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_cos_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_cos_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_tan_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_tan_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_sincos_u10_f64_masked(const double *x, const uint8_t *mask, double *out_sin,
+                                             double *out_cos, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sincos_u35_f64_masked(const double *x, const uint8_t *mask, double *out_sin,
+                                             double *out_cos, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_exp_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_log_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_log_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u10_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                          size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_pow_u35_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                          size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_asin_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_asin_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_acos_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_atan_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u10_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                            size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_atan2_u35_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                            size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_fmod_u10_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                           size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_fmod_u35_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                           size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u10_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                                size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_remainder_u35_f64_masked(const double *x, const double *y, const uint8_t *mask, double *out,
+                                                size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_exp2_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_exp2_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_exp10_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_expm1_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_log2_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_log10_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_log1p_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_cbrt_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_sinh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_cosh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_tanh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_asinh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_acosh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_atanh_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                            sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_erf_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                          sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_erfc_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                           sleefcu_stream stream);
+sleefcu_status sleefcu_tgamma_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                             sleefcu_stream stream);
+sleefcu_status sleefcu_tgamma_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                             sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u10_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                             sleefcu_stream stream);
+sleefcu_status sleefcu_lgamma_u35_f64_masked(const double *x, const uint8_t *mask, double *out, size_t n,
+                                             sleefcu_stream stream);
+
 /* ---------------- FP32 family (float-float forms) ----------------
  * The same methods in binary32 arithmetic only, with float-float pairs where
  * the 1-ULP bound needs them (the paper describes the FP64 functions; "all

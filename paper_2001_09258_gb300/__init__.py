@@ -54,6 +54,12 @@ def entry_points():
     return out
 
 
+def masked_entry_points():
+    """The masked FP64 entry points (sleefcu_<name>_masked), by the name of
+    the entry point they mask."""
+    return [e for e in entry_points() if e.endswith("_f64")]
+
+
 def lib():
     """Load libsleefcu.so (building it first if it does not exist)."""
     global _lib
@@ -77,6 +83,12 @@ def lib():
             f = getattr(L, "sleefcu_" + name)
             f.restype = ctypes.c_int
             nptr = {"u": 2, "b": 3, "sc": 3}[FUNCS[fn]]
+            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+        for name in masked_entry_points():
+            fn = name.split("_")[0]
+            f = getattr(L, "sleefcu_" + name + "_masked")
+            f.restype = ctypes.c_int
+            nptr = {"u": 3, "b": 4, "sc": 4}[FUNCS[fn]]          # the mask comes after the inputs
             f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
         _lib = L
     return _lib
@@ -125,6 +137,37 @@ def call(name, x, y=None, out=None, out2=None, stream=None):
     else:
         rc = f(x.data_ptr(), out.data_ptr(), out2.data_ptr(), x.numel(), sp)
     _check(rc, name)
+    return (out, out2) if kind == "sc" else out
+
+
+def call_masked(name, x, mask, y=None, out=None, out2=None, stream=None):
+    """sleefcu_<name>_masked on CUDA tensors: out[i] (and out2[i]) is
+    computed where mask[i] != 0 (a uint8/bool tensor of x's length) and left
+    as it is elsewhere.  Allocates outputs with empty_like when not given."""
+    import torch
+    fn = name.split("_")[0]
+    kind = FUNCS[fn]
+    if not x.is_cuda or not mask.is_cuda:
+        raise SleefcuError("sleefcu works on CUDA tensors only")
+    if mask.numel() != x.numel():
+        raise SleefcuError("call_masked: mask and x differ in length")
+    x = x.contiguous()
+    m = mask.contiguous().view(torch.uint8) if mask.dtype == torch.bool else mask.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    if kind == "sc" and out2 is None:
+        out2 = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    sp = ctypes.c_void_p(st.cuda_stream)
+    f = raw(name + "_masked")
+    if kind == "u":
+        rc = f(x.data_ptr(), m.data_ptr(), out.data_ptr(), x.numel(), sp)
+    elif kind == "b":
+        y = y.contiguous()
+        rc = f(x.data_ptr(), y.data_ptr(), m.data_ptr(), out.data_ptr(), x.numel(), sp)
+    else:
+        rc = f(x.data_ptr(), m.data_ptr(), out.data_ptr(), out2.data_ptr(), x.numel(), sp)
+    _check(rc, name + "_masked")
     return (out, out2) if kind == "sc" else out
 
 

@@ -643,41 +643,83 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_unary64<derived64::F>("sleefcu_" #NAME, x, out, n, s);                    \
   }
+#define UNARY64_MASKED(NAME, F)                                                     \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<derived64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 #define SORTED64(NAME, F)                                                                   \
   extern "C" sleefcu_status sleefcu_##NAME(const double *x, double *out, size_t n,          \
                                            sleefcu_stream s) {                              \
     return launch_sorted64<derived64::F>("sleefcu_" #NAME, x, out, n, s);                   \
   }
+#define SORTED64_MASKED(NAME, F)                                                    \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<derived64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 UNARY64(exp2_u10_f64, Exp2U10)
+UNARY64_MASKED(exp2_u10_f64, Exp2U10)
 UNARY64(exp2_u35_f64, Exp2U35)
+UNARY64_MASKED(exp2_u35_f64, Exp2U35)
 UNARY64(exp10_u10_f64, Exp10U10)
+UNARY64_MASKED(exp10_u10_f64, Exp10U10)
 UNARY64(exp10_u35_f64, Exp10U35)
+UNARY64_MASKED(exp10_u35_f64, Exp10U35)
 UNARY64(expm1_u10_f64, Expm1U10)
+UNARY64_MASKED(expm1_u10_f64, Expm1U10)
 UNARY64(expm1_u35_f64, Expm1U35)
+UNARY64_MASKED(expm1_u35_f64, Expm1U35)
 UNARY64(log2_u10_f64, Log2U10)
+UNARY64_MASKED(log2_u10_f64, Log2U10)
 UNARY64(log2_u35_f64, Log2U35)
+UNARY64_MASKED(log2_u35_f64, Log2U35)
 UNARY64(log10_u10_f64, Log10U10)
+UNARY64_MASKED(log10_u10_f64, Log10U10)
 UNARY64(log10_u35_f64, Log10U35)
+UNARY64_MASKED(log10_u35_f64, Log10U35)
 UNARY64(log1p_u10_f64, Log1pU10)
+UNARY64_MASKED(log1p_u10_f64, Log1pU10)
 UNARY64(log1p_u35_f64, Log1pU35)
+UNARY64_MASKED(log1p_u35_f64, Log1pU35)
 UNARY64(cbrt_u10_f64, CbrtU10)
+UNARY64_MASKED(cbrt_u10_f64, CbrtU10)
 UNARY64(cbrt_u35_f64, CbrtU35)
+UNARY64_MASKED(cbrt_u35_f64, CbrtU35)
 SORTED64(sinh_u10_f64, SinhU10)
+SORTED64_MASKED(sinh_u10_f64, SinhU10)
 SORTED64(sinh_u35_f64, SinhU35)
+SORTED64_MASKED(sinh_u35_f64, SinhU35)
 SORTED64(cosh_u10_f64, CoshU10)
+SORTED64_MASKED(cosh_u10_f64, CoshU10)
 SORTED64(cosh_u35_f64, CoshU35)
+SORTED64_MASKED(cosh_u35_f64, CoshU35)
 UNARY64(tanh_u10_f64, TanhU10)
+UNARY64_MASKED(tanh_u10_f64, TanhU10)
 UNARY64(tanh_u35_f64, TanhU35)
+UNARY64_MASKED(tanh_u35_f64, TanhU35)
 SORTED64(asinh_u10_f64, AsinhU10)
+SORTED64_MASKED(asinh_u10_f64, AsinhU10)
 SORTED64(asinh_u35_f64, AsinhU10)
+SORTED64_MASKED(asinh_u35_f64, AsinhU10)
 SORTED64(acosh_u10_f64, AcoshU10)
+SORTED64_MASKED(acosh_u10_f64, AcoshU10)
 SORTED64(acosh_u35_f64, AcoshU10)
+SORTED64_MASKED(acosh_u35_f64, AcoshU10)
 SORTED64(erf_u10_f64, ErfU10)
+SORTED64_MASKED(erf_u10_f64, ErfU10)
 SORTED64(erf_u35_f64, ErfU35)
+SORTED64_MASKED(erf_u35_f64, ErfU35)
 SORTED64(erfc_u10_f64, ErfcU10)
+SORTED64_MASKED(erfc_u10_f64, ErfcU10)
 SORTED64(erfc_u35_f64, ErfcU10)
+SORTED64_MASKED(erfc_u35_f64, ErfcU10)
 UNARY64(atanh_u10_f64, AtanhU10)
+UNARY64_MASKED(atanh_u10_f64, AtanhU10)
 UNARY64(atanh_u35_f64, AtanhU10)
+UNARY64_MASKED(atanh_u35_f64, AtanhU10)
 #undef UNARY64
+#undef UNARY64_MASKED
 #undef SORTED64
+#undef SORTED64_MASKED
 #endif  // SLEEFCU_FUNCTORS_ONLY

@@ -155,10 +155,19 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_unary64<explog64::F>("sleefcu_" #NAME, x, out, n, s);                     \
   }
+#define UNARY64_MASKED(NAME, F)                                                     \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<explog64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 UNARY64(exp_u10_f64, ExpU10)
+UNARY64_MASKED(exp_u10_f64, ExpU10)
 UNARY64(exp_u35_f64, ExpU35)
+UNARY64_MASKED(exp_u35_f64, ExpU35)
 UNARY64(log_u10_f64, LogU10)
+UNARY64_MASKED(log_u10_f64, LogU10)
 UNARY64(log_u35_f64, LogU35)
+UNARY64_MASKED(log_u35_f64, LogU35)
 
 extern "C" sleefcu_status sleefcu_pow_u10_f64(const double *x, const double *y, double *out, size_t n,
                                               sleefcu_stream s) {
@@ -168,5 +177,14 @@ extern "C" sleefcu_status sleefcu_pow_u35_f64(const double *x, const double *y, 
                                               sleefcu_stream s) {
   return launch_binary64<explog64::PowU10>("sleefcu_pow_u35_f64", x, y, out, n, s);
 }
+extern "C" sleefcu_status sleefcu_pow_u10_f64_masked(const double *x, const double *y, const uint8_t *mask,
+                                                     double *out, size_t n, sleefcu_stream s) {
+  return launch_masked64b<explog64::PowU10>("sleefcu_pow_u10_f64_masked", x, y, mask, out, n, s);
+}
+extern "C" sleefcu_status sleefcu_pow_u35_f64_masked(const double *x, const double *y, const uint8_t *mask,
+                                                     double *out, size_t n, sleefcu_stream s) {
+  return launch_masked64b<explog64::PowU10>("sleefcu_pow_u35_f64_masked", x, y, mask, out, n, s);
+}
 #undef UNARY64
+#undef UNARY64_MASKED
 #endif  // SLEEFCU_FUNCTORS_ONLY

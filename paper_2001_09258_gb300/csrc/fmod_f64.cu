@@ -147,11 +147,22 @@ using namespace sleefcu;
                                            size_t n, sleefcu_stream s) {                    \
     return launch_sorted64b<fmod64::F>("sleefcu_" #NAME, x, y, out, n, s);                  \
   }
+#define BIN64_MASKED(NAME, F)                                                               \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const double *y,           \
+                                                    const uint8_t *mask, double *out, size_t n, \
+                                                    sleefcu_stream s) {                         \
+    return launch_masked64b<fmod64::F>("sleefcu_" #NAME "_masked", x, y, mask, out, n, s);      \
+  }
 BIN64(fmod_u10_f64, FmodF)
 BIN64(fmod_u35_f64, FmodF)
 BIN64(remainder_u10_f64, RemainderF)
 BIN64(remainder_u35_f64, RemainderF)
+BIN64_MASKED(fmod_u10_f64, FmodF)
+BIN64_MASKED(fmod_u35_f64, FmodF)
+BIN64_MASKED(remainder_u10_f64, RemainderF)
+BIN64_MASKED(remainder_u35_f64, RemainderF)
 #undef BIN64
+#undef BIN64_MASKED
 
 extern "C" sleefcu_status sleefcu_fmod_steps_f64(const double *x, const double *y, double *out, size_t n,
                                                  sleefcu_stream s) {

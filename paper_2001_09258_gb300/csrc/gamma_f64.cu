@@ -212,9 +212,19 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_sorted64<gamma64::F>("sleefcu_" #NAME, x, out, n, s);                     \
   }
+#define SORTED64_MASKED(NAME, F)                                                    \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<gamma64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 SORTED64(tgamma_u10_f64, TgammaU10)
+SORTED64_MASKED(tgamma_u10_f64, TgammaU10)
 SORTED64(tgamma_u35_f64, TgammaU10)
+SORTED64_MASKED(tgamma_u35_f64, TgammaU10)
 SORTED64(lgamma_u10_f64, LgammaU10)
+SORTED64_MASKED(lgamma_u10_f64, LgammaU10)
 SORTED64(lgamma_u35_f64, LgammaU10)
+SORTED64_MASKED(lgamma_u35_f64, LgammaU10)
 #undef SORTED64
+#undef SORTED64_MASKED
 #endif  // SLEEFCU_FUNCTORS_ONLY

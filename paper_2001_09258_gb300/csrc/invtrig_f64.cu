@@ -254,12 +254,23 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_sorted64<invtrig64::F>("sleefcu_" #NAME, x, out, n, s);                   \
   }
+#define SORTED64_MASKED(NAME, F)                                                    \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<invtrig64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 SORTED64(asin_u10_f64, AsinU10)
+SORTED64_MASKED(asin_u10_f64, AsinU10)
 SORTED64(asin_u35_f64, AsinU35)
+SORTED64_MASKED(asin_u35_f64, AsinU35)
 SORTED64(acos_u10_f64, AcosU10)
+SORTED64_MASKED(acos_u10_f64, AcosU10)
 SORTED64(acos_u35_f64, AcosU35)
+SORTED64_MASKED(acos_u35_f64, AcosU35)
 SORTED64(atan_u10_f64, AtanU10)
+SORTED64_MASKED(atan_u10_f64, AtanU10)
 SORTED64(atan_u35_f64, AtanU35)
+SORTED64_MASKED(atan_u35_f64, AtanU35)
 
 extern "C" sleefcu_status sleefcu_atan2_u10_f64(const double *x, const double *y, double *out, size_t n,
                                                 sleefcu_stream s) {
@@ -269,5 +280,14 @@ extern "C" sleefcu_status sleefcu_atan2_u35_f64(const double *x, const double *y
                                                 sleefcu_stream s) {
   return launch_sorted64b<invtrig64::Atan2U35>("sleefcu_atan2_u35_f64", x, y, out, n, s);
 }
+extern "C" sleefcu_status sleefcu_atan2_u10_f64_masked(const double *x, const double *y, const uint8_t *mask,
+                                                       double *out, size_t n, sleefcu_stream s) {
+  return launch_masked64b<invtrig64::Atan2U10>("sleefcu_atan2_u10_f64_masked", x, y, mask, out, n, s);
+}
+extern "C" sleefcu_status sleefcu_atan2_u35_f64_masked(const double *x, const double *y, const uint8_t *mask,
+                                                       double *out, size_t n, sleefcu_stream s) {
+  return launch_masked64b<invtrig64::Atan2U35>("sleefcu_atan2_u35_f64_masked", x, y, mask, out, n, s);
+}
 #undef SORTED64
+#undef SORTED64_MASKED
 #endif  // SLEEFCU_FUNCTORS_ONLY

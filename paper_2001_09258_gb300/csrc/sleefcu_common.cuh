@@ -275,13 +275,18 @@ __device__ __forceinline__ void sort_count(const int (&cl)[EPT], int *cnt, int t
 // unary (NOUT = 1) or one-input-two-output (NOUT = 2) sorted kernel; each
 // result overwrites its staged argument (a sorted position belongs to one
 // thread), the second output of NOUT = 2 has its own buffer
-template <class F, int NOUT>
-__global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1, double *o2, size_t n) {
+//
+// MASKED: only the elements whose mask byte is non-zero are classified,
+// evaluated (densely, as the tile's sorted prefix) and stored; the other
+// outputs are left untouched (the masked entry points).
+template <class F, int NOUT, bool MASKED = false>
+__global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1, double *o2, size_t n,
+                                                     const uint8_t *mask = nullptr) {
   constexpr int NC = F::NCLS, EPT = sort_ept<F>::value, TILE = kBlock * EPT;
   __shared__ double sx[TILE];
   __shared__ double so2[NOUT == 2 ? TILE : 1];
   __shared__ unsigned short sidx[TILE];
-  __shared__ int cnt[NC], cur[NC];
+  __shared__ int cnt[NC], cur[NC], tot;
   F f;
   const int tid = threadIdx.x;
   const size_t ntiles = (n + TILE - 1) / TILE;
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1
       int e = j * kBlock + tid;
       double v = 0.0;
       cl[j] = -1;
-      if (e < valid) {
+      if (e < valid && (!MASKED || mask[base + e])) {
         v = __ldcs(x + base + e);
         cl[j] = F::cls(v);
       }
@@ -307,11 +312,13 @@ __global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
+      tot = acc;
     }
     __syncthreads();
     sort_scatter<NC, EPT>(cl, cur, sidx, tid);
     __syncthreads();
-    for (int k = tid; k < valid; k += kBlock) {
+    const int m = MASKED ? tot : valid;
+    for (int k = tid; k < m; k += kBlock) {
       int e = sidx[k];
       if constexpr (NOUT == 1) {
         sx[e] = f(sx[e]);
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
-      if (e < valid) {
+      if (e < valid && (!MASKED || mask[base + e])) {
         __stcs(o1 + base + e, sx[e]);
         if constexpr (NOUT == 2) __stcs(o2 + base + e, so2[e]);
       }
@@ -336,13 +343,14 @@ __global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1
 }
 
 // binary sorted kernel: class from (x, y)
-template <class F>
-__global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const double *y, double *o, size_t n) {
+template <class F, bool MASKED = false>
+__global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const double *y, double *o, size_t n,
+                                                      const uint8_t *mask = nullptr) {
   constexpr int NC = F::NCLS;
   __shared__ double sx[kSortTile];
   __shared__ double sy[kSortTile];
   __shared__ unsigned short sidx[kSortTile];
-  __shared__ int cnt[NC], cur[NC];
+  __shared__ int cnt[NC], cur[NC], tot;
   F f;
   const int tid = threadIdx.x;
   const size_t ntiles = (n + kSortTile - 1) / kSortTile;
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
     for (int j = 0; j < kSortEPT; j++) {
       int e = j * kBlock + tid;
       double a = 0.0, b = 0.0;
-      if (e < valid) {
+      if (e < valid && (!MASKED || mask[base + e])) {
         a = __ldcs(x + base + e);
         b = __ldcs(y + base + e);
         cl[j] = F::cls(a, b);
@@ -371,11 +379,13 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
     if (tid == 0) {
       int acc = 0;
       for (int c = 0; c < NC; c++) { cur[c] = acc; acc += cnt[c]; }
+      tot = acc;
     }
     __syncthreads();
     sort_scatter<NC, kSortEPT>(cl, cur, sidx, tid);
     __syncthreads();
-    for (int k = tid; k < valid; k += kBlock) {
+    const int m = MASKED ? tot : valid;
+    for (int k = tid; k < m; k += kBlock) {
       int e = sidx[k];
       double r = f(sx[e], sy[e]);
       sx[e] = r;   // each e is owned by exactly one k
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
 #pragma unroll
     for (int j = 0; j < kSortEPT; j++) {
       int e = j * kBlock + tid;
-      if (e < valid) __stcs(o + base + e, sx[e]);
+      if (e < valid && (!MASKED || mask[base + e])) __stcs(o + base + e, sx[e]);
     }
     __syncthreads();
   }
@@ -450,7 +460,7 @@ sleefcu_status launch_sorted64(const char *name, const double *x, double *out, s
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted64<F, 1>;
   constexpr int EPT = sort_ept<F>::value;
-  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n);
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n, nullptr);
   return check_launch(name);
 }
 template <class F>
@@ -460,7 +470,7 @@ sleefcu_status launch_sorted64_dual(const char *name, const double *x, double *o
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted64<F, 2>;
   constexpr int EPT = sort_ept<F>::value;
-  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n);
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n, nullptr);
   return check_launch(name);
 }
 template <class F>
@@ -469,7 +479,56 @@ sleefcu_status launch_sorted64b(const char *name, const double *x, const double 
   if (n == 0) return SLEEFCU_OK;
   if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   auto k = k_sorted64b<F>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n);
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, nullptr);
+  return check_launch(name);
+}
+
+// ---- masked entry points (the paper's whole-function opmask) ----
+// A functor without path classes is sorted as one class, so that the
+// selected elements are still evaluated densely.
+template <class F, class = void>
+struct has_classes : std::false_type {};
+template <class F>
+struct has_classes<F, std::void_t<decltype(F::NCLS)>> : std::true_type {};
+template <class F>
+struct OneClass : F {
+  static constexpr int NCLS = 1;
+  __device__ static int cls(double) { return 0; }
+  __device__ static int cls(double, double) { return 0; }
+};
+template <class F>
+using sortable_t = typename std::conditional<has_classes<F>::value, F, OneClass<F>>::type;
+
+template <class F>
+sleefcu_status launch_masked64(const char *name, const double *x, const uint8_t *mask, double *out, size_t n,
+                               sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !mask || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  using G = sortable_t<F>;
+  auto k = k_sorted64<G, 1, true>;
+  constexpr int EPT = sort_ept<G>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n, mask);
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_masked64_dual(const char *name, const double *x, const uint8_t *mask, double *o1,
+                                    double *o2, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !mask || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  using G = sortable_t<F>;
+  auto k = k_sorted64<G, 2, true>;
+  constexpr int EPT = sort_ept<G>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n, mask);
+  return check_launch(name);
+}
+template <class F>
+sleefcu_status launch_masked64b(const char *name, const double *x, const double *y, const uint8_t *mask,
+                                double *out, size_t n, sleefcu_stream s) {
+  if (n == 0) return SLEEFCU_OK;
+  if (!x || !y || !mask || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  using G = sortable_t<F>;
+  auto k = k_sorted64b<G, true>;
+  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, mask);
   return check_launch(name);
 }
 

@@ -370,12 +370,23 @@ using namespace sleefcu;
                                            sleefcu_stream s) {                              \
     return launch_sorted64<trig64::F>("sleefcu_" #NAME, x, out, n, s);                       \
   }
+#define UNARY64_MASKED(NAME, F)                                                     \
+  extern "C" sleefcu_status sleefcu_##NAME##_masked(const double *x, const uint8_t *mask,  \
+                                                    double *out, size_t n, sleefcu_stream s) { \
+    return launch_masked64<trig64::F>("sleefcu_" #NAME "_masked", x, mask, out, n, s);         \
+  }
 UNARY64(sin_u10_f64, SinU10)
+UNARY64_MASKED(sin_u10_f64, SinU10)
 UNARY64(sin_u35_f64, SinU35)
+UNARY64_MASKED(sin_u35_f64, SinU35)
 UNARY64(cos_u10_f64, CosU10)
+UNARY64_MASKED(cos_u10_f64, CosU10)
 UNARY64(cos_u35_f64, CosU35)
+UNARY64_MASKED(cos_u35_f64, CosU35)
 UNARY64(tan_u10_f64, TanU10)
+UNARY64_MASKED(tan_u10_f64, TanU10)
 UNARY64(tan_u35_f64, TanU35)
+UNARY64_MASKED(tan_u35_f64, TanU35)
 
 extern "C" sleefcu_status sleefcu_sincos_u10_f64(const double *x, double *os, double *oc, size_t n,
                                                  sleefcu_stream s) {
@@ -385,5 +396,14 @@ extern "C" sleefcu_status sleefcu_sincos_u35_f64(const double *x, double *os, do
                                                  sleefcu_stream s) {
   return launch_sorted64_dual<trig64::SinCosU35>("sleefcu_sincos_u35_f64", x, os, oc, n, s);
 }
+extern "C" sleefcu_status sleefcu_sincos_u10_f64_masked(const double *x, const uint8_t *mask, double *os,
+                                                        double *oc, size_t n, sleefcu_stream s) {
+  return launch_masked64_dual<trig64::SinCosU10>("sleefcu_sincos_u10_f64_masked", x, mask, os, oc, n, s);
+}
+extern "C" sleefcu_status sleefcu_sincos_u35_f64_masked(const double *x, const uint8_t *mask, double *os,
+                                                        double *oc, size_t n, sleefcu_stream s) {
+  return launch_masked64_dual<trig64::SinCosU35>("sleefcu_sincos_u35_f64_masked", x, mask, os, oc, n, s);
+}
 #undef UNARY64
+#undef UNARY64_MASKED
 #endif  // SLEEFCU_FUNCTORS_ONLY

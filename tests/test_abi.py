@@ -32,6 +32,8 @@ def test_binding_covers_header():
         assert "sleefcu_" + e in names, e
     fn_decl = {n for n in names if re.match(r"sleefcu_\w+_u(10|35)_(f64|f32|bf16|f16)$", n)}
     assert fn_decl == {"sleefcu_" + e for e in sleefcu.entry_points()}
+    masked = {n for n in names if n.endswith("_masked")}
+    assert masked == {"sleefcu_" + e + "_masked" for e in sleefcu.masked_entry_points()}
 
 
 def test_version_and_error_text():
@@ -84,3 +86,14 @@ def test_phtab_generators_agree():
     tab, ib = oracle.ph_table()
     assert np.array_equal(np.array(t64), tab)
     assert list(ib) == i64
+
+
+@pytest.mark.parametrize("name", sleefcu.masked_entry_points())
+def test_masked_n_zero_and_null_pointers(name):
+    """The masked entry points follow the same argument rules, the mask
+    included."""
+    f = sleefcu.raw(name + "_masked")
+    nptr = len(f.argtypes) - 2
+    assert f(*([None] * nptr), 0, None) == 0
+    assert f(*([None] * nptr), 5, None) == -1
+    assert name + "_masked" in sleefcu.last_error()
