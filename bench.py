@@ -385,9 +385,9 @@ def masked(sleefcu, torch, device, st, sp, n=1 << 26):
         o = torch.empty_like(ins[0])
         full = time_calls(torch, st, lambda: launch(sleefcu, name, ins, [o], sp), reps=3)
         rec = {"unmasked_ms": round(full, 3)}
-        r = torch.from_numpy(I.raw("c2/mask", n) % np.uint64(10)).to(device)
+        r = (I.raw("c2/mask", n) % np.uint64(10)).astype(np.uint8)
         for label, keep in (("tenth", 1), ("half", 5)):
-            m = (r < keep).to(torch.uint8)
+            m = torch.from_numpy((r < keep).astype(np.uint8)).to(device)
             y = ins[1] if len(ins) > 1 else None
             ms = time_calls(torch, st, lambda: sleefcu.call_masked(name, ins[0], m, y=y, out=o, stream=st), reps=3)
             sel = keep / 10
