@@ -14,6 +14,9 @@ from . import build as _build
 
 _lib = None
 K_U64, K_B64, K_SC64, K_U32, K_B32, K_SC32, K_U16 = 1, 2, 3, 11, 12, 13, 21
+# the int32 kinds of the remaining C99 set: ilogb (x -> int), ldexp (x, int -> x),
+# frexp (x -> x, int)
+K_UI64, K_BI64, K_SI64, K_UI32, K_BI32, K_SI32 = 4, 5, 6, 14, 15, 16
 
 
 def lib():
@@ -29,6 +32,8 @@ def lib():
         _lib.oracle_count.restype = ctypes.c_int
         _lib.oracle_name.restype = ctypes.c_char_p
         _lib.oracle_name.argtypes = [ctypes.c_int]
+        _lib.oracle_group.restype = ctypes.c_int
+        _lib.oracle_group.argtypes = [ctypes.c_int]
         _lib.oracle_ph_reduce.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib.oracle_ph_table_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -42,8 +47,15 @@ def lib():
 
 
 def names():
+    """The functions of the vectorized method's set (group 0)."""
     L = lib()
-    return [L.oracle_name(i).decode() for i in range(L.oracle_count())]
+    return [L.oracle_name(i).decode() for i in range(L.oracle_count()) if L.oracle_group(i) == 0]
+
+
+def c99_names():
+    """The remaining C99 functions (group 1)."""
+    L = lib()
+    return [L.oracle_name(i).decode() for i in range(L.oracle_count()) if L.oracle_group(i) == 1]
 
 
 def kind(name):
@@ -66,11 +78,13 @@ def apply(name, x, y=None, nthreads=None):
     dt = np.float64 if k < 10 else (np.float32 if k < 20 else np.uint16)
     x = np.ascontiguousarray(x, dtype=dt)
     n = x.size
-    out = np.empty_like(x)
+    out = np.empty(n, dtype=np.int32) if k in (K_UI64, K_UI32) else np.empty_like(x)
     out2 = np.empty_like(x) if k in (K_SC64, K_SC32) else None
+    if k in (K_SI64, K_SI32):
+        out2 = np.empty(n, dtype=np.int32)
     yp = None
-    if k in (K_B64, K_B32):
-        y = np.ascontiguousarray(y, dtype=dt)
+    if k in (K_B64, K_B32, K_BI64, K_BI32):
+        y = np.ascontiguousarray(y, dtype=np.int32 if k in (K_BI64, K_BI32) else dt)
         assert y.size == n
         yp = y.ctypes.data
     rc = lib().oracle_apply(name.encode(), x.ctypes.data, yp, out.ctypes.data,

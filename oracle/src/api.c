@@ -7,6 +7,9 @@
  * oracle_apply(name, x, y, out, out2, n, nthreads) evaluates the scalar
  * function `name` ("sin_u10_f64", ...) over n elements on nthreads POSIX
  * threads (static contiguous split).  Returns 0, or -1 for an unknown name.
+ * Group 0 is the function set of the vectorized method (registry.inc), group 1
+ * the remaining C99 functions (registry_c99.inc), whose kinds include int32
+ * operands and results (ilogb, ldexp, frexp).
  */
 #include <pthread.h>
 #include <stdlib.h>
@@ -14,11 +17,12 @@
 #include <stddef.h>
 #include "oracle.h"
 
-enum { K_U64 = 1, K_B64 = 2, K_SC64 = 3, K_U32 = 11, K_B32 = 12, K_SC32 = 13, K_U16 = 21 };
+enum { K_U64 = 1, K_B64 = 2, K_SC64 = 3, K_UI64 = 4, K_BI64 = 5, K_SI64 = 6,
+       K_U32 = 11, K_B32 = 12, K_SC32 = 13, K_UI32 = 14, K_BI32 = 15, K_SI32 = 16, K_U16 = 21 };
 
 typedef struct {
   const char *name;
-  int kind;
+  int kind, grp;
   union {
     double (*u64)(double);
     double (*b64)(double, double);
@@ -27,21 +31,41 @@ typedef struct {
     float (*b32)(float, float);
     void (*sc32)(float, float *, float *);
     uint16_t (*u16)(uint16_t);
+    int32_t (*ui64)(double);
+    double (*bi64)(double, int32_t);
+    double (*si64)(double, int32_t *);
+    int32_t (*ui32)(float);
+    float (*bi32)(float, int32_t);
+    float (*si32)(float, int32_t *);
     void *any;
   } f;
 } entry;
 
-#define U64(n) { #n, K_U64, { .u64 = oracle_##n } }
-#define B64(n) { #n, K_B64, { .b64 = oracle_##n } }
-#define SC64(n) { #n, K_SC64, { .sc64 = oracle_##n } }
-#define U32(n) { #n, K_U32, { .u32 = oracle_##n } }
-#define B32(n) { #n, K_B32, { .b32 = oracle_##n } }
-#define SC32(n) { #n, K_SC32, { .sc32 = oracle_##n } }
-#define U16(n) { #n, K_U16, { .u16 = oracle_##n } }
+#define U64(n) { #n, K_U64, 0, { .u64 = oracle_##n } }
+#define B64(n) { #n, K_B64, 0, { .b64 = oracle_##n } }
+#define SC64(n) { #n, K_SC64, 0, { .sc64 = oracle_##n } }
+#define U32(n) { #n, K_U32, 0, { .u32 = oracle_##n } }
+#define B32(n) { #n, K_B32, 0, { .b32 = oracle_##n } }
+#define SC32(n) { #n, K_SC32, 0, { .sc32 = oracle_##n } }
+#define U16(n) { #n, K_U16, 0, { .u16 = oracle_##n } }
+
+#define XU64(n) { #n, K_U64, 1, { .u64 = oracle_##n } }
+#define XB64(n) { #n, K_B64, 1, { .b64 = oracle_##n } }
+#define XSC64(n) { #n, K_SC64, 1, { .sc64 = oracle_##n } }
+#define XUI64(n) { #n, K_UI64, 1, { .ui64 = oracle_##n } }
+#define XBI64(n) { #n, K_BI64, 1, { .bi64 = oracle_##n } }
+#define XSI64(n) { #n, K_SI64, 1, { .si64 = oracle_##n } }
+#define XU32(n) { #n, K_U32, 1, { .u32 = oracle_##n } }
+#define XB32(n) { #n, K_B32, 1, { .b32 = oracle_##n } }
+#define XSC32(n) { #n, K_SC32, 1, { .sc32 = oracle_##n } }
+#define XUI32(n) { #n, K_UI32, 1, { .ui32 = oracle_##n } }
+#define XBI32(n) { #n, K_BI32, 1, { .bi32 = oracle_##n } }
+#define XSI32(n) { #n, K_SI32, 1, { .si32 = oracle_##n } }
 
 static const entry REG[] = {
 #include "registry.inc"
-  { NULL, 0, { .any = NULL } }
+#include "registry_c99.inc"
+  { NULL, 0, 0, { .any = NULL } }
 };
 
 static const entry *find(const char *name) {
@@ -57,6 +81,7 @@ int oracle_kind(const char *name) {
 
 int oracle_count(void) { int n = 0; for (const entry *e = REG; e->name; e++) n++; return n; }
 const char *oracle_name(int i) { return (i >= 0 && i < oracle_count()) ? REG[i].name : NULL; }
+int oracle_group(int i) { return (i >= 0 && i < oracle_count()) ? REG[i].grp : -1; }
 
 typedef struct {
   const entry *e; const void *x, *y; void *o, *o2; size_t lo, hi;
@@ -73,6 +98,12 @@ static void run(const job *j) {
       case K_B32: ((float *)j->o)[i] = e->f.b32(((const float *)j->x)[i], ((const float *)j->y)[i]); break;
       case K_SC32: e->f.sc32(((const float *)j->x)[i], (float *)j->o + i, (float *)j->o2 + i); break;
       case K_U16: ((uint16_t *)j->o)[i] = e->f.u16(((const uint16_t *)j->x)[i]); break;
+      case K_UI64: ((int32_t *)j->o)[i] = e->f.ui64(((const double *)j->x)[i]); break;
+      case K_BI64: ((double *)j->o)[i] = e->f.bi64(((const double *)j->x)[i], ((const int32_t *)j->y)[i]); break;
+      case K_SI64: ((double *)j->o)[i] = e->f.si64(((const double *)j->x)[i], (int32_t *)j->o2 + i); break;
+      case K_UI32: ((int32_t *)j->o)[i] = e->f.ui32(((const float *)j->x)[i]); break;
+      case K_BI32: ((float *)j->o)[i] = e->f.bi32(((const float *)j->x)[i], ((const int32_t *)j->y)[i]); break;
+      case K_SI32: ((float *)j->o)[i] = e->f.si32(((const float *)j->x)[i], (int32_t *)j->o2 + i); break;
     }
   }
 }

@@ -41,4 +41,10 @@
 #define LGAMMA_ST_COEFFS 0x1.5555555555555p-4, -0x1.6c16c16c16c16p-9, 0x1.a01a01a0196bap-11, -0x1.381381362b216p-11, 0x1.b951df87db260p-11, -0x1.f6a98a1bab42ap-10, 0x1.a3e150e3f70bdp-8, -0x1.dee553034d0abp-6, 0x1.490abb645435cp-3, -0x1.7031193624fc5p-1
 #define SINPI_HEAD -0x1.4abbce625be53p+2, 0x1.05511c684d1cbp-52
 #define SINPI_COEFFS 0x1.466bc6775aae2p+1, -0x1.32d2cce62bddep-1, 0x1.50783487f6d9cp-4, -0x1.e3074fec25b1dp-8, 0x1.e8f4422d6f029p-12, -0x1.6fb6226ceb4fdp-16, 0x1.b1dd7b5e6be80p-21, -0x1.5249d9e04752dp-24, 0x1.46d5e635ea9dep-23, -0x1.f9b2ef7ed3d1ep-23, 0x1.563183599af6cp-23
+/* C99 set: sin(pi s) = s (c0 + t (c1 + t P(t))) and cos(pi s) = 1 + t (c0 + t P(t)),
+ * t = s^2 in [0, 1/16]; HEAD = the DD leading coefficients (oracle/coeffs/fit_c99.py) */
+#define C99_SINPI_HEAD 0x1.921fb54442d18p+1, 0x1.1a5ee6df61731p-53, -0x1.4abbce625be53p+2, 0x1.1317e21cffea3p-52
+#define C99_SINPI_COEFFS 0x1.466bc6775aad9p+1, -0x1.32d2cce62ac1bp-1, 0x1.50783485cd9dep-4, -0x1.e3074b54cb043p-8, 0x1.e8eed5bfbbb87p-12, -0x1.6c5d06da75ea5p-16
+#define C99_COSPI_HEAD -0x1.3bd3cc9be45dep+2, -0x1.692b254f96cb6p-52
+#define C99_COSPI_COEFFS 0x1.03c1f081b5ac4p+2, -0x1.55d3c7e3cc16cp+0, 0x1.e1f5068965fb7p-3, -0x1.a6d1f30fc0185p-6, 0x1.f9d42dc364f31p-10, -0x1.b7598d34a382dp-14, 0x1.41f35eddaaed2p-18
 #endif

@@ -159,6 +159,56 @@ uint16_t oracle_f32_to_bf16(float);
 float oracle_f16_to_f32(uint16_t);
 uint16_t oracle_f32_to_f16(float);
 
+/* the remaining C99 set (c99ext.c) */
+double oracle_fabs_f64(double);
+double oracle_trunc_f64(double);
+double oracle_floor_f64(double);
+double oracle_ceil_f64(double);
+double oracle_round_f64(double);
+double oracle_rint_f64(double);
+double oracle_logb_f64(double);
+double oracle_sqrt_u05_f64(double);
+double oracle_sqrt_u35_f64(double);
+double oracle_sinpi_u05_f64(double);
+double oracle_sinpi_u35_f64(double);
+double oracle_cospi_u05_f64(double);
+double oracle_cospi_u35_f64(double);
+double oracle_copysign_f64(double, double);
+double oracle_fmax_f64(double, double);
+double oracle_fmin_f64(double, double);
+double oracle_fdim_f64(double, double);
+double oracle_nextafter_f64(double, double);
+double oracle_hypot_u05_f64(double, double);
+double oracle_hypot_u35_f64(double, double);
+void oracle_modf_f64(double, double *, double *);
+int32_t oracle_ilogb_f64(double);
+double oracle_ldexp_f64(double, int32_t);
+double oracle_frexp_f64(double, int32_t *);
+float oracle_fabs_f32(float);
+float oracle_trunc_f32(float);
+float oracle_floor_f32(float);
+float oracle_ceil_f32(float);
+float oracle_round_f32(float);
+float oracle_rint_f32(float);
+float oracle_logb_f32(float);
+float oracle_sqrt_u05_f32(float);
+float oracle_sqrt_u35_f32(float);
+float oracle_sinpi_u05_f32(float);
+float oracle_sinpi_u35_f32(float);
+float oracle_cospi_u05_f32(float);
+float oracle_cospi_u35_f32(float);
+float oracle_copysign_f32(float, float);
+float oracle_fmax_f32(float, float);
+float oracle_fmin_f32(float, float);
+float oracle_fdim_f32(float, float);
+float oracle_nextafter_f32(float, float);
+float oracle_hypot_u05_f32(float, float);
+float oracle_hypot_u35_f32(float, float);
+void oracle_modf_f32(float, float *, float *);
+int32_t oracle_ilogb_f32(float);
+float oracle_ldexp_f32(float, int32_t);
+float oracle_frexp_f32(float, int32_t *);
+
 int oracle_apply(const char *name, const void *x, const void *y, void *out, void *out2,
                  size_t n, int nthreads);
 #endif

@@ -52,6 +52,22 @@ static int eval(const char *fn, double xd, double yd, Q *r) {
   else if (!strcmp(fn, "lgamma")) *r = lgammaq(x);
   else if (!strcmp(fn, "fmod")) *r = fmodq(x, y);
   else if (!strcmp(fn, "remainder")) *r = remainderq(x, y);
+  else if (!strcmp(fn, "hypot")) *r = hypotq(x, y);
+  else if (!strcmp(fn, "sqrt")) *r = sqrtq(x);
+  else if (!strcmp(fn, "sinpi") || !strcmp(fn, "cospi")) {
+    /* reduce exactly in binary128 (x is a double): r = x - 2 rint(x/2) in [-1, 1] */
+    if (isinfq(x) || isnanq(x)) { *r = nanq(""); return 0; }
+    Q rr = x - 2 * rintq(x / 2);
+    if (!strcmp(fn, "sinpi")) {
+      if (rr == rintq(rr)) { *r = signbitq(x) ? -(Q)0 : (Q)0; return 0; }   /* integers: +-0 */
+      if (rr > 0.5Q) rr = 1 - rr;                    /* sin(pi r) = sin(pi (1 - r)) */
+      if (rr < -0.5Q) rr = -1 - rr;
+      *r = sinq(M_PIq * rr);
+    } else {
+      Q h = 0.5Q - fabsq(rr);                        /* cos(pi r) = sin(pi (1/2 - |r|)) */
+      *r = h == 0 ? (Q)0 : sinq(M_PIq * h);
+    }
+  }
   else return -1;
   return 0;
 }
