@@ -299,41 +299,28 @@ float oracle_hypot_u35_f32(float x, float y) { return hypot32(x, y, 0); }
 
 /* ---------------- sinpi, cospi ----------------
  * sin(pi s) = s g(t) and cos(pi s) = 1 + t f(t), t = s^2, |s| <= 1/4, with
- * g = c0 + t (c1 + t (c2 + t Q(t))) and f = c0 + t (c1 + t R(t)).  In the
- * 0.5-ULP forms every Horner step down to the plain polynomial is a DD (FF)
- * step, so that the rounding of Q or R is damped by t^3 or t^2.  For
- * |s| < 2^-500 (2^-60) sin(pi s) is pi s to far below an ulp; the product is
- * formed from s 2^200 (2^64) so that the DD (FF) tail stays representable. */
-static const double SPI_H[4] = { C99_SINPI_HEAD };     /* g: c0 (hi, lo), c1 (hi, lo) */
-static const double SPI_P[6] = { C99_SINPI_COEFFS };   /* c2, then Q */
-static const double CPI_H[2] = { C99_COSPI_HEAD };     /* f: c0 (hi, lo) */
-static const double CPI_P[7] = { C99_COSPI_COEFFS };   /* c1, then R */
+ * g and f of eight coefficients each.  Both take one shape, so that an
+ * element's quadrant only selects coefficients (Section 5's branch-free
+ * evaluation): P = k0 + t (k1 + t (k2 + t p(t))), p the plain polynomial of
+ * the five highest coefficients (three in binary32, cos padded with a zero),
+ * then sin(pi s) = s P and cos(pi s) = 1 + t P.  In the 0.5-ULP forms k0 and
+ * k1 are DD (FF) pairs and the three outer Horner steps are DD (FF) steps,
+ * so that the rounding of p is damped by t^3; for |s| < 2^-500 (2^-100) the
+ * sine is evaluated on s 2^200 (s 2^80) and scaled back, so that the DD (FF)
+ * tails stay representable (the scaled argument stays below 2^-300 (2^-20),
+ * where sin(pi s) is pi s to far below an ulp).  The 3.5-ULP forms take the heads and plain
+ * Horner steps. */
+static const double SPI_H[4] = { C99_SINPI_HEAD };     /* g: k0 (hi, lo), k1 (hi, lo) */
+static const double SPI_P[6] = { C99_SINPI_COEFFS };   /* g: k2, then p */
+static const double CPI_H[2] = { C99_COSPI_HEAD };     /* f: k0 (hi, lo) */
+static const double CPI_P[7] = { C99_COSPI_COEFFS };   /* f: k1, k2, then p */
 
-static dd_t sin_pi_dd(double s) {
-  dd_t t = ddmul_d2_d_d(s, s);
-  double p = poly_d(t.x, SPI_P + 1, 5);
-  dd_t in = ddadd2_d2_d_d(SPI_P[0], t.x * p);
-  in = ddadd2_d2_d2_d2(dd(SPI_H[2], SPI_H[3]), ddmul_d2_d2_d2(t, in));
-  in = ddadd2_d2_d2_d2(dd(SPI_H[0], SPI_H[1]), ddmul_d2_d2_d2(t, in));
-  return ddmul_d2_d2_d(in, s);
-}
-static dd_t cos_pi_dd(double s) {
-  dd_t t = ddmul_d2_d_d(s, s);
-  double p = poly_d(t.x, CPI_P + 1, 6);
-  dd_t in = ddadd2_d2_d_d(CPI_P[0], t.x * p);
-  in = ddadd2_d2_d2_d2(dd(CPI_H[0], CPI_H[1]), ddmul_d2_d2_d2(t, in));
-  return ddadd2_d2_d_d2(1.0, ddmul_d2_d2_d2(t, in));
-}
-/* the 3.5-ULP forms: the heads of the pairs, plain Horner steps */
-static double sin_pi_35(double s) {
-  double t = s * s;
-  double p = poly_d(t, SPI_P + 1, 5);
-  return s * fma(t, fma(t, fma(t, p, SPI_P[0]), SPI_H[2]), SPI_H[0]);
-}
-static double cos_pi_35(double s) {
-  double t = s * s;
-  double p = poly_d(t, CPI_P + 1, 6);
-  return fma(t, fma(t, fma(t, p, CPI_P[0]), CPI_H[0]), 1.0);
+typedef struct { dd_t k0, k1; double k2; const double *p; } pik_t;
+static pik_t pi_coeffs(int cosine) {
+  pik_t c;
+  if (cosine) { c.k0 = dd(CPI_H[0], CPI_H[1]); c.k1 = dd(CPI_P[0], 0.0); c.k2 = CPI_P[1]; c.p = CPI_P + 2; }
+  else { c.k0 = dd(SPI_H[0], SPI_H[1]); c.k1 = dd(SPI_H[2], SPI_H[3]); c.k2 = SPI_P[0]; c.p = SPI_P + 1; }
+  return c;
 }
 
 /* x = q/2 + s exactly, with q = rint(2x) and o = q mod 4; |x| >= 2^53 is an
@@ -350,15 +337,25 @@ static double sincospi64(double x, int cosine, int u05) {
   if (isnan(x) || isinf(x)) return canon_nan();
   double s = reduce_pi(x, &o);
   o = (o + cosine) & 3;                       /* cos(pi x) = sin(pi (x + 1/2)) */
+  int c = o & 1;                              /* the cosine polynomial of s */
+  pik_t k = pi_coeffs(c);
   double v;
-  if (u05 && !(o & 1) && fabs(s) < 0x1p-500) {
-    dd_t r = ddmul_d2_d2_d(dd(SPI_H[0], SPI_H[1]), s * 0x1p200);
-    v = (r.x + r.y) * 0x1p-200;
-  } else if (u05) {
-    dd_t r = (o & 1) ? cos_pi_dd(s) : sin_pi_dd(s);
+  if (u05) {
+    int tiny = !c && fabs(s) < 0x1p-500;
+    if (tiny) s *= 0x1p200;
+    dd_t t = ddmul_d2_d_d(s, s);
+    double p = poly_d(t.x, k.p, 5);
+    dd_t P = ddadd2_d2_d_d(k.k2, t.x * p);
+    P = ddadd2_d2_d2_d2(k.k1, ddmul_d2_d2_d2(t, P));
+    P = ddadd2_d2_d2_d2(k.k0, ddmul_d2_d2_d2(t, P));
+    dd_t r = c ? ddadd2_d2_d_d2(1.0, ddmul_d2_d2_d2(t, P)) : ddmul_d2_d2_d(P, s);
     v = r.x + r.y;
+    if (tiny) v *= 0x1p-200;
   } else {
-    v = (o & 1) ? cos_pi_35(s) : sin_pi_35(s);
+    double t = s * s;
+    double p = poly_d(t, k.p, 5);
+    double P = fma(t, fma(t, fma(t, p, k.k2), k.k1.x), k.k0.x);
+    v = c ? fma(t, P, 1.0) : s * P;
   }
   if (o & 2) v = -v;
   /* zero results: sinpi(n) = +-0 with the sign of n, cospi(n + 1/2) = +0 */
@@ -373,32 +370,14 @@ double oracle_cospi_u35_f64(double x) { return sincospi64(x, 1, 0); }
 static const float SPIF_H[4] = { C99_SINPIF_HEAD };
 static const float SPIF_P[4] = { C99_SINPIF_COEFFS };
 static const float CPIF_H[2] = { C99_COSPIF_HEAD };
-static const float CPIF_P[4] = { C99_COSPIF_COEFFS };
+static const float CPIF_P[5] = { C99_COSPIF_COEFFS, 0.0f };
 
-static ff_t sin_pi_ff(float s) {
-  ff_t t = ffmul_f2_f_f(s, s);
-  float p = poly_f(t.x, SPIF_P + 1, 3);
-  ff_t in = ffadd2_f2_f_f(SPIF_P[0], t.x * p);
-  in = ffadd2_f2_f2_f2(ff(SPIF_H[2], SPIF_H[3]), ffmul_f2_f2_f2(t, in));
-  in = ffadd2_f2_f2_f2(ff(SPIF_H[0], SPIF_H[1]), ffmul_f2_f2_f2(t, in));
-  return ffmul_f2_f2_f(in, s);
-}
-static ff_t cos_pi_ff(float s) {
-  ff_t t = ffmul_f2_f_f(s, s);
-  float p = poly_f(t.x, CPIF_P + 1, 3);
-  ff_t in = ffadd2_f2_f_f(CPIF_P[0], t.x * p);
-  in = ffadd2_f2_f2_f2(ff(CPIF_H[0], CPIF_H[1]), ffmul_f2_f2_f2(t, in));
-  return ffadd2_f2_f_f2(1.0f, ffmul_f2_f2_f2(t, in));
-}
-static float sin_pi_35f(float s) {
-  float t = s * s;
-  float p = poly_f(t, SPIF_P + 1, 3);
-  return s * fmaf(t, fmaf(t, fmaf(t, p, SPIF_P[0]), SPIF_H[2]), SPIF_H[0]);
-}
-static float cos_pi_35f(float s) {
-  float t = s * s;
-  float p = poly_f(t, CPIF_P + 1, 3);
-  return fmaf(t, fmaf(t, fmaf(t, p, CPIF_P[0]), CPIF_H[0]), 1.0f);
+typedef struct { ff_t k0, k1; float k2; const float *p; } pikf_t;
+static pikf_t pi_coeffsf(int cosine) {
+  pikf_t c;
+  if (cosine) { c.k0 = ff(CPIF_H[0], CPIF_H[1]); c.k1 = ff(CPIF_P[0], 0.0f); c.k2 = CPIF_P[1]; c.p = CPIF_P + 2; }
+  else { c.k0 = ff(SPIF_H[0], SPIF_H[1]); c.k1 = ff(SPIF_H[2], SPIF_H[3]); c.k2 = SPIF_P[0]; c.p = SPIF_P + 1; }
+  return c;
 }
 static float reduce_pif(float x, int *o) {
   if (fabsf(x) >= 0x1p24f) { *o = 0; return 0.0f; }
@@ -411,15 +390,25 @@ static float sincospi32(float x, int cosine, int u05) {
   if (isnan(x) || isinf(x)) return canon_nanf();
   float s = reduce_pif(x, &o);
   o = (o + cosine) & 3;
+  int c = o & 1;
+  pikf_t k = pi_coeffsf(c);
   float v;
-  if (u05 && !(o & 1) && fabsf(s) < 0x1p-60f) {
-    ff_t r = ffmul_f2_f2_f(ff(SPIF_H[0], SPIF_H[1]), s * 0x1p64f);
-    v = (r.x + r.y) * 0x1p-64f;
-  } else if (u05) {
-    ff_t r = (o & 1) ? cos_pi_ff(s) : sin_pi_ff(s);
+  if (u05) {
+    int tiny = !c && fabsf(s) < 0x1p-100f;
+    if (tiny) s *= 0x1p80f;
+    ff_t t = ffmul_f2_f_f(s, s);
+    float p = poly_f(t.x, k.p, 3);
+    ff_t P = ffadd2_f2_f_f(k.k2, t.x * p);
+    P = ffadd2_f2_f2_f2(k.k1, ffmul_f2_f2_f2(t, P));
+    P = ffadd2_f2_f2_f2(k.k0, ffmul_f2_f2_f2(t, P));
+    ff_t r = c ? ffadd2_f2_f_f2(1.0f, ffmul_f2_f2_f2(t, P)) : ffmul_f2_f2_f(P, s);
     v = r.x + r.y;
+    if (tiny) v *= 0x1p-80f;
   } else {
-    v = (o & 1) ? cos_pi_35f(s) : sin_pi_35f(s);
+    float t = s * s;
+    float p = poly_f(t, k.p, 3);
+    float P = fmaf(t, fmaf(t, fmaf(t, p, k.k2), k.k1.x), k.k0.x);
+    v = c ? fmaf(t, P, 1.0f) : s * P;
   }
   if (o & 2) v = -v;
   if (v == 0) v = cosine ? 0.0f : copysignf(0.0f, x);
