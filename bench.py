@@ -399,6 +399,58 @@ def masked(sleefcu, torch, device, st, sp, n=1 << 26):
     return {"n": n, "workload": "C2 arrays, mask bytes from a seeded stream", "entry_points": out}
 
 
+def c99(sleefcu, torch, device, st, sp, peaks, peak_fp64, n=1 << 26):
+    """The remaining C99 functions, both formats, on the C99 workload (2^26
+    elements per entry point, larger than L2): Gelem/s, HBM bytes and
+    algorithmic pipe operations per element, and the fraction of the
+    roofline (the slower of the HBM bound and the FP-pipe bound)."""
+    from paper_2001_09258_gb300 import inputs as I, opcounts
+    cnt = opcounts.table().get("c99", {})
+    hbm = peaks.get("hbm_gbs")
+    peak_fp32 = pipe_peak(sleefcu, torch, device, "fp32")
+    out = {}
+    host = {}
+
+    def arr(name, operand):
+        # functions of one input class share their arrays (inputs.c99_workload)
+        fn, prec = name.split("_")[0], name.split("_")[-1]
+        cls = (fn if fn in ("hypot", "sqrt") or (fn == "ldexp" and operand == 1) else "x", prec, operand)
+        if cls not in host:
+            host[cls] = torch.from_numpy(I.c99_workload(name, n, operand=operand)).to(device)
+        return host[cls]
+
+    for name in sleefcu.c99_entry_points():
+        kd = sleefcu.C99_FUNCS[name.split("_")[0]]
+        prec = name.split("_")[-1]
+        x = arr(name, 0)
+        y = arr(name, 1) if kd in ("b", "bi") else None
+        o = torch.empty_like(x, dtype=torch.int32) if kd == "ui" else torch.empty_like(x)
+        o2 = None
+        if kd in ("sc", "si"):
+            o2 = torch.empty_like(x, dtype=torch.int32) if kd == "si" else torch.empty_like(x)
+        ms = time_calls(torch, st, lambda: sleefcu.call_c99(name, x, y, out=o, out2=o2, stream=st), reps=5)
+        g = n / (ms * 1e-3) / 1e9
+        nbytes = sum(t.element_size() for t in (x, y, o, o2) if t is not None)
+        ops = cnt.get(name, {}).get("ops", 0.0)
+        rec = {"gelem_s": round(g, 2), "bytes_per_element": nbytes, "hbm_gbs": round(g * nbytes, 1),
+               "ops_per_element": ops}
+        hfrac = g * nbytes / hbm if hbm else None
+        pfrac = g * 1e9 * ops / (peak_fp64 if prec == "f64" else peak_fp32)
+        rec["hbm_frac"] = round(hfrac, 4) if hfrac is not None else None
+        rec["pipe_frac"] = round(pfrac, 4)
+        rec["bound"] = "hbm" if hfrac is not None and hfrac >= pfrac else ("fp64" if prec == "f64" else "fp32")
+        rec["roofline_frac"] = round(max(pfrac, hfrac or 0.0), 4)
+        out[name] = rec
+        del o, o2
+    del host
+    torch.cuda.empty_cache()
+    return {"n": n, "workload": "x uniform [-100, 100] with the specials, y independent; sqrt |x|; hypot "
+                                "log-uniform magnitudes; ldexp exponents uniform in [-60, 60]",
+            "peaks": {"hbm_gbs": hbm, "fp64_pipe_tops": round(peak_fp64 / 1e12, 4),
+                      "fp32_pipe_tops": round(peak_fp32 / 1e12, 3)},
+            "entry_points": out}
+
+
 def batched(sleefcu, torch, device, st, sp, narrays=4096):
     """4096 arrays, lengths log-uniform in [1, 2^20], each assigned an FP64 or
     FP32 entry point uniformly at random: one autotuned persistent launch (plain
@@ -634,6 +686,8 @@ def main():
         ext["fmod_sweep"] = fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64)
         torch.cuda.empty_cache()
         ext["masked"] = masked(sleefcu, torch, device, st, sp)
+        torch.cuda.empty_cache()
+        ext["c99"] = c99(sleefcu, torch, device, st, sp, measured_peaks(), peak_fp64)
     dom = max(names, key=lambda nm: avg[nm])
     hx = host[dom.split("_")[0]]
     steps = None

@@ -577,6 +577,113 @@ sleefcu_status sleefcu_probe_ffma(float *out, int blocks, int iters, sleefcu_str
 sleefcu_status sleefcu_fmod_steps_f64(const double *x, const double *y, double *out, size_t n,
                                       sleefcu_stream stream);
 
+/* ---------------- the remaining C99 real functions ----------------
+ * The library's claim to the whole C99 real set (Section 1): the functions
+ * below complete it beside the families above.  Conventions as at the top of
+ * this file (device pointers owned by the caller, any alignment, n == 0 is a
+ * no-op, null with n > 0 is SLEEFCU_EINVAL, asynchronous on stream), with
+ * int32_t arrays where C99 has an int.
+ *
+ * Exact functions (no accuracy tag; the result is the exact value, or the
+ * correctly rounded one where C99 rounds): fabs, copysign, fmax, fmin, fdim,
+ * trunc, floor, ceil, round (ties away from zero), rint (ties to even),
+ * nextafter, logb, ilogb, ldexp, frexp, modf.  NaN results are the canonical
+ * quiet NaN except for fabs and copysign, which change only the sign bit.
+ * Choices C99 leaves to the implementation:
+ *   fmax(+0, -0) = fmax(-0, +0) = +0 and fmin(+0, -0) = fmin(-0, +0) = -0;
+ *   fmax / fmin with one NaN operand return the other operand;
+ *   ilogb(+-0) = SLEEFCU_FP_ILOGB0, ilogb(NaN) = SLEEFCU_FP_ILOGBNAN,
+ *   ilogb(+-inf) = INT32_MAX; logb(+-0) = -inf, logb(+-inf) = +inf;
+ *   frexp(+-0, +-inf, NaN) returns x (NaN canonical) and stores 0;
+ *   modf(+-inf) = (+-0, +-inf); ldexp rounds once, overflow gives +-inf.
+ *
+ * sqrt_u05 / sqrt_u35: the IEEE square root (correctly rounded; the u35 entry
+ * point runs the same sequence).  sqrt(-0) = -0, sqrt(x < 0) = NaN.
+ * hypot_u05 (<= 0.5 + 2^-20 ULP for normal results, <= 1 ULP for subnormal
+ * ones) and hypot_u35 (<= 1 ULP): the larger magnitude's exponent is taken out
+ * exactly, the sum of squares and its square root in double-double
+ * (float-float) arithmetic (u05) or one fma and a square root (u35).
+ * hypot(+-inf, y) = +inf even for a NaN y; hypot(x, +-0) = |x|.
+ * sinpi_u05 / cospi_u05 (<= 0.501 ULP for normal results, <= 1 ULP for
+ * subnormal ones) and the u35 forms (<= 2 ULP): sin(pi x) and cos(pi x) from
+ * the exact reduction x = q/2 + s, |s| <= 1/4, and one polynomial shape whose
+ * coefficients the quadrant selects.  sinpi(+-n) = +-0 for integers n,
+ * cospi(n + 1/2) = +0, cospi(+-0) = 1, +-inf and NaN give NaN. */
+#define SLEEFCU_FP_ILOGB0 INT32_MIN
+#define SLEEFCU_FP_ILOGBNAN INT32_MAX
+sleefcu_status sleefcu_fabs_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_trunc_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_floor_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_ceil_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_round_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_rint_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_logb_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sqrt_u05_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sqrt_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinpi_u05_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinpi_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cospi_u05_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cospi_u35_f64(const double *x, double *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_copysign_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fmax_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fmin_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fdim_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_nextafter_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_hypot_u05_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_hypot_u35_f64(const double *x, const double *y, double *out, size_t n,
+                               sleefcu_stream stream);
+/* modf: frac[i] = the fractional part (sign of x[i]), ipart[i] = the integral part */
+sleefcu_status sleefcu_modf_f64(const double *x, double *frac, double *ipart, size_t n, sleefcu_stream stream);
+/* ilogb: out[i] = the unbiased exponent of x[i] */
+sleefcu_status sleefcu_ilogb_f64(const double *x, int32_t *out, size_t n, sleefcu_stream stream);
+/* ldexp: out[i] = x[i] 2^e[i], rounded once */
+sleefcu_status sleefcu_ldexp_f64(const double *x, const int32_t *e, double *out, size_t n,
+                               sleefcu_stream stream);
+/* frexp: x[i] = m[i] 2^e[i] with |m[i]| in [1/2, 1) */
+sleefcu_status sleefcu_frexp_f64(const double *x, double *m, int32_t *e, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_fabs_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_trunc_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_floor_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_ceil_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_round_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_rint_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_logb_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sqrt_u05_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sqrt_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinpi_u05_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_sinpi_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cospi_u05_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_cospi_u35_f32(const float *x, float *out, size_t n, sleefcu_stream stream);
+sleefcu_status sleefcu_copysign_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fmax_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fmin_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_fdim_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_nextafter_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_hypot_u05_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+sleefcu_status sleefcu_hypot_u35_f32(const float *x, const float *y, float *out, size_t n,
+                               sleefcu_stream stream);
+/* modf: frac[i] = the fractional part (sign of x[i]), ipart[i] = the integral part */
+sleefcu_status sleefcu_modf_f32(const float *x, float *frac, float *ipart, size_t n, sleefcu_stream stream);
+/* ilogb: out[i] = the unbiased exponent of x[i] */
+sleefcu_status sleefcu_ilogb_f32(const float *x, int32_t *out, size_t n, sleefcu_stream stream);
+/* ldexp: out[i] = x[i] 2^e[i], rounded once */
+sleefcu_status sleefcu_ldexp_f32(const float *x, const int32_t *e, float *out, size_t n,
+                               sleefcu_stream stream);
+/* frexp: x[i] = m[i] 2^e[i] with |m[i]| in [1/2, 1) */
+sleefcu_status sleefcu_frexp_f32(const float *x, float *m, int32_t *e, size_t n, sleefcu_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,21 @@ struct entry {
 #define U16(n) { #n, K_U16, (void *)(uint16_t (*)(uint16_t))oracle_##n }
 const entry REG[] = {
 #include "registry.inc"
+/* the C99 set: the floating-point kinds are counted; the int32 kinds
+ * (ilogb, ldexp, frexp: exponent handling only) are not registered */
+#define XU64(n) U64(n)
+#define XB64(n) B64(n)
+#define XSC64(n) SC64(n)
+#define XU32(n) U32(n)
+#define XB32(n) B32(n)
+#define XSC32(n) SC32(n)
+#define XUI64(n) { #n, 0, NULL }
+#define XBI64(n) { #n, 0, NULL }
+#define XSI64(n) { #n, 0, NULL }
+#define XUI32(n) { #n, 0, NULL }
+#define XBI32(n) { #n, 0, NULL }
+#define XSI32(n) { #n, 0, NULL }
+#include "registry_c99.inc"
   { nullptr, 0, nullptr }
 };
 const entry *find(const char *name) {

@@ -97,8 +97,10 @@ def _binary(name):
     return oracle.kind(name) in (oracle.K_B64, oracle.K_B32)
 
 
-def _entry(t, n):
-    f = t["f64"] if t["f64"]["add"] + t["f64"]["mul"] + t["f64"]["fma"] else t["f32"]
+def _entry(t, n, prec=None):
+    if prec is None:
+        prec = "f64" if t["f64"]["add"] + t["f64"]["mul"] + t["f64"]["fma"] else "f32"
+    f = t[prec]
     ops = sum(f[c] for c in oracle.ALGO_CATS)
     return {"ops": round(ops / n, 4), "div": round(f["div"] / n, 4), "sqrt": round(f["sqrt"] / n, 4), "n": n}
 
@@ -176,9 +178,18 @@ def table():
             h = I.activations("opcount/act", (128, 256), prec).reshape(-1)
             _, t = oracle.count(name, h)
             lowp[name] = _entry(t, h.size)
+    c99 = {}
+    for name in oracle.c99_names():
+        if oracle.kind(name) in (oracle.K_UI64, oracle.K_BI64, oracle.K_SI64,
+                                 oracle.K_UI32, oracle.K_BI32, oracle.K_SI32):
+            continue                     # exponent handling only: no floating-point arithmetic to count
+        x = I.c99_workload(name, SAMPLE // 4)
+        y = I.c99_workload(name, SAMPLE // 4, operand=1) if _binary(name) else None
+        _, t = oracle.count(name, x, y)
+        c99[name] = _entry(t, x.size, name.split("_")[-1])
     return {"unit": "algorithmic operations per element (add/sub, mul, fma, div, sqrt, round each one)",
             "source": "counting build of the oracle (oracle/counting), python -m oracle.counting.gen_opcounts",
-            "f64": f64, "f32": f32, "lowp": lowp}
+            "f64": f64, "f32": f32, "lowp": lowp, "c99": c99}
 
 
 def main():

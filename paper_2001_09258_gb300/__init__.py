@@ -37,6 +37,19 @@ for _fn in ("erf", "tanh", "exp", "log1p"):
     PRECS[_fn] = PRECS[_fn] + ("bf16", "f16")
 ACCS = ("u10", "u35")
 
+# The remaining C99 real functions, both formats (binary64, binary32): kind as
+# above plus "ui" (int32 result: ilogb), "bi" (int32 second operand: ldexp)
+# and "si" (int32 second result: frexp).  Exact functions carry no accuracy
+# tag (sleefcu_<fn>_<prec>); the approximated ones have a 0.5-ULP and a
+# 3.5-ULP form (sleefcu_<fn>_<u05|u35>_<prec>).
+C99_FUNCS = {
+    "fabs": "u", "trunc": "u", "floor": "u", "ceil": "u", "round": "u", "rint": "u", "logb": "u",
+    "copysign": "b", "fmax": "b", "fmin": "b", "fdim": "b", "nextafter": "b",
+    "modf": "sc", "ilogb": "ui", "ldexp": "bi", "frexp": "si",
+    "sqrt": "u", "hypot": "b", "sinpi": "u", "cospi": "u",
+}
+C99_ACCS = {"sqrt": ("u05", "u35"), "hypot": ("u05", "u35"), "sinpi": ("u05", "u35"), "cospi": ("u05", "u35")}
+
 _lib = None
 
 
@@ -51,6 +64,18 @@ def entry_points():
         for prec in PRECS[fn]:
             for acc in ACCS:
                 out.append(f"{fn}_{acc}_{prec}")
+    return out
+
+
+def c99_entry_points():
+    """The entry points of the remaining C99 functions (without the prefix)."""
+    out = []
+    for fn in C99_FUNCS:
+        for prec in ("f64", "f32"):
+            if fn in C99_ACCS:
+                out += [f"{fn}_{a}_{prec}" for a in C99_ACCS[fn]]
+            else:
+                out.append(f"{fn}_{prec}")
     return out
 
 
@@ -83,6 +108,11 @@ def lib():
             f = getattr(L, "sleefcu_" + name)
             f.restype = ctypes.c_int
             nptr = {"u": 2, "b": 3, "sc": 3}[FUNCS[fn]]
+            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+        for name in c99_entry_points():
+            f = getattr(L, "sleefcu_" + name)
+            f.restype = ctypes.c_int
+            nptr = {"u": 2, "b": 3, "sc": 3, "ui": 2, "bi": 3, "si": 3}[C99_FUNCS[name.split("_")[0]]]
             f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
         for name in masked_entry_points():
             fn = name.split("_")[0]
@@ -171,6 +201,36 @@ def call_masked(name, x, mask, y=None, out=None, out2=None, stream=None):
     return (out, out2) if kind == "sc" else out
 
 
+def call_c99(name, x, y=None, out=None, out2=None, stream=None):
+    """Call a C99-set entry point (c99_entry_points()) on CUDA tensors.
+    ldexp takes an int32 tensor y; ilogb returns an int32 tensor; frexp and
+    modf return two tensors (frexp: mantissa and int32 exponent; modf:
+    fractional and integral part)."""
+    import torch
+    kind = C99_FUNCS[name.split("_")[0]]
+    if not x.is_cuda:
+        raise SleefcuError("sleefcu works on CUDA tensors only")
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x, dtype=torch.int32) if kind == "ui" else torch.empty_like(x)
+    if kind in ("sc", "si") and out2 is None:
+        out2 = torch.empty_like(x, dtype=torch.int32) if kind == "si" else torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    sp = ctypes.c_void_p(st.cuda_stream)
+    f = raw(name)
+    if kind in ("u", "ui"):
+        rc = f(x.data_ptr(), out.data_ptr(), x.numel(), sp)
+    elif kind in ("b", "bi"):
+        y = y.contiguous()
+        if y.numel() != x.numel():
+            raise SleefcuError(f"{name}: x and y differ in length")
+        rc = f(x.data_ptr(), y.data_ptr(), out.data_ptr(), x.numel(), sp)
+    else:
+        rc = f(x.data_ptr(), out.data_ptr(), out2.data_ptr(), x.numel(), sp)
+    _check(rc, name)
+    return (out, out2) if kind in ("sc", "si") else out
+
+
 def _prec_of(x):
     import torch
     return {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16",
@@ -192,6 +252,20 @@ def _mk(fn):
 
 for _fn in FUNCS:
     globals()[_fn] = _mk(_fn)
+
+
+def _mk_c99(fn):
+    def f(x, y=None, ulp=5, out=None, out2=None):
+        prec = _prec_of(x)
+        name = f"{fn}_u{ulp:02d}_{prec}" if fn in C99_ACCS else f"{fn}_{prec}"
+        return call_c99(name, x, y, out=out, out2=out2)
+    f.__name__ = fn
+    f.__doc__ = f"Elementwise {fn} via sleefcu_{fn}_<prec> (ulp=5 or 35 where the function has accuracy forms)."
+    return f
+
+
+for _fn in C99_FUNCS:
+    globals()[_fn] = _mk_c99(_fn)
 
 
 # ---------------- batched mixed launch ----------------

@@ -225,6 +225,29 @@ def fmod_sweep(r, n, key="sweep"):
     return u * (r * d), d
 
 
+def c99_workload(name, n, key="c99", operand=0):
+    """Inputs of the remaining C99 functions: x uniform in [-100, 100] with
+    the 64 specials mixed in at the front (binary32 values rounded from
+    binary64), the second operand independent the same way; sqrt takes |x|;
+    hypot takes magnitudes log-uniform over [1e-300, 1e300] ([1e-35, 1e35]
+    in binary32); ldexp's exponents are int32 uniform in [-60, 60]."""
+    parts = name.split("_")
+    fn, prec = parts[0], parts[-1]
+    dt = np.float64 if prec == "f64" else np.float32
+    cls = fn if fn in ("hypot", "ldexp") and operand == 1 or fn == "hypot" else "x"
+    k = f"{key}/{cls}/{prec}/{operand}"          # the same arrays for every function of a class
+    if fn == "ldexp" and operand == 1:
+        return (raw(k, n) % np.uint64(121)).astype(np.int64).astype(np.int32) - 60
+    if fn == "hypot":
+        span = (1e-300, 1e300) if prec == "f64" else (1e-35, 1e35)
+        return loguniform(k, n, *span, dtype=dt)
+    x = uniform(k, n, -100.0, 100.0, dtype=dt)
+    m = min(n, SPECIALS_F64.size)
+    with np.errstate(over="ignore"):
+        x[:m] = SPECIALS_F64[:m].astype(dt)
+    return np.abs(x) if fn == "sqrt" else x
+
+
 def to_bf16_bits(x32):
     """binary32 -> bf16 bit patterns, round-to-nearest-even (input preparation)."""
     b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)

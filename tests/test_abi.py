@@ -30,10 +30,28 @@ def test_binding_covers_header():
     names = set(declared())
     for e in sleefcu.entry_points():
         assert "sleefcu_" + e in names, e
-    fn_decl = {n for n in names if re.match(r"sleefcu_\w+_u(10|35)_(f64|f32|bf16|f16)$", n)}
+    c99 = {"sleefcu_" + e for e in sleefcu.c99_entry_points()}
+    fn_decl = {n for n in names if re.match(r"sleefcu_\w+_u(10|35)_(f64|f32|bf16|f16)$", n)} - c99
     assert fn_decl == {"sleefcu_" + e for e in sleefcu.entry_points()}
     masked = {n for n in names if n.endswith("_masked")}
     assert masked == {"sleefcu_" + e + "_masked" for e in sleefcu.masked_entry_points()}
+    assert c99 <= names
+    other = {n for n in names if re.match(r"sleefcu_[a-z0-9]+(_u(05|35))?_(f64|f32)$", n)} - fn_decl
+    assert other == c99
+
+
+@pytest.mark.parametrize("name", sleefcu.c99_entry_points())
+def test_c99_n_zero_and_null_pointers(name):
+    f = sleefcu.raw(name)
+    nptr = len(f.argtypes) - 2
+    assert f(*([None] * nptr), 0, None) == 0
+    assert f(*([None] * nptr), 7, None) == -1
+    assert name in sleefcu.last_error()
+
+
+def test_c99_set_matches_oracle_names():
+    import oracle
+    assert sorted(sleefcu.c99_entry_points()) == sorted(oracle.c99_names())
 
 
 def test_version_and_error_text():
