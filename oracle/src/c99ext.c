@@ -6,8 +6,8 @@
  * frexp and modf.  Each is written out from its definition in C99 (7.12 and
  * Annex F) on the fields of the IEEE encoding (sign, biased exponent,
  * significand), with integer rounding where a result is rounded (rint,
- * round, ldexp into the subnormal range).  NaN results are the canonical
- * quiet NaN, except for fabs and copysign, which only touch the sign bit.
+ * round, ldexp into the subnormal range).  Every NaN result is the canonical
+ * quiet NaN, fabs and copysign included (as everywhere in the library).
  * Choices C99 leaves open: fmax(+0, -0) = +0 and fmin(+0, -0) = -0;
  * ilogb(0) = INT_MIN, ilogb(NaN) = INT_MAX; frexp(inf or NaN) stores 0.
  *
@@ -129,9 +129,9 @@ static int32_t ilogb_b(uint64_t b, fmt_t f) {
 }
 
 /* ---------------- binary64 exact functions ---------------- */
-double oracle_fabs_f64(double x) { return d64(b64(x) & ~sgn_bit(F64)); }
+double oracle_fabs_f64(double x) { return canon(d64(b64(x) & ~sgn_bit(F64))); }
 double oracle_copysign_f64(double x, double y) {
-  return d64((b64(x) & ~sgn_bit(F64)) | (b64(y) & sgn_bit(F64)));
+  return canon(d64((b64(x) & ~sgn_bit(F64)) | (b64(y) & sgn_bit(F64))));
 }
 double oracle_trunc_f64(double x) { return canon(d64(trunc_b(b64(x), F64))); }
 double oracle_floor_f64(double x) {
@@ -188,9 +188,9 @@ double oracle_nextafter_f64(double x, double y) {
 }
 
 /* ---------------- binary32 exact functions ---------------- */
-float oracle_fabs_f32(float x) { return f32(b32(x) & ~sgn_bit(F32)); }
+float oracle_fabs_f32(float x) { return canonf(f32(b32(x) & ~sgn_bit(F32))); }
 float oracle_copysign_f32(float x, float y) {
-  return f32((b32(x) & ~sgn_bit(F32)) | (b32(y) & sgn_bit(F32)));
+  return canonf(f32((b32(x) & ~sgn_bit(F32)) | (b32(y) & sgn_bit(F32))));
 }
 float oracle_trunc_f32(float x) { return canonf(f32(trunc_b(b32(x), F32))); }
 float oracle_floor_f32(float x) {
