@@ -587,8 +587,8 @@ sleefcu_status sleefcu_fmod_steps_f64(const double *x, const double *y, double *
  * Exact functions (no accuracy tag; the result is the exact value, or the
  * correctly rounded one where C99 rounds): fabs, copysign, fmax, fmin, fdim,
  * trunc, floor, ceil, round (ties away from zero), rint (ties to even),
- * nextafter, logb, ilogb, ldexp, frexp, modf.  NaN results are the canonical
- * quiet NaN except for fabs and copysign, which change only the sign bit.
+ * nextafter, logb, ilogb, ldexp, frexp, modf.  Every NaN result is the
+ * canonical quiet NaN (fabs and copysign included).
  * Choices C99 leaves to the implementation:
  *   fmax(+0, -0) = fmax(-0, +0) = +0 and fmin(+0, -0) = fmin(-0, +0) = -0;
  *   fmax / fmin with one NaN operand return the other operand;

@@ -2,13 +2,14 @@
 //
 // Exact functions (C99 7.12 and Annex F): fabs, copysign, fmax, fmin, fdim,
 // trunc, floor, ceil, round, rint, nextafter, logb, ilogb, ldexp, frexp, modf.
-// The roundings to an integer are the hardware's IEEE roundToIntegral
-// operations; everything that reads or builds an exponent (logb, ilogb,
+// binary64 trunc, floor, ceil, rint, round and modf round on the integer
+// pipe (binary32 uses the hardware's roundToIntegral operations, which cost
+// little there); everything that reads or builds an exponent (logb, ilogb,
 // ldexp, frexp) and every comparison runs on the integer pipe.  ldexp splits
 // x into m 2^e with m in [1, 2) and either writes the exponent field (normal
 // results) or rounds m 2^(e + n + 1074) to an integer once (subnormal
-// results).  NaN results are the canonical quiet NaN, except for fabs and
-// copysign, which only touch the sign bit.  Choices C99 leaves open:
+// results).  Every NaN result is the canonical quiet NaN (fabs and copysign
+// included).  Choices C99 leaves open:
 // fmax(+0, -0) = +0, fmin(+0, -0) = -0, ilogb(0) = INT_MIN, ilogb(NaN) =
 // INT_MAX, frexp(inf or NaN) stores 0.
 //
@@ -36,6 +37,22 @@ namespace c99 {
 
 constexpr uint64_t SIGN64 = 0x8000000000000000ull, FRAC64 = 0x000FFFFFFFFFFFFFull;
 constexpr uint32_t SIGN32 = 0x80000000u, FRAC32 = 0x007FFFFFu;
+
+// The bits of a double or float through an opaque register move: the
+// compiler may turn a NaN or infinity test written on the bits back into a
+// floating-point comparison, which takes an FP64-pipe slot on this chip.
+__device__ __forceinline__ uint64_t ib(double d) {
+  uint64_t r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(d));
+  return r;
+}
+__device__ __forceinline__ uint32_t ibf(float f) {
+  uint32_t r;
+  asm("mov.b32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+__device__ __forceinline__ double canon_i(double y) { return (ib(y) & ABS64) > EXP64 ? from_bits(QNAN64) : y; }
+__device__ __forceinline__ float canonf_i(float y) { return (ibf(y) & ABS32) > EXP32 ? from_fbits(QNAN32) : y; }
 
 // ---------------- exponent handling on the integer pipe ----------------
 // finite non-zero |x| (its bits ab) = m 2^e, m in [1, 2)
@@ -66,8 +83,8 @@ __device__ __forceinline__ float pow2_32(int k) {
 }
 
 __device__ __forceinline__ double ldexp64(double x, int n) {
-  uint64_t b = bits(x), ab = b & ABS64, sg = b & SIGN64;
-  if (ab == 0 || ab >= EXP64) return canon(x);
+  uint64_t b = ib(x), ab = b & ABS64, sg = b & SIGN64;
+  if (ab == 0 || ab >= EXP64) return canon_i(x);
   n = max(min(n, 4000), -4000);
   int k = expo64(ab) + n;
   uint64_t mb = mant64(ab);
@@ -76,11 +93,11 @@ __device__ __forceinline__ double ldexp64(double x, int n) {
   int kk = k + 1074;                                        // subnormal: one rounding on the 2^-1074 grid
   if (kk < -1) return from_bits(sg);
   double r = __dmul_rn(rint(__dmul_rn(from_bits(mb), pow2_64(kk))), 0x1p-1074);
-  return from_bits(sg | bits(r));
+  return from_bits(sg | ib(r));
 }
 __device__ __forceinline__ float ldexp32(float x, int n) {
-  uint32_t b = fbits(x), ab = b & ABS32, sg = b & SIGN32;
-  if (ab == 0 || ab >= EXP32) return canonf(x);
+  uint32_t b = ibf(x), ab = b & ABS32, sg = b & SIGN32;
+  if (ab == 0 || ab >= EXP32) return canonf_i(x);
   n = max(min(n, 1000), -1000);
   int k = expo32(ab) + n;
   uint32_t mb = mant32(ab);
@@ -89,61 +106,99 @@ __device__ __forceinline__ float ldexp32(float x, int n) {
   int kk = k + 149;
   if (kk < -1) return from_fbits(sg);
   float r = __fmul_rn(rintf(__fmul_rn(from_fbits(mb), pow2_32(kk))), 0x1p-149f);
-  return from_fbits(sg | fbits(r));
+  return from_fbits(sg | ibf(r));
+}
+
+// binary64 roundings to an integer on the integer pipe.  b: the bits of x.
+// trunc clears the fraction bits; rint and round add half an integer unit
+// (less one ulp plus the quotient's low bit for ties to even) to the
+// significand and shift; the integer q <= 2^53 is written back exactly.
+__device__ __forceinline__ uint64_t trunc_b64(uint64_t b) {
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e >= 52) return b;                                    // integers, infinities, NaNs
+  if (e < 0) return b & SIGN64;
+  return b & ~(FRAC64 >> e);
+}
+__device__ __forceinline__ uint64_t from_uint64(uint64_t q) {   // q <= 2^53, exact
+  if (q == 0) return 0;
+  int p = 63 - __clzll((long long)q);
+  return ((uint64_t)(p + 1023) << 52) | ((q << (52 - p)) & FRAC64);
+}
+template <bool EVEN>
+__device__ __forceinline__ uint64_t round_b64(uint64_t b) {
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  uint64_t sg = b & SIGN64;
+  if (e >= 52) return b;
+  if (e < -1) return sg;                                    // |x| < 1/2
+  int s = 52 - e;                                           // 1 .. 53
+  uint64_t M = (b & FRAC64) | (1ull << 52), half = 1ull << (s - 1);
+  uint64_t add = EVEN ? half - 1 + ((M >> s) & 1) : half;
+  return sg | from_uint64((M + add) >> s);
+}
+// an int32 as a double, exactly, on the integer pipe
+__device__ __forceinline__ double from_int32(int v) {
+  uint64_t a = (uint64_t)(v < 0 ? -(long long)v : v);
+  return from_bits(((uint64_t)(v < 0) << 63) | from_uint64(a));
 }
 
 // ---------------- functors: one per function, both formats ----------------
 struct Fabs {
-  __device__ double operator()(double x) const { return from_bits(bits(x) & ABS64); }
-  __device__ float operator()(float x) const { return from_fbits(fbits(x) & ABS32); }
+  __device__ double operator()(double x) const { return canon_i(from_bits(ib(x) & ABS64)); }
+  __device__ float operator()(float x) const { return canonf_i(from_fbits(ibf(x) & ABS32)); }
 };
 struct Copysign {
   __device__ double operator()(double x, double y) const {
-    return from_bits((bits(x) & ABS64) | (bits(y) & SIGN64));
+    return canon_i(from_bits((ib(x) & ABS64) | (ib(y) & SIGN64)));
   }
   __device__ float operator()(float x, float y) const {
-    return from_fbits((fbits(x) & ABS32) | (fbits(y) & SIGN32));
+    return canonf_i(from_fbits((ibf(x) & ABS32) | (ibf(y) & SIGN32)));
   }
 };
 struct Trunc {
-  __device__ double operator()(double x) const { return canon(trunc(x)); }
-  __device__ float operator()(float x) const { return canonf(truncf(x)); }
+  __device__ double operator()(double x) const { return canon_i(from_bits(trunc_b64(ib(x)))); }
+  __device__ float operator()(float x) const { return canonf_i(truncf(x)); }
 };
+// floor / ceil: trunc on the bits, one step only where the fraction was not
+// zero and the sign points that way (|t| < 2^52: exact)
 struct Floor {
-  __device__ double operator()(double x) const { return canon(floor(x)); }
-  __device__ float operator()(float x) const { return canonf(floorf(x)); }
+  __device__ double operator()(double x) const {
+    uint64_t b = ib(x), t = trunc_b64(b);
+    double r = (t != b && (b >> 63)) ? __dsub_rn(from_bits(t), 1.0) : from_bits(t);
+    return canon_i(r);
+  }
+  __device__ float operator()(float x) const { return canonf_i(floorf(x)); }
 };
 struct Ceil {
-  __device__ double operator()(double x) const { return canon(ceil(x)); }
-  __device__ float operator()(float x) const { return canonf(ceilf(x)); }
+  __device__ double operator()(double x) const {
+    uint64_t b = ib(x), t = trunc_b64(b);
+    double r = (t != b && !(b >> 63)) ? __dadd_rn(from_bits(t), 1.0) : from_bits(t);
+    return canon_i(r);
+  }
+  __device__ float operator()(float x) const { return canonf_i(ceilf(x)); }
 };
 struct Rint {
-  __device__ double operator()(double x) const { return canon(rint(x)); }
-  __device__ float operator()(float x) const { return canonf(rintf(x)); }
+  __device__ double operator()(double x) const { return canon_i(from_bits(round_b64<true>(ib(x)))); }
+  __device__ float operator()(float x) const { return canonf_i(rintf(x)); }
 };
-// ties away from zero: t = trunc(x), x - t exact, one step away from zero
-// when |x - t| >= 1/2 (only for |x| < 2^52, where t +- 1 is exact)
+// ties away from zero.  binary32: t = trunc(x), x - t exact, one step away
+// from zero when |x - t| >= 1/2 (only for |x| < 2^23, where t +- 1 is exact)
 struct Round {
-  __device__ double operator()(double x) const {
-    double t = trunc(x), d = __dsub_rn(x, t);
-    bool up = (bits(d) & ABS64) >= 0x3FE0000000000000ull && (bits(d) & ABS64) <= EXP64;
-    return canon(up ? __dadd_rn(t, from_bits((bits(x) & SIGN64) | 0x3FF0000000000000ull)) : t);
-  }
+  __device__ double operator()(double x) const { return canon_i(from_bits(round_b64<false>(ib(x)))); }
   __device__ float operator()(float x) const {
     float t = truncf(x), d = __fsub_rn(x, t);
-    bool up = (fbits(d) & ABS32) >= 0x3F000000u && (fbits(d) & ABS32) <= EXP32;
-    return canonf(up ? __fadd_rn(t, from_fbits((fbits(x) & SIGN32) | 0x3F800000u)) : t);
+    bool up = (ibf(d) & ABS32) >= 0x3F000000u && (ibf(d) & ABS32) <= EXP32;
+    return canonf_i(up ? __fadd_rn(t, from_fbits((ibf(x) & SIGN32) | 0x3F800000u)) : t);
   }
 };
 struct Logb {
   __device__ double operator()(double x) const {
-    uint64_t ab = bits(x) & ABS64;
+    uint64_t ab = ib(x) & ABS64;
     if (ab == 0) return from_bits(SIGN64 | EXP64);
     if (ab >= EXP64) return ab == EXP64 ? from_bits(EXP64) : from_bits(QNAN64);
-    return (double)expo64(ab);
+    return from_int32(expo64(ab));
   }
   __device__ float operator()(float x) const {
-    uint32_t ab = fbits(x) & ABS32;
+    uint32_t ab = ibf(x) & ABS32;
     if (ab == 0) return from_fbits(SIGN32 | EXP32);
     if (ab >= EXP32) return ab == EXP32 ? from_fbits(EXP32) : from_fbits(QNAN32);
     return (float)expo32(ab);
@@ -151,11 +206,11 @@ struct Logb {
 };
 struct Ilogb {
   __device__ int32_t operator()(double x) const {
-    uint64_t ab = bits(x) & ABS64;
+    uint64_t ab = ib(x) & ABS64;
     return ab == 0 ? INT_MIN : (ab >= EXP64 ? INT_MAX : expo64(ab));
   }
   __device__ int32_t operator()(float x) const {
-    uint32_t ab = fbits(x) & ABS32;
+    uint32_t ab = ibf(x) & ABS32;
     return ab == 0 ? INT_MIN : (ab >= EXP32 ? INT_MAX : expo32(ab));
   }
 };
@@ -165,16 +220,16 @@ struct Ldexp {
 };
 struct Frexp {
   __device__ double operator()(double x, int32_t &k) const {
-    uint64_t b = bits(x), ab = b & ABS64;
+    uint64_t b = ib(x), ab = b & ABS64;
     k = 0;
-    if (ab == 0 || ab >= EXP64) return canon(x);
+    if (ab == 0 || ab >= EXP64) return canon_i(x);
     k = expo64(ab) + 1;
     return from_bits((b & SIGN64) | (mant64(ab) - (1ull << 52)));   // m / 2 in [1/2, 1)
   }
   __device__ float operator()(float x, int32_t &k) const {
-    uint32_t b = fbits(x), ab = b & ABS32;
+    uint32_t b = ibf(x), ab = b & ABS32;
     k = 0;
-    if (ab == 0 || ab >= EXP32) return canonf(x);
+    if (ab == 0 || ab >= EXP32) return canonf_i(x);
     k = expo32(ab) + 1;
     return from_fbits((b & SIGN32) | (mant32(ab) - (1u << 23)));
   }
@@ -183,72 +238,76 @@ struct Frexp {
 // integral part
 struct Modf {
   __device__ void operator()(double x, double &fr, double &ip) const {
-    uint64_t b = bits(x);
-    double t = trunc(x);
+    uint64_t b = ib(x);
+    double t = from_bits(trunc_b64(b));
     double d = (b & ABS64) == EXP64 ? 0.0 : __dsub_rn(x, t);
-    fr = canon(from_bits((bits(d) & ABS64) | (b & SIGN64)));
-    ip = canon(t);
-    if (is_nan_b(b)) fr = from_bits(QNAN64);
+    fr = from_bits((ib(d) & ABS64) | (b & SIGN64));
+    ip = t;
+    if ((b & ABS64) > EXP64) fr = ip = from_bits(QNAN64);
   }
   __device__ void dual(float x, float &fr, float &ip) const {
-    uint32_t b = fbits(x);
+    uint32_t b = ibf(x);
     float t = truncf(x);
     float d = (b & ABS32) == EXP32 ? 0.0f : __fsub_rn(x, t);
-    fr = canonf(from_fbits((fbits(d) & ABS32) | (b & SIGN32)));
-    ip = canonf(t);
+    fr = canonf_i(from_fbits((ibf(d) & ABS32) | (b & SIGN32)));
+    ip = canonf_i(t);
     if ((b & ABS32) > EXP32) fr = from_fbits(QNAN32);
   }
 };
+__device__ __forceinline__ long long okey_i(double d) {
+  long long b = (long long)ib(d);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
 __device__ __forceinline__ int okey32(float f) {
-  int b = (int)fbits(f);
+  int b = (int)ibf(f);
   return b ^ ((b >> 31) & 0x7FFFFFFF);
 }
 struct Fmax {
   __device__ double operator()(double x, double y) const {
-    if (is_nan_b(bits(x))) return canon(y);
-    if (is_nan_b(bits(y))) return x;
-    return okey(x) >= okey(y) ? x : y;                 // -0 orders below +0
+    if (is_nan_b(ib(x))) return canon_i(y);
+    if (is_nan_b(ib(y))) return x;
+    return okey_i(x) >= okey_i(y) ? x : y;                 // -0 orders below +0
   }
   __device__ float operator()(float x, float y) const {
-    if ((fbits(x) & ABS32) > EXP32) return canonf(y);
-    if ((fbits(y) & ABS32) > EXP32) return x;
+    if ((ibf(x) & ABS32) > EXP32) return canonf_i(y);
+    if ((ibf(y) & ABS32) > EXP32) return x;
     return okey32(x) >= okey32(y) ? x : y;
   }
 };
 struct Fmin {
   __device__ double operator()(double x, double y) const {
-    if (is_nan_b(bits(x))) return canon(y);
-    if (is_nan_b(bits(y))) return x;
-    return okey(x) <= okey(y) ? x : y;
+    if (is_nan_b(ib(x))) return canon_i(y);
+    if (is_nan_b(ib(y))) return x;
+    return okey_i(x) <= okey_i(y) ? x : y;
   }
   __device__ float operator()(float x, float y) const {
-    if ((fbits(x) & ABS32) > EXP32) return canonf(y);
-    if ((fbits(y) & ABS32) > EXP32) return x;
+    if ((ibf(x) & ABS32) > EXP32) return canonf_i(y);
+    if ((ibf(y) & ABS32) > EXP32) return x;
     return okey32(x) <= okey32(y) ? x : y;
   }
 };
 // x > y ? x - y : +0 (for x = +0, y = -0 both branches give +0)
 struct Fdim {
   __device__ double operator()(double x, double y) const {
-    if (is_nan_b(bits(x)) || is_nan_b(bits(y))) return from_bits(QNAN64);
-    return okey(x) > okey(y) ? __dsub_rn(x, y) : 0.0;
+    if (is_nan_b(ib(x)) || is_nan_b(ib(y))) return from_bits(QNAN64);
+    return okey_i(x) > okey_i(y) ? __dsub_rn(x, y) : 0.0;
   }
   __device__ float operator()(float x, float y) const {
-    if ((fbits(x) & ABS32) > EXP32 || (fbits(y) & ABS32) > EXP32) return from_fbits(QNAN32);
+    if ((ibf(x) & ABS32) > EXP32 || (ibf(y) & ABS32) > EXP32) return from_fbits(QNAN32);
     return okey32(x) > okey32(y) ? __fsub_rn(x, y) : 0.0f;
   }
 };
 struct Nextafter {
   __device__ double operator()(double x, double y) const {
-    uint64_t bx = bits(x), by = bits(y);
+    uint64_t bx = ib(x), by = ib(y);
     if (is_nan_b(bx) || is_nan_b(by)) return from_bits(QNAN64);
     if (bx == by || ((bx | by) & ABS64) == 0) return y;
     if ((bx & ABS64) == 0) return from_bits((by & SIGN64) | 1);
-    bool away = (okey(y) > okey(x)) == !(bx >> 63);     // the magnitude grows
+    bool away = (okey_i(y) > okey_i(x)) == !(bx >> 63);     // the magnitude grows
     return from_bits(away ? bx + 1 : bx - 1);
   }
   __device__ float operator()(float x, float y) const {
-    uint32_t bx = fbits(x), by = fbits(y);
+    uint32_t bx = ibf(x), by = ibf(y);
     if ((bx & ABS32) > EXP32 || (by & ABS32) > EXP32) return from_fbits(QNAN32);
     if (bx == by || ((bx | by) & ABS32) == 0) return y;
     if ((bx & ABS32) == 0) return from_fbits((by & SIGN32) | 1);
@@ -257,15 +316,15 @@ struct Nextafter {
   }
 };
 struct Sqrt {
-  __device__ double operator()(double x) const { return canon(__dsqrt_rn(x)); }
-  __device__ float operator()(float x) const { return canonf(__fsqrt_rn(x)); }
+  __device__ double operator()(double x) const { return canon_i(__dsqrt_rn(x)); }
+  __device__ float operator()(float x) const { return canonf_i(__fsqrt_rn(x)); }
 };
 
 // ---------------- hypot ----------------
 template <bool U05>
 struct Hypot {
   __device__ double operator()(double x, double y) const {
-    uint64_t ax = bits(x) & ABS64, ay = bits(y) & ABS64;
+    uint64_t ax = ib(x) & ABS64, ay = ib(y) & ABS64;
     if (ax == EXP64 || ay == EXP64) return from_bits(EXP64);   // an infinity wins over a NaN
     if (ax > EXP64 || ay > EXP64) return from_bits(QNAN64);
     uint64_t ab = ax > ay ? ax : ay, bb = ax > ay ? ay : ax;
@@ -287,7 +346,7 @@ struct Hypot {
     return __dmul_rn(r, pow2_64(e));                           // one rounding at most
   }
   __device__ float operator()(float x, float y) const {
-    uint32_t ax = fbits(x) & ABS32, ay = fbits(y) & ABS32;
+    uint32_t ax = ibf(x) & ABS32, ay = ibf(y) & ABS32;
     if (ax == EXP32 || ay == EXP32) return from_fbits(EXP32);
     if (ax > EXP32 || ay > EXP32) return from_fbits(QNAN32);
     uint32_t ab = ax > ay ? ax : ay, bb = ax > ay ? ay : ax;
@@ -336,7 +395,7 @@ __device__ constexpr float CPf[3] = {0x1.e1474ap-3f, -0x1.76f7fcp-6f, 0.0f};
 template <bool COS, bool U05>
 struct Sincospi {
   __device__ double operator()(double x) const {
-    uint64_t b = bits(x), ab = b & ABS64;
+    uint64_t b = ib(x), ab = b & ABS64;
     if (ab >= EXP64) return from_bits(QNAN64);
     double s = 0.0;
     int o = 0;
@@ -353,7 +412,7 @@ struct Sincospi {
     double k2 = c ? CK2 : SK2;
     double v;
     if (U05) {
-      bool tiny = !c && (bits(s) & ABS64) < 0x20B0000000000000ull;   // |s| < 2^-500
+      bool tiny = !c && (ib(s) & ABS64) < 0x20B0000000000000ull;   // |s| < 2^-500
       if (tiny) s = __dmul_rn(s, 0x1p200);
       d2 t = mul_dd(s, s);
       double p = poly(t.x, pc);
@@ -371,11 +430,11 @@ struct Sincospi {
     }
     v = neg_if(v, o & 2);
     // zero results: sinpi(n) = +-0 with the sign of n, cospi(n + 1/2) = +0
-    if ((bits(v) & ABS64) == 0) v = COS ? 0.0 : from_bits(b & SIGN64);
+    if ((ib(v) & ABS64) == 0) v = COS ? 0.0 : from_bits(b & SIGN64);
     return v;
   }
   __device__ float operator()(float x) const {
-    uint32_t b = fbits(x), ab = b & ABS32;
+    uint32_t b = ibf(x), ab = b & ABS32;
     if (ab >= EXP32) return from_fbits(QNAN32);
     float s = 0.0f;
     int o = 0;
@@ -392,7 +451,7 @@ struct Sincospi {
     float k2 = c ? CK2f : SK2f;
     float v;
     if (U05) {
-      bool tiny = !c && (fbits(s) & ABS32) < 0x0D800000u;     // |s| < 2^-100
+      bool tiny = !c && (ibf(s) & ABS32) < 0x0D800000u;     // |s| < 2^-100
       if (tiny) s = __fmul_rn(s, 0x1p80f);
       f2 t = mul_ff(s, s);
       float p = polyf(t.x, pc);
@@ -409,7 +468,7 @@ struct Sincospi {
       v = c ? __fmaf_rn(t, P, 1.0f) : __fmul_rn(s, P);
     }
     v = negf_if(v, o & 2);
-    if ((fbits(v) & ABS32) == 0) v = COS ? 0.0f : from_fbits(b & SIGN32);
+    if ((ibf(v) & ABS32) == 0) v = COS ? 0.0f : from_fbits(b & SIGN32);
     return v;
   }
 };
