@@ -10,7 +10,14 @@
 namespace sleefcu {
 
 // ---------------- bit helpers (integer pipe) ----------------
-__device__ __forceinline__ uint64_t bits(double d) { return (uint64_t)__double_as_longlong(d); }
+// The bits of a double through an opaque register move: the compiler would
+// otherwise turn NaN, infinity and sign tests written on the bits back into
+// FP64 comparisons, and on GB300 each takes an FP64-pipe slot like an FMA.
+__device__ __forceinline__ uint64_t bits(double d) {
+  uint64_t r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(d));
+  return r;
+}
 __device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ uint32_t fbits(float f) { return (uint32_t)__float_as_uint(f); }
 __device__ __forceinline__ float from_fbits(uint32_t b) { return __uint_as_float(b); }
