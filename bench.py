@@ -161,16 +161,10 @@ def launch(sleefcu, name, ins, outs, stream_ptr):
 E2E_CHUNK = 1 << 24          # elements per host-pipeline chunk of the end-to-end step
 
 
-def measured_pipe_counts():
-    """FP64 instructions per element measured by ncu for each FP64 entry point
-    (profiles/fp64_inst.json), or None when the kernel sources have changed
-    since the capture (the file records a hash of the CUDA sources)."""
+def csrc_sha():
+    """hash of the CUDA sources (every file of csrc/): a stored ncu figure is
+    used only while the kernels it was taken on are unchanged"""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fp64_inst.json")
-    try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
-        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2001_09258_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
@@ -178,7 +172,19 @@ def measured_pipe_counts():
         if os.path.isfile(fp):
             h.update(f.encode())
             h.update(open(fp, "rb").read())
-    return rec.get("per_entry_point") if h.hexdigest()[:16] == rec.get("csrc_sha") else None
+    return h.hexdigest()[:16]
+
+
+def measured_pipe_counts():
+    """FP64 instructions per element measured by ncu for each FP64 entry point
+    (profiles/fp64_inst.json), or None when the kernel sources have changed
+    since the capture (the file records a hash of the CUDA sources)."""
+    path = os.path.join(ROOT, "profiles", "fp64_inst.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    return rec.get("per_entry_point") if csrc_sha() == rec.get("csrc_sha") else None
 
 
 def pipe_peak(sleefcu, torch, device, pipe="fp64"):
@@ -716,11 +722,8 @@ def main():
     if os.path.exists(prof):
         try:
             tr = json.load(open(prof)).get(dom)
-            if tr:
-                import hashlib
-                src = open(os.path.join(ROOT, "paper_2001_09258_gb300", "csrc", tr["source"]), "rb").read()
-                if hashlib.sha256(src).hexdigest()[:16] == tr["source_sha"]:
-                    roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
+            if tr and tr.get("csrc_sha") == csrc_sha():        # null once any kernel source changed
+                roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
         except (OSError, ValueError, KeyError):
             pass
     cpu = None
