@@ -53,6 +53,28 @@ def test_counting_build_computes_the_oracle(name):
     assert oracle.algo_ops(tally, "f64") + oracle.algo_ops(tally, "f32") > 0
 
 
+@pytest.mark.parametrize("name", [n for n in oracle.c99_names()
+                                  if oracle.kind(n) in (oracle.K_U64, oracle.K_B64, oracle.K_SC64,
+                                                        oracle.K_U32, oracle.K_B32, oracle.K_SC32)])
+def test_counting_build_computes_the_c99_oracle(name):
+    """the remaining C99 functions: the counting build gives the plain
+    build's bits on their workload and on random bit patterns"""
+    prec = name.split("_")[-1]
+    n = 4096
+    r = I.raw(f"opc99/{name}", n)
+    rb = r.view(np.float64) if prec == "f64" else (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    x = np.concatenate([I.c99_workload(name, n), rb])
+    y = None
+    if oracle.kind(name) in (oracle.K_B64, oracle.K_B32):
+        y = np.concatenate([I.c99_workload(name, n, operand=1), rb[::-1].copy()])
+    want = oracle.apply(name, x, y, nthreads=1)
+    got, _ = oracle.count(name, x, y)
+    ws = want if isinstance(want, tuple) else (want,)
+    gs = got if isinstance(got, tuple) else (got,)
+    for w, g in zip(ws, gs):
+        assert w.tobytes() == g.tobytes(), name
+
+
 def test_payne_hanek_counts_match_the_paper_table():
     """Section 5.8, table of FP operators in Payne-Hanek implementations:
     36 add/sub, 5 mul, 11 FMA per reduction.  The paper's 8 rounds are 2 per
