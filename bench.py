@@ -44,6 +44,9 @@ def parse():
                    help="skip the FP32 / bf16 / f16 family measurements")
     p.add_argument("--n32", type=int, default=1 << 28, help="elements per FP32 entry point")
     p.add_argument("--n5", type=int, default=1 << 28, help="elements of the large-argument stress")
+    p.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
+                   help="file for the per-entry-point rows and the families' tables (stdout gets "
+                        "one compact line)")
     return p.parse_args()
 
 
@@ -188,12 +191,15 @@ def measured_pipe_counts():
 
 
 def pipe_peak(sleefcu, torch, device, pipe="fp64"):
-    """Measured FMA-pipe throughput (ops/s) with the library's probe kernels
-    (8 independent FMA chains per thread, 8 blocks of 256 per SM)."""
+    """Measured FMA-pipe throughput (ops/s) with the bench's probe kernels
+    (measure/probe.cu: 8 independent FMA chains per thread, 8 blocks of 256
+    per SM)."""
+    import measure
     props = torch.cuda.get_device_properties(device)
     blocks = props.multi_processor_count * 8
-    dt, probe, iters = ((torch.float64, sleefcu.lib().sleefcu_probe_dfma, 2048) if pipe == "fp64"
-                        else (torch.float32, sleefcu.lib().sleefcu_probe_ffma, 16384))
+    P = measure.probe_lib()
+    dt, probe, iters = ((torch.float64, P.probe_dfma, 2048) if pipe == "fp64"
+                        else (torch.float32, P.probe_ffma, 16384))
     out = torch.empty(blocks * 256, dtype=dt, device=device)
     st = torch.cuda.current_stream(device)
     sp = ctypes.c_void_p(st.cuda_stream)
@@ -231,7 +237,7 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
     """FP32 family (2^28 floats) and bf16/f16 activation forms ([8192, 28672]),
     each with its speedup over the plain FP64 / FP32 form of the function."""
     from paper_2001_09258_gb300 import inputs as I
-    from paper_2001_09258_gb300 import opcounts
+    from measure import opcounts
     import numpy as np
     hbm = peaks.get("hbm_gbs")
     peak_fp32 = pipe_peak(sleefcu, torch, device, "fp32")
@@ -282,7 +288,7 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
                             "fp32_pipe_peak_tops": round(peak_fp32 / 1e12, 3),
                             "fp32_frac_note": "algorithmic binary32 ops per element (oracle counting build, "
                                               "mean over the workload) x Gelem/s / measured FFMA peak "
-                                              "(sleefcu_probe_ffma)",
+                                              "(measure/probe.cu probe_ffma)",
                             "entry_points": f32},
             "bf16_f16_forms": {"shape": list(shape), "inputs": "N(0,3) rounded to the 16-bit format",
                                "entry_points": low}}
@@ -315,7 +321,7 @@ def stress(sleefcu, torch, device, st, sp, n5, peak_fp64):
     kernel groups a tile's elements by step count, so a warp's time is
     its largest count after that grouping)."""
     from paper_2001_09258_gb300 import inputs as I
-    from paper_2001_09258_gb300 import opcounts
+    from measure import opcounts
     import numpy as np
     out = {}
     for fn in I.STRESS_FNS:
@@ -360,7 +366,7 @@ def fmod_sweep(sleefcu, torch, device, st, sp, peak_fp64, n=1 << 22):
     fraction.  The steps grow by one every 52 bits of quotient, so the
     throughput falls in steps."""
     from paper_2001_09258_gb300 import inputs as I
-    from paper_2001_09258_gb300 import opcounts
+    from measure import opcounts
     pts = []
     for e in range(0, 26):
         r = 10.0 ** e
@@ -410,7 +416,8 @@ def c99(sleefcu, torch, device, st, sp, peaks, peak_fp64, n=1 << 26):
     elements per entry point, larger than L2): Gelem/s, HBM bytes and
     algorithmic pipe operations per element, and the fraction of the
     roofline (the slower of the HBM bound and the FP-pipe bound)."""
-    from paper_2001_09258_gb300 import inputs as I, opcounts
+    from paper_2001_09258_gb300 import inputs as I
+    from measure import opcounts
     cnt = opcounts.table().get("c99", {})
     hbm = peaks.get("hbm_gbs")
     peak_fp32 = pipe_peak(sleefcu, torch, device, "fp32")
@@ -570,7 +577,7 @@ def main():
         return
     import torch
     import paper_2001_09258_gb300 as sleefcu
-    from paper_2001_09258_gb300 import opcounts
+    from measure import opcounts
     device = torch.device(f"cuda:{local}")
     torch.cuda.set_device(device)
     names = args.fns.split(",") if args.fns else default_fns(sleefcu)
@@ -708,11 +715,11 @@ def main():
             "achieved": round(achieved / 1e12, 5), "peak": round(peak_fp64 / 1e12, 5),
             "unit": "Tops/s (FP64 pipe: add, mul, fma, rint, div, sqrt each one op)",
             "frac": round(achieved / peak_fp64, 4),
-            "peak_source": "measured in this run with sleefcu_probe_dfma (8 independent FMA chains "
+            "peak_source": "measured in this run with measure/probe.cu probe_dfma (8 independent FMA chains "
                            "per thread, all SMs)",
             "ops_per_element": round(ops / n, 3), "div_per_element": round(dv / n, 3),
             "sqrt_per_element": round(sq / n, 3),
-            "ops_source": "oracle counting build, per path class (paper_2001_09258_gb300/opcounts.json), "
+            "ops_source": "oracle counting build, per path class (measure/opcounts.json), "
                           "weighted by this launch's path mix",
             "fp64_inst_per_element": (pipe_counts or {}).get(dom, {}).get("fp64_inst"),
             "fp64_inst_source": "ncu sm__sass_thread_inst_executed_op_fp64_pred_on on the C2 mix "
@@ -735,7 +742,7 @@ def main():
                          f"({len(names)} entry points)",
                "single_core_value": round(el1 / s1 / 1e9, 6),
                "single_core_sample": f"{max(1024, args.cpu_sample // 16)} elements per entry point, one thread"}
-    line = {
+    detail = {
         "metric": "Gelem/s (full FP64 C99 set, u10+u35) at max-ULP <=1.0/3.5",
         "value": round(value, 4), "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max / args.steps, 4),
@@ -753,7 +760,61 @@ def main():
         "forms": ext,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line))
+    path = os.path.abspath(args.detail)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(detail, f, indent=1)
+    print(json.dumps(headline(detail, path)))
+
+
+def _spread(vals):
+    vals = sorted(v for v in vals if v is not None)
+    if not vals:
+        return None
+    return {"min": vals[0], "median": round(statistics.median(vals), 4), "max": vals[-1], "count": len(vals)}
+
+
+def headline(d, detail_path):
+    """The one JSON line bench.py prints: the contract's keys, the dominant
+    kernel's roofline, the CPU baseline, the end-to-end figure, the clocks
+    and one summary per family; the per-entry-point rows and the families'
+    tables stay in the detail file."""
+    roof = {k: d["roofline"][k] for k in ("kernel", "bound", "pipe", "achieved", "peak", "frac",
+                                          "ops_per_element", "div_per_element", "fp64_inst_per_element",
+                                          "traffic")}
+    roof["unit"] = "Tops/s"
+    roof["unit_note"] = "FP64 pipe ops: add, mul, fma, rint, div, sqrt one each (oracle counting build)"
+    roof["peak_source"] = "measured DFMA peak, this run (measure/probe.cu)"
+    fr = [r["fp64_frac"] for r in d["per_function_roofline"].values()]
+    summ = {"fp64_entry_points": {"gelem_s": _spread(list(d["per_function_gelem_s"].values())),
+                                  "roofline_frac": _spread(fr),
+                                  "at_or_above_0.8": sum(1 for v in fr if v >= 0.8)}}
+    ext = d.get("forms") or {}
+    if ext:
+        f32 = ext["fp32_family"]["entry_points"]
+        low = ext["bf16_f16_forms"]["entry_points"]
+        summ["fp32_family"] = {"gelem_s": _spread([r["gelem_s"] for r in f32.values()]),
+                               "hbm_frac": _spread([r["hbm_frac"] for r in f32.values()]),
+                               "issue_frac": _spread([r.get("issue_frac") for r in f32.values()]),
+                               "speedup_vs_f64": _spread([r["speedup_vs_f64"] for r in f32.values()])}
+        summ["bf16_f16_forms"] = {"gelem_s": _spread([r["gelem_s"] for r in low.values()]),
+                                  "hbm_frac": _spread([r["hbm_frac"] for r in low.values()]),
+                                  "speedup_vs_f32": _spread([r["speedup_vs_f32"] for r in low.values()])}
+        b = ext["batched"]
+        summ["batched"] = {k: b.get(k) for k in ("batched_graph_gelem_s", "speedup_vs_single_launches",
+                                                 "speedup_vs_single_launch_graph", "fp_frac")}
+        stv = ext["stress"]["entry_points"]
+        summ["stress"] = {"gelem_s": _spread([r["gelem_s"] for r in stv.values()]),
+                          "fp64_frac": _spread([r["fp64_frac"] for r in stv.values()])}
+        summ["c99"] = {"roofline_frac": _spread([r["roofline_frac"] for r in ext["c99"]["entry_points"].values()])}
+    cfg = dict(d["config"])
+    cfg["entry_points"] = len(cfg["entry_points"])
+    out = {k: d[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                             "higher_is_better", "scaling", "vs_baseline", "dtype", "data")}
+    out.update({"config": cfg, "roofline": roof, "cpu_baseline": d["cpu_baseline"], "e2e": d["e2e"],
+                "gpu_launches": d["gpu_launches"], "clocks": d["clocks"], "summary": summ,
+                "detail": os.path.relpath(detail_path, ROOT) if detail_path.startswith(ROOT) else detail_path})
+    return out
 
 
 if __name__ == "__main__":

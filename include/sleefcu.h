@@ -560,14 +560,7 @@ sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk);
  * buffers. */
 sleefcu_status sleefcu_eval_host_many(const sleefcu_batch_item *items, size_t count, size_t chunk);
 
-/* ---------------- diagnostics (not part of the method) ----------------
- * Pipe-throughput probes for the roofline denominators: blocks x 256 threads
- * each run 8 independent chains of `iters` fused multiply-adds in FP64
- * (probe_dfma) or FP32 (probe_ffma), i.e. blocks*256*iters*8 FMAs, and write
- * one value per thread to out (blocks*256 elements, device memory owned by
- * the caller).  EINVAL for a null out or non-positive blocks / iters. */
-sleefcu_status sleefcu_probe_dfma(double *out, int blocks, int iters, sleefcu_stream stream);
-sleefcu_status sleefcu_probe_ffma(float *out, int blocks, int iters, sleefcu_stream stream);
+/* ---------------- diagnostics (not part of the method) ---------------- */
 
 /* Long-division step count of the remainder kernels (Section 5.9): out[i] =
  * the number of steps the fmod kernel takes for |x[i]| mod |y[i]| (0 where

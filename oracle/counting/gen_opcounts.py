@@ -1,6 +1,6 @@
 """Write the algorithmic operation counts of the benchmark's workloads from
 the counting build of the oracle (test infrastructure: the table it writes,
-paper_2001_09258_gb300/opcounts.json, is data for the roofline of bench.py;
+measure/opcounts.json, is data for the roofline of bench.py;
 nothing in the package imports or runs this file).
 
 Binary64 entry points are counted per reduction path (path classes defined
@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 import oracle  # noqa: E402
 from paper_2001_09258_gb300 import inputs as I  # noqa: E402
 
-OUT = os.path.join(ROOT, "paper_2001_09258_gb300", "opcounts.json")
+OUT = os.path.join(ROOT, "measure", "opcounts.json")
 SAMPLE = 1 << 17            # workload sample drawn per function
 SAMPLE_PER_CLASS = 2048     # elements counted per path class
 FMOD_SAMPLE = 512           # elements counted one by one per fmod workload

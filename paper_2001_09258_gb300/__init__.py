@@ -14,8 +14,6 @@ library is missing or fails to load, every call raises.
 import ctypes
 import os
 
-from . import inputs  # noqa: F401  (seeded synthetic inputs; no method arithmetic)
-
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsleefcu.so")
 
@@ -98,9 +96,6 @@ def lib():
             raise SleefcuError(f"cannot load {LIB_PATH}: {e}") from e
         L.sleefcu_last_error.restype = ctypes.c_char_p
         L.sleefcu_version.restype = ctypes.c_char_p
-        for probe in ("sleefcu_probe_dfma", "sleefcu_probe_ffma"):
-            getattr(L, probe).restype = ctypes.c_int
-            getattr(L, probe).argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
         L.sleefcu_fmod_steps_f64.restype = ctypes.c_int
         L.sleefcu_fmod_steps_f64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]
         for name in entry_points():

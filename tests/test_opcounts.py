@@ -18,7 +18,7 @@ import pytest
 import oracle
 from oracle.counting import gen_opcounts as G
 from paper_2001_09258_gb300 import inputs as I
-from paper_2001_09258_gb300 import opcounts as O
+from measure import opcounts as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -117,7 +117,7 @@ def test_tan_has_one_dd_division_and_no_square_root():
 def test_exact_counts_of_fixed_paths():
     """A few paths are branch-free, so their count is the same for every
     element: an exact integer mean in the table."""
-    t = json.load(open(os.path.join(ROOT, "paper_2001_09258_gb300", "opcounts.json")))["f64"]
+    t = json.load(open(os.path.join(ROOT, "measure", "opcounts.json")))["f64"]
     for name, cls in [("sin_u10_f64", "cw1"), ("exp_u10_f64", "all"), ("tan_u10_f64", "ph"),
                       ("atan_u10_f64", "small"), ("erf_u10_f64", "f")]:
         v = t[name][cls]["ops"]
