@@ -489,8 +489,7 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
         out2 = torch.empty_like(x) if sleefcu.FUNCS[fn] == "sc" else None
         items.append((name, x, y, out, out2))
     total = int(lens.sum())
-    b = sleefcu.Batch(items)
-    b.autotune(os.path.join(ROOT, "paper_2001_09258_gb300", "_build", "batch_tune.jsonl"))
+    b = sleefcu.Batch(items, tune_file=os.path.join(ROOT, "paper_2001_09258_gb300", "_build", "batch_tune.jsonl"))
     cfg = b.config()
     ms_plain = time_calls(torch, st, lambda: b.launch(st), reps=5)
     ms_graph = time_calls(torch, st, lambda: b.launch(st, graph=True), reps=5)
@@ -509,6 +508,22 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
                        [out] + ([out2] if out2 is not None else []), csp)
     ms_single_graph = time_calls(torch, st, lambda: g.replay(), reps=3)
     b.close()
+    # host-side latency of the allocation-free launch over the same 4096
+    # items, on an idle stream and behind a 50 ms busy kernel (the call must
+    # return without waiting for the stream)
+    lat = {}
+    for label, busy in (("idle_stream_us", False), ("busy_stream_us", True)):
+        sleefcu.batch_launch_static(items, stream=st)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            if busy:
+                torch.cuda._sleep(100_000_000)
+            t = time.perf_counter()
+            sleefcu.batch_launch_static(items, stream=st)
+            ts.append((time.perf_counter() - t) * 1e6)
+            torch.cuda.synchronize()
+        lat[label] = round(statistics.median(ts), 1)
     gel = lambda ms: round(total / (ms * 1e-3) / 1e9, 3)
     return {"arrays": narrays, "elements": total, "entry_points": len(names_all), "config": cfg,
             "batched_ms": round(ms_plain, 3), "batched_graph_ms": round(ms_graph, 3),
@@ -516,7 +531,8 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
             "batched_gelem_s": gel(ms_plain), "batched_graph_gelem_s": gel(ms_graph),
             "single_launches_gelem_s": gel(ms_single), "single_launches_graph_gelem_s": gel(ms_single_graph),
             "speedup_vs_single_launches": round(ms_single / ms_graph, 2),
-            "speedup_vs_single_launch_graph": round(ms_single_graph / ms_graph, 2)}
+            "speedup_vs_single_launch_graph": round(ms_single_graph / ms_graph, 2),
+            "static_launch_host_latency": lat}
 
 
 def cpu_baseline(names, n_sample, rank, threads=None):

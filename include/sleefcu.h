@@ -7,7 +7,9 @@
  *
  * Common conventions of every sleefcu_<fn>_<u10|u35>_<f64|f32> entry point:
  *  - x, y, out, out2 are DEVICE pointers owned by the caller; the library
- *    neither allocates nor frees them.  Host pointers are undefined behaviour.
+ *    neither allocates nor frees them.  Host pointers are undefined behaviour
+ *    in this library; the checked build (libsleefcu_checked.so, see the
+ *    diagnostics section) rejects them with SLEEFCU_EINVAL.
  *  - Layout: contiguous 1-D arrays of n elements.  Any alignment is accepted
  *    (16-byte-aligned arrays take the vectorized path).  out may equal x
  *    (in place); any other overlap between inputs and outputs is undefined.
@@ -471,6 +473,12 @@ sleefcu_status sleefcu_log1p_u35_f16(const void *x, void *out, size_t n, sleefcu
  * for a combination the library does not have, EINVAL for a null pointer
  * with n > 0, ENOMEM when the descriptors do not fit.  Items with n == 0 are
  * ignored.  The caller keeps the arrays alive while the plan is launched.
+ * tune_file_or_null: NULL keeps the default configuration (block 256, tile
+ * 4096, grid multiplier 2, vector width 2); otherwise create ends with
+ * sleefcu_batch_autotune(plan, tune_file_or_null, default stream) and waits
+ * for it, with "" meaning "tune without a cache file" (the tuning runs write
+ * the outputs).  Tuning is also its own call so that a plan can be re-tuned
+ * (after sleefcu_batch_set_config, or on other data of the same shape).
  * sleefcu_batch_launch enqueues one memset and one kernel on the stream, no
  * allocation and no synchronization: it may be captured in a CUDA graph.
  * sleefcu_batch_launch_graph captures that pair once into a graph owned by
@@ -504,7 +512,8 @@ typedef struct {
 } sleefcu_batch_item;
 typedef struct sleefcu_batch sleefcu_batch;
 
-sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count, sleefcu_batch **plan);
+sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count, const char *tune_file_or_null,
+                                    sleefcu_batch **plan);
 sleefcu_status sleefcu_batch_launch(sleefcu_batch *plan, sleefcu_stream stream);
 sleefcu_status sleefcu_batch_launch_graph(sleefcu_batch *plan, sleefcu_stream stream);
 sleefcu_status sleefcu_batch_autotune(sleefcu_batch *plan, const char *cache_file_or_null, sleefcu_stream stream);
@@ -516,21 +525,28 @@ void sleefcu_batch_destroy(sleefcu_batch *plan);
 /* Batched launch without allocation (this library's addition; the paper has
  * no counterpart).  The same evaluation as a plan's sleefcu_batch_launch,
  * bit for bit, for callers that may not allocate device memory when they
- * launch: the descriptors, tile prefix sums and tile counter live in one
+ * launch: an application whose caching allocator owns the device heap (a
+ * cudaMalloc of its own would fragment it or fail), or a latency-critical
+ * path that cannot take cudaMalloc/cudaFree and the synchronization they
+ * imply.  The descriptors, tile prefix sums and tile counter live in one
  * fixed device array of about 230 KB inside the library instead of
- * cudaMalloc'd plan buffers.  items: host array of count descriptors (the
+ * cudaMalloc'd plan buffers; every GPU that loads the library holds it
+ * until the process exits.  items: host array of count descriptors (the
  * same rules as sleefcu_batch_create; items with n == 0 are skipped).
  * count > 4096 returns SLEEFCU_EINVAL with a message; an unsupported
- * combination SLEEFCU_EUNSUPPORTED.  The call enqueues two host-to-device
- * copies of the descriptors (from library-owned host memory), a memset that
- * zeroes the tile counter, and the kernel, in that order on `stream`; the
- * configuration is the default one (block 256, tile 4096).  The first call
- * on each device looks up the array's address with that device current, so
- * make it before any stream capture that should contain later calls.  One
- * array serves all callers on a device: calls whose work can overlap (other
- * streams, other host threads) race on it and corrupt each other's
- * descriptors; serialize them on one stream or synchronize in between.
- * Nothing is allocated, by this call or the first one. */
+ * combination SLEEFCU_EUNSUPPORTED; every item is checked before anything
+ * is enqueued.  The call enqueues ceil(items with n > 0 / 256) small staging
+ * kernels, which carry the descriptors as kernel arguments and also zero
+ * the tile counter, then the batched kernel, in that order on `stream`, and
+ * returns without waiting for the stream (there is no copy from host
+ * memory); the configuration is the default one (block 256, tile 4096).
+ * The first call on each device looks up the array's address with that
+ * device current; make that first call before any stream capture.  One
+ * array serves all callers on a device and keeps the last call's contents:
+ * calls whose work can overlap on the GPU (other streams, other host
+ * threads) race on it and corrupt each other's descriptors; serialize them
+ * on one stream or synchronize in between.  Nothing is allocated, by this
+ * call or the first one. */
 sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size_t count,
                                            sleefcu_stream stream);
 
@@ -560,7 +576,26 @@ sleefcu_status sleefcu_eval_host(const sleefcu_batch_item *item, size_t chunk);
  * buffers. */
 sleefcu_status sleefcu_eval_host_many(const sleefcu_batch_item *items, size_t count, size_t chunk);
 
-/* ---------------- diagnostics (not part of the method) ---------------- */
+/* ---------------- diagnostics (not part of the method) ----------------
+ * The checked build (libsleefcu_checked.so, compiled with -DSLEEFCU_CHECKED
+ * from the same sources) has every entry point of this header with the same
+ * results, plus checks that cost time: before any launch, each device
+ * pointer argument is looked up (cudaPointerGetAttributes and the
+ * allocation's address range) and the call returns SLEEFCU_EINVAL, with a
+ * message, for host memory, memory of another device, or an array whose n
+ * elements run past the end of its allocation (sleefcu_eval_host and
+ * sleefcu_eval_host_many, which take host arrays, are not checked); and the
+ * kernels count table indices that had to be clamped for a finite argument
+ * (the Payne-Hanek table gathers; a non-zero count means a lane reached the
+ * gather on a path it should not take), without trapping.
+ * sleefcu_is_checked: 1 in the checked build, 0 in the normal one.
+ * sleefcu_checked_error_count: the count since the last reset, summed over
+ * the library's kernels on the current device (synchronous: it reads device
+ * memory); reset != 0 zeroes it.  EINVAL for a null count; in the normal
+ * build it returns SLEEFCU_EUNSUPPORTED. */
+int sleefcu_is_checked(void);
+sleefcu_status sleefcu_checked_error_count(unsigned long long *count, int reset);
+
 
 /* Long-division step count of the remainder kernels (Section 5.9): out[i] =
  * the number of steps the fmod kernel takes for |x[i]| mod |y[i]| (0 where

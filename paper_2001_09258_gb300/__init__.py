@@ -16,6 +16,7 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsleefcu.so")
+LIB_CHECKED_PATH = os.path.join(_HERE, "_build", "libsleefcu_checked.so")
 
 # (function, kind) for every entry point; kind: "u" unary, "b" binary (x, y),
 # "sc" one input two outputs.  Each is exported for the listed accuracies and
@@ -49,6 +50,7 @@ C99_FUNCS = {
 C99_ACCS = {"sqrt": ("u05", "u35"), "hypot": ("u05", "u35"), "sinpi": ("u05", "u35"), "cospi": ("u05", "u35")}
 
 _lib = None
+_lib_checked = None
 
 
 class SleefcuError(RuntimeError):
@@ -83,40 +85,74 @@ def masked_entry_points():
     return [e for e in entry_points() if e.endswith("_f64")]
 
 
+def _declare(L):
+    """Declare the argument and result types of every exported function."""
+    L.sleefcu_last_error.restype = ctypes.c_char_p
+    L.sleefcu_version.restype = ctypes.c_char_p
+    L.sleefcu_is_checked.restype = ctypes.c_int
+    L.sleefcu_is_checked.argtypes = []
+    L.sleefcu_checked_error_count.restype = ctypes.c_int
+    L.sleefcu_checked_error_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+    L.sleefcu_fmod_steps_f64.restype = ctypes.c_int
+    L.sleefcu_fmod_steps_f64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]
+    for name in entry_points():
+        fn = name.split("_")[0]
+        f = getattr(L, "sleefcu_" + name)
+        f.restype = ctypes.c_int
+        nptr = {"u": 2, "b": 3, "sc": 3}[FUNCS[fn]]
+        f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+    for name in c99_entry_points():
+        f = getattr(L, "sleefcu_" + name)
+        f.restype = ctypes.c_int
+        nptr = {"u": 2, "b": 3, "sc": 3, "ui": 2, "bi": 3, "si": 3}[C99_FUNCS[name.split("_")[0]]]
+        f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+    for name in masked_entry_points():
+        fn = name.split("_")[0]
+        f = getattr(L, "sleefcu_" + name + "_masked")
+        f.restype = ctypes.c_int
+        nptr = {"u": 3, "b": 4, "sc": 4}[FUNCS[fn]]          # the mask comes after the inputs
+        f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
+    L.sleefcu_batch_create.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_char_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]
+    for f in ("sleefcu_batch_launch", "sleefcu_batch_launch_graph"):
+        getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.sleefcu_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
+    L.sleefcu_batch_set_config.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+    L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.sleefcu_batch_launch_static.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_void_p]
+    L.sleefcu_eval_host.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t]
+    L.sleefcu_eval_host_many.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_size_t]
+    L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
+    L.sleefcu_batch_destroy.restype = None
+    return L
+
+
+def _load(path):
+    if not os.path.exists(path):
+        from . import _build
+        _build.build()
+    try:
+        return _declare(ctypes.CDLL(path))
+    except OSError as e:
+        raise SleefcuError(f"cannot load {path}: {e}") from e
+
+
 def lib():
     """Load libsleefcu.so (building it first if it does not exist)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            from . import _build
-            _build.build()
-        try:
-            L = ctypes.CDLL(LIB_PATH)
-        except OSError as e:
-            raise SleefcuError(f"cannot load {LIB_PATH}: {e}") from e
-        L.sleefcu_last_error.restype = ctypes.c_char_p
-        L.sleefcu_version.restype = ctypes.c_char_p
-        L.sleefcu_fmod_steps_f64.restype = ctypes.c_int
-        L.sleefcu_fmod_steps_f64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]
-        for name in entry_points():
-            fn = name.split("_")[0]
-            f = getattr(L, "sleefcu_" + name)
-            f.restype = ctypes.c_int
-            nptr = {"u": 2, "b": 3, "sc": 3}[FUNCS[fn]]
-            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
-        for name in c99_entry_points():
-            f = getattr(L, "sleefcu_" + name)
-            f.restype = ctypes.c_int
-            nptr = {"u": 2, "b": 3, "sc": 3, "ui": 2, "bi": 3, "si": 3}[C99_FUNCS[name.split("_")[0]]]
-            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
-        for name in masked_entry_points():
-            fn = name.split("_")[0]
-            f = getattr(L, "sleefcu_" + name + "_masked")
-            f.restype = ctypes.c_int
-            nptr = {"u": 3, "b": 4, "sc": 4}[FUNCS[fn]]          # the mask comes after the inputs
-            f.argtypes = [ctypes.c_void_p] * nptr + [ctypes.c_size_t, ctypes.c_void_p]
-        _lib = L
+        _lib = _load(LIB_PATH)
     return _lib
+
+
+def lib_checked():
+    """Load the checked build, libsleefcu_checked.so: the same entry points
+    and results, plus device-pointer checks before every launch and a device
+    error word (sleefcu_checked_error_count)."""
+    global _lib_checked
+    if _lib_checked is None:
+        _lib_checked = _load(LIB_CHECKED_PATH)
+    return _lib_checked
 
 
 def last_error():
@@ -278,22 +314,7 @@ class BatchItem(ctypes.Structure):
 
 
 def _batch_lib():
-    L = lib()
-    if not getattr(L, "_batch_ready", False):
-        L.sleefcu_batch_create.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t,
-                                           ctypes.POINTER(ctypes.c_void_p)]
-        for f in ("sleefcu_batch_launch", "sleefcu_batch_launch_graph"):
-            getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
-        L.sleefcu_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
-        L.sleefcu_batch_set_config.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
-        L.sleefcu_batch_get_config.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4
-        L.sleefcu_batch_launch_static.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_void_p]
-        L.sleefcu_eval_host.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t]
-        L.sleefcu_eval_host_many.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_size_t, ctypes.c_size_t]
-        L.sleefcu_batch_destroy.argtypes = [ctypes.c_void_p]
-        L.sleefcu_batch_destroy.restype = None
-        L._batch_ready = True
-    return L
+    return lib()
 
 
 def _items_array(items):
@@ -349,9 +370,11 @@ def eval_host_many(items, chunk=0):
 
 class Batch:
     """A plan for sleefcu_batch_*: items are (entry point name, x, y, out, out2)
-    with CUDA tensors (y / out2 None where unused)."""
+    with CUDA tensors (y / out2 None where unused).  tune_file: None keeps the
+    default configuration; a path (or "" for no cache file) autotunes the
+    plan inside sleefcu_batch_create."""
 
-    def __init__(self, items):
+    def __init__(self, items, tune_file=None):
         L = _batch_lib()
         arr = (BatchItem * len(items))()
         self._keep = items
@@ -361,7 +384,8 @@ class Batch:
                                x.data_ptr(), y.data_ptr() if y is not None else None,
                                out.data_ptr(), out2.data_ptr() if out2 is not None else None, x.numel())
         h = ctypes.c_void_p()
-        _check(L.sleefcu_batch_create(arr, len(items), ctypes.byref(h)), "batch_create")
+        tf = None if tune_file is None else tune_file.encode()
+        _check(L.sleefcu_batch_create(arr, len(items), tf, ctypes.byref(h)), "batch_create")
         self.handle = h
 
     def _stream(self, stream):

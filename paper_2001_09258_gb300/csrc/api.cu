@@ -5,6 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
+#include <vector>
+#ifdef SLEEFCU_CHECKED
+#include <cuda.h>
+#endif
 #include "sleefcu_common.cuh"
 
 namespace sleefcu {
@@ -58,7 +62,107 @@ int grid_for(const void *kernel, size_t work_items) {
   return (int)(need < (size_t)cap ? need : (size_t)cap);
 }
 
+// ---------------- checked build ----------------
+namespace {
+std::mutex g_chk_mu;
+std::vector<sleefcu_status (*)(unsigned long long *, int)> &checked_words() {
+  static std::vector<sleefcu_status (*)(unsigned long long *, int)> v;
+  return v;
+}
+}  // namespace
+
+void register_checked_word(sleefcu_status (*read)(unsigned long long *, int)) {
+  std::lock_guard<std::mutex> lock(g_chk_mu);
+  checked_words().push_back(read);
+}
+
+#ifdef SLEEFCU_CHECKED
+namespace {
+// cuMemGetAddressRange through the runtime's driver entry point (no link
+// dependency on libcuda): the base and size of the allocation holding p
+typedef CUresult (*AddrRangeFn)(CUdeviceptr *, size_t *, CUdeviceptr);
+AddrRangeFn addr_range_fn() {
+  static AddrRangeFn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return (AddrRangeFn)f;
+  }();
+  return fn;
+}
+}  // namespace
+
+sleefcu_status check_dev_range(const char *name, const void *p, size_t bytes) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: pointer %p: %s (checked build)", name, p, cudaGetErrorString(e));
+    return SLEEFCU_EINVAL;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+    set_error("%s: %p is not device memory (memory type %d; checked build)", name, p, (int)a.type);
+    return SLEEFCU_EINVAL;
+  }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (a.device != dev) {
+    set_error("%s: %p is memory of device %d, the current device is %d (checked build)", name, p, a.device, dev);
+    return SLEEFCU_EINVAL;
+  }
+  if (a.type == cudaMemoryTypeDevice) {
+    if (AddrRangeFn fn = addr_range_fn()) {
+      CUdeviceptr base = 0;
+      size_t size = 0;
+      if (fn(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS &&
+          (uintptr_t)p + bytes > (uintptr_t)base + size) {
+        set_error("%s: %zu bytes from %p run past the end of its allocation (%zu bytes from %p; checked build)",
+                  name, bytes, p, size, (void *)(uintptr_t)base);
+        return SLEEFCU_EINVAL;
+      }
+    }
+  }
+  return SLEEFCU_OK;
+}
+#endif
+
 }  // namespace sleefcu
 
+extern "C" int sleefcu_is_checked(void) {
+#ifdef SLEEFCU_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" sleefcu_status sleefcu_checked_error_count(unsigned long long *count, int reset) {
+#ifdef SLEEFCU_CHECKED
+  if (!count) { sleefcu::set_error("sleefcu_checked_error_count: null count"); return SLEEFCU_EINVAL; }
+  *count = 0;
+  std::lock_guard<std::mutex> lock(sleefcu::g_chk_mu);
+  for (auto read : sleefcu::checked_words()) {
+    if (read(count, reset) != SLEEFCU_OK) {
+      sleefcu::set_error("sleefcu_checked_error_count: %s", cudaGetErrorString(cudaGetLastError()));
+      return SLEEFCU_ECUDA;
+    }
+  }
+  return SLEEFCU_OK;
+#else
+  (void)count;
+  (void)reset;
+  sleefcu::set_error("sleefcu_checked_error_count: not a checked build (load libsleefcu_checked.so)");
+  return SLEEFCU_EUNSUPPORTED;
+#endif
+}
+
 extern "C" const char *sleefcu_last_error(void) { return sleefcu::g_err; }
-extern "C" const char *sleefcu_version(void) { return "sleefcu 0.1 (sm_103a)"; }
+#ifdef SLEEFCU_CHECKED
+extern "C" const char *sleefcu_version(void) { return "sleefcu 0.2 (sm_103a, checked)"; }
+#else
+extern "C" const char *sleefcu_version(void) { return "sleefcu 0.2 (sm_103a)"; }
+#endif

@@ -516,7 +516,21 @@ static sleefcu_status upload_prefix(sleefcu_batch *p) {
   return SLEEFCU_OK;
 }
 
-extern "C" sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count, sleefcu_batch **plan) {
+// checked build: every array of an item must be device memory holding its n elements
+static sleefcu_status check_item(const char *name, const sleefcu_batch_item &it, int code) {
+  size_t es = it.dtype == SLEEFCU_F64 ? 8 : it.dtype == SLEEFCU_F32 ? 4 : 2;
+  if (sleefcu_status r = check_args(name, it.n * es, (const unsigned char *)it.x,
+                                    (const unsigned char *)it.out))
+    return r;
+  if (needs_y(code))
+    if (sleefcu_status r = check_args(name, it.n * es, (const unsigned char *)it.y)) return r;
+  if (needs_out2(code))
+    if (sleefcu_status r = check_args(name, it.n * es, (const unsigned char *)it.out2)) return r;
+  return SLEEFCU_OK;
+}
+
+extern "C" sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, size_t count,
+                                               const char *tune_file_or_null, sleefcu_batch **plan) {
   if (!plan || (count && !items)) { set_error("sleefcu_batch_create: null argument"); return SLEEFCU_EINVAL; }
   *plan = nullptr;
   sleefcu_batch *p = new sleefcu_batch();
@@ -533,6 +547,10 @@ extern "C" sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, 
       set_error("sleefcu_batch_create: item %zu: null pointer with n = %zu", i, it.n);
       delete p;
       return SLEEFCU_EINVAL;
+    }
+    if (sleefcu_status r = check_item("sleefcu_batch_create", it, c)) {
+      delete p;
+      return r;
     }
     p->desc.push_back(Desc{it.x, it.y, it.out, it.out2, (long long)it.n, c, 0});
   }
@@ -556,6 +574,12 @@ extern "C" sleefcu_status sleefcu_batch_create(const sleefcu_batch_item *items, 
     }
   }
   sleefcu_status st = upload_prefix(p);
+  if (st == SLEEFCU_OK && tune_file_or_null)
+    st = sleefcu_batch_autotune(p, *tune_file_or_null ? tune_file_or_null : nullptr, nullptr);
+  if (st == SLEEFCU_OK && tune_file_or_null && cudaStreamSynchronize(nullptr) != cudaSuccess) {
+    set_error("sleefcu_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
+    st = SLEEFCU_ECUDA;
+  }
   if (st != SLEEFCU_OK) { sleefcu_batch_destroy(p); return st; }
   *plan = p;
   return SLEEFCU_OK;
@@ -719,7 +743,10 @@ extern "C" sleefcu_status sleefcu_batch_autotune(sleefcu_batch *p, const char *c
 // is not acceptable.  For them this entry point keeps the descriptors, the
 // tile prefix sums and the tile counter in one fixed device array of file
 // scope, sized for at most kStaticItems arrays (about 230 KB), and runs the
-// same k_batch kernel with the default configuration.
+// same k_batch kernel with the default configuration.  The descriptors reach
+// the array as arguments of small staging kernels (up to kStageItems per
+// launch), not by copies from host memory: a copy from pageable host memory
+// would first wait for all earlier work on the stream.
 namespace {
 constexpr size_t kStaticItems = 4096;
 constexpr size_t kStaticDescBytes = kStaticItems * sizeof(sleefcu::batch::Desc);
@@ -727,15 +754,38 @@ constexpr size_t kStaticPreBytes = (kStaticItems + 1) * sizeof(long long);
 constexpr size_t kStaticBytes = kStaticDescBytes + kStaticPreBytes + sizeof(unsigned long long);
 constexpr int kStaticMaxDevices = 64;
 constexpr int kStaticBlock = 256, kStaticTile = 4096, kStaticGridMult = 2, kStaticVec = 2;
-
-std::mutex g_static_mu;                                   // guards the host staging and the table
+std::mutex g_static_mu;                                   // guards the address table
 void *g_static_dev[kStaticMaxDevices];                     // scratch address per device
-sleefcu::batch::Desc g_static_hdesc[kStaticItems];         // host staging, reused by every call
-long long g_static_hpre[kStaticItems + 1];
 }  // namespace
+
+namespace sleefcu {
+namespace batch {
+constexpr int kStageItems = 256;
+// one staging launch: descriptors first .. first+count-1 and their prefix sums
+struct StageChunk {
+  Desc desc[kStageItems];
+  long long pre[kStageItems];            // pre[j]: tiles of items 0 .. first+j
+  int first, count;
+};
+static_assert(sizeof(StageChunk) < 32000, "staging chunk exceeds the kernel argument limit");
+}  // namespace batch
+}  // namespace sleefcu
 
 // layout: Desc[kStaticItems], long long pre[kStaticItems + 1], tile counter
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
+
+__global__ void __launch_bounds__(kStageItems) k_static_stage(const StageChunk c, Desc *d_desc, long long *d_pre,
+                                                              unsigned long long *d_ctr) {
+  int j = threadIdx.x;
+  if (j < c.count) {
+    d_desc[c.first + j] = c.desc[j];
+    d_pre[c.first + j + 1] = c.pre[j];
+  }
+  if (c.first == 0 && j == 0) {
+    d_pre[0] = 0;
+    *d_ctr = 0;                          // the tile counter starts at 0 on every call
+  }
+}
 
 extern "C" sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *items, size_t count,
                                                       sleefcu_stream s) {
@@ -752,18 +802,9 @@ extern "C" sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *
     set_error("sleefcu_batch_launch_static: device %d beyond the %d supported", dev, kStaticMaxDevices);
     return SLEEFCU_EUNSUPPORTED;
   }
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_dev[dev]) {                               // first call on this device (device current)
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_batch_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("sleefcu_batch_launch_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      return SLEEFCU_ECUDA;
-    }
-    g_static_dev[dev] = p;
-  }
+  // every item is checked before anything is enqueued
   size_t nd = 0;
-  g_static_hpre[0] = 0;
+  long long ntiles = 0;
   for (size_t i = 0; i < count; i++) {
     const sleefcu_batch_item &it = items[i];
     int c = code_of(it);
@@ -777,24 +818,50 @@ extern "C" sleefcu_status sleefcu_batch_launch_static(const sleefcu_batch_item *
       set_error("sleefcu_batch_launch_static: item %zu: null pointer with n = %zu", i, it.n);
       return SLEEFCU_EINVAL;
     }
-    g_static_hdesc[nd] = Desc{it.x, it.y, it.out, it.out2, (long long)it.n, c, 0};
-    g_static_hpre[nd + 1] = g_static_hpre[nd] + (long long)((it.n + kStaticTile - 1) / kStaticTile);
+    if (sleefcu_status r = check_item("sleefcu_batch_launch_static", it, c)) return r;
     nd++;
+    ntiles += (long long)((it.n + kStaticTile - 1) / kStaticTile);
   }
-  long long ntiles = g_static_hpre[nd];
   if (ntiles == 0) return SLEEFCU_OK;
-  unsigned char *base = (unsigned char *)g_static_dev[dev];
+  void *addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_dev[dev]) {                             // first call on this device (device current)
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_batch_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error("sleefcu_batch_launch_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return SLEEFCU_ECUDA;
+      }
+      g_static_dev[dev] = p;
+    }
+    addr = g_static_dev[dev];
+  }
+  unsigned char *base = (unsigned char *)addr;
   Desc *d_desc = (Desc *)base;
   long long *d_pre = (long long *)(base + kStaticDescBytes);
   unsigned long long *d_ctr = (unsigned long long *)(base + kStaticDescBytes + kStaticPreBytes);
   cudaStream_t st = (cudaStream_t)s;
-  // pageable sources: each copy returns once the bytes are staged, so the
-  // host arrays may be refilled by the next call
-  e = cudaMemcpyAsync(d_desc, g_static_hdesc, nd * sizeof(Desc), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_pre, g_static_hpre, (nd + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);   // counter starts at 0
-  if (e != cudaSuccess) { set_error("sleefcu_batch_launch_static: %s", cudaGetErrorString(e)); return SLEEFCU_ECUDA; }
+  StageChunk chunk;
+  chunk.first = 0;
+  chunk.count = 0;
+  long long pre = 0;
+  size_t k = 0;
+  for (size_t i = 0; i < count; i++) {
+    const sleefcu_batch_item &it = items[i];
+    if (it.n == 0) continue;
+    pre += (long long)((it.n + kStaticTile - 1) / kStaticTile);
+    chunk.desc[chunk.count] = Desc{it.x, it.y, it.out, it.out2, (long long)it.n, code_of(it), 0};
+    chunk.pre[chunk.count] = pre;
+    chunk.count++;
+    k++;
+    if (chunk.count == kStageItems || k == nd) {
+      k_static_stage<<<1, kStageItems, 0, st>>>(chunk, d_desc, d_pre, d_ctr);
+      if (sleefcu_status r = check_launch("sleefcu_batch_launch_static")) return r;
+      chunk.first += chunk.count;
+      chunk.count = 0;
+    }
+  }
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_batch, kStaticBlock, 0);

@@ -586,6 +586,7 @@ template <class T, class F>
 sleefcu_status launch_toint(const char *name, const T *x, int32_t *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned_v<T>(out)) {
     auto k = k_toint<T, F, true>;
@@ -600,6 +601,7 @@ template <class T, class F>
 sleefcu_status launch_withint(const char *name, const T *x, const int32_t *e, T *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !e || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, e, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(out) && aligned_v<T>(e)) {
     auto k = k_withint<T, F, true>;
@@ -614,6 +616,7 @@ template <class T, class F>
 sleefcu_status launch_splitint(const char *name, const T *x, T *m, int32_t *e, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !m || !e) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, m, e)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(m) && aligned_v<T>(e)) {
     auto k = k_splitint<T, F, true>;

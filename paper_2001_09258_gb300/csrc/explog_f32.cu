@@ -81,6 +81,7 @@ sleefcu_status launch_lowp(const char *name, const void *x, void *out, size_t n,
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   const uint16_t *xi = (const uint16_t *)x;
   uint16_t *oi = (uint16_t *)out;
+  if (sleefcu_status rc_ = check_args(name, n, xi, oi)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(out)) {
     auto k = k_lowp<F, BF, true>;

@@ -9,6 +9,36 @@
 
 namespace sleefcu {
 
+// ---------------- checked build: device error word ----------------
+// In the checked build each translation unit keeps a counter of table
+// indices that had to be clamped for a finite argument (a lane that reached
+// a table gather it should never reach); the kernels count and go on, they
+// never trap.  sleefcu_checked_error_count() sums the counters of all units.
+#ifdef SLEEFCU_CHECKED
+static __device__ unsigned long long g_checked_count;
+void register_checked_word(sleefcu_status (*read)(unsigned long long *, int));
+namespace {
+sleefcu_status read_checked_word(unsigned long long *v, int reset) {
+  unsigned long long x = 0;
+  if (cudaMemcpyFromSymbol(&x, g_checked_count, sizeof x) != cudaSuccess) return SLEEFCU_ECUDA;
+  if (reset) {
+    const unsigned long long z = 0;
+    if (cudaMemcpyToSymbol(g_checked_count, &z, sizeof z) != cudaSuccess) return SLEEFCU_ECUDA;
+  }
+  *v += x;
+  return SLEEFCU_OK;
+}
+struct CheckedWordReg {
+  CheckedWordReg() { register_checked_word(&read_checked_word); }
+} g_checked_word_reg;
+}  // namespace
+__device__ __forceinline__ void checked_note(bool bad) {
+  if (bad) atomicAdd(&g_checked_count, 1ull);
+}
+#else
+__device__ __forceinline__ void checked_note(bool) {}
+#endif
+
 // ---------------- bit helpers (integer pipe) ----------------
 // The bits of a double through an opaque register move: the compiler would
 // otherwise turn NaN, infinity and sign tests written on the bits back into
@@ -412,12 +442,30 @@ void set_error(const char *fmt, ...);
 sleefcu_status check_launch(const char *what);
 int grid_for(const void *kernel, size_t work_items);
 
+// Argument checks of the checked build (-DSLEEFCU_CHECKED, libsleefcu_checked.so):
+// every device array of a call must be device (or managed) memory of the
+// current device holding its n elements; otherwise the call returns
+// SLEEFCU_EINVAL before any launch.  In the normal build the check is empty.
+#ifdef SLEEFCU_CHECKED
+sleefcu_status check_dev_range(const char *name, const void *p, size_t bytes);
+template <class... P>
+sleefcu_status check_args(const char *name, size_t n, const P *...p) {
+  sleefcu_status r = SLEEFCU_OK;
+  ((r = (r == SLEEFCU_OK ? check_dev_range(name, (const void *)p, n * sizeof(P)) : r)), ...);
+  return r;
+}
+#else
+template <class... P>
+constexpr sleefcu_status check_args(const char *, size_t, const P *...) { return SLEEFCU_OK; }
+#endif
+
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 template <class F>
 sleefcu_status launch_unary64(const char *name, const double *x, double *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(out)) {
     auto k = k_unary64<F, true>;
@@ -434,6 +482,7 @@ sleefcu_status launch_binary64(const char *name, const double *x, const double *
                                sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, y, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(y) && aligned16(out)) {
     auto k = k_binary64<F, true>;
@@ -450,6 +499,7 @@ sleefcu_status launch_dual64(const char *name, const double *x, double *o1, doub
                              sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, o1, o2)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(o1) && aligned16(o2)) {
     auto k = k_dual64<F, true>;
@@ -465,6 +515,7 @@ template <class F>
 sleefcu_status launch_sorted64(const char *name, const double *x, double *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, out)) return rc_;
   auto k = k_sorted64<F, 1>;
   constexpr int EPT = sort_ept<F>::value;
   k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, out, n, nullptr);
@@ -475,6 +526,7 @@ sleefcu_status launch_sorted64_dual(const char *name, const double *x, double *o
                                     sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, o1, o2)) return rc_;
   auto k = k_sorted64<F, 2>;
   constexpr int EPT = sort_ept<F>::value;
   k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, o1, o2, n, nullptr);
@@ -485,6 +537,7 @@ sleefcu_status launch_sorted64b(const char *name, const double *x, const double 
                                 sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, y, out)) return rc_;
   auto k = k_sorted64b<F>;
   k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, nullptr);
   return check_launch(name);
@@ -511,6 +564,7 @@ sleefcu_status launch_masked64(const char *name, const double *x, const uint8_t 
                                sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !mask || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, mask, out)) return rc_;
   using G = sortable_t<F>;
   auto k = k_sorted64<G, 1, true>;
   constexpr int EPT = sort_ept<G>::value;
@@ -522,6 +576,7 @@ sleefcu_status launch_masked64_dual(const char *name, const double *x, const uin
                                     double *o2, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !mask || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, mask, o1, o2)) return rc_;
   using G = sortable_t<F>;
   auto k = k_sorted64<G, 2, true>;
   constexpr int EPT = sort_ept<G>::value;
@@ -533,6 +588,7 @@ sleefcu_status launch_masked64b(const char *name, const double *x, const double 
                                 double *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !y || !mask || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, y, mask, out)) return rc_;
   using G = sortable_t<F>;
   auto k = k_sorted64b<G, true>;
   k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, mask);
@@ -776,6 +832,7 @@ template <class F>
 sleefcu_status launch_unary32(const char *name, const float *x, float *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if constexpr (has_defer<F>::value) {
     if (aligned16(x) && aligned16(out)) {
@@ -797,6 +854,7 @@ template <class F>
 sleefcu_status launch_sorted32(const char *name, const float *x, float *out, size_t n, sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, out)) return rc_;
   auto k = k_sorted32<F>;
   constexpr int EPT = sort_ept<F>::value;
   k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, out, n);
@@ -808,6 +866,7 @@ sleefcu_status launch_binary32(const char *name, const float *x, const float *y,
                                sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, y, out)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if (aligned16(x) && aligned16(y) && aligned16(out)) {
     auto k = k_binary32<F, true>;
@@ -823,6 +882,7 @@ sleefcu_status launch_dual32(const char *name, const float *x, float *o1, float 
                              sleefcu_stream s) {
   if (n == 0) return SLEEFCU_OK;
   if (!x || !o1 || !o2) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
+  if (sleefcu_status rc_ = check_args(name, n, x, o1, o2)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
   if constexpr (has_defer<F>::value) {
     if (aligned16(x) && aligned16(o1) && aligned16(o2)) {

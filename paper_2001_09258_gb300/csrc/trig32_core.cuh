@@ -57,6 +57,7 @@ static __device__ __noinline__ f2 ph(float d, int &q) {
   int e = (int)((bf >> 23) & 0xFF) - 127;
   int sh = e > 64 ? 66 : 2;
   int ex = min(max(e, 0), 127);
+  checked_note(fin && ex != e);         // a finite argument below 2^20 never comes here
   float u = bf ? from_fbits(bf - ((uint32_t)sh << 23)) : 0.0f;   // d * 2^-sh, exact
   float4 T = __ldg(reinterpret_cast<const float4 *>(k_phtab32 + 4 * ex));
   int qq = 0;

@@ -101,6 +101,7 @@ static __device__ __noinline__ d2 ph(double d, int &q) {
   int e = (int)((bf >> 52) & 0x7FF) - 1023;
   int sh = e > 700 ? 130 : 2;
   int ex = min(max(e, 0), 1023);
+  checked_note(fin && ex != e);       // a finite argument below 1e14 never comes here
   double u = bf ? from_bits(bf - ((uint64_t)sh << 52)) : 0.0;   // d * 2^-sh, exact
   const double2 *T = reinterpret_cast<const double2 *>(k_phtab64 + 4 * ex);
   double2 ta = __ldg(T), tb = __ldg(T + 1);

@@ -115,3 +115,18 @@ def test_masked_n_zero_and_null_pointers(name):
     assert f(*([None] * nptr), 0, None) == 0
     assert f(*([None] * nptr), 5, None) == -1
     assert name + "_masked" in sleefcu.last_error()
+
+
+def test_checked_build_exports_every_declared_symbol():
+    """libsleefcu_checked.so (-DSLEEFCU_CHECKED) has the whole interface and
+    says which build it is; the normal build refuses the checked-only query."""
+    L = sleefcu.lib_checked()
+    missing = [n for n in declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert L.sleefcu_is_checked() == 1
+    assert sleefcu.lib().sleefcu_is_checked() == 0
+    assert b"checked" in L.sleefcu_version()
+    c = ctypes.c_ulonglong(7)
+    assert sleefcu.lib().sleefcu_checked_error_count(ctypes.byref(c), 0) == -3
+    assert "checked" in sleefcu.last_error()
+    assert L.sleefcu_checked_error_count(None, 0) == -1

@@ -90,6 +90,15 @@ def test_autotune_and_cache(tmp_path):
     assert b2.config() == cfg
     b2.launch()
     check(items, host)
+    b3 = sleefcu.Batch(items, tune_file=cache)      # tuned inside sleefcu_batch_create
+    assert b3.config() == cfg
+    b3.launch()
+    check(items, host)
+    b4 = sleefcu.Batch(items, tune_file="")         # tuned, no cache file
+    b4.launch(graph=True)
+    check(items, host)
+    for b_ in (b, b2, b3, b4):
+        b_.close()
 
 
 def test_empty_and_bad_items():

@@ -1,7 +1,9 @@
 """The allocation-free batched launch (sleefcu_batch_launch_static): two
 calls in a row on the same arrays give the same bits as a plan's launch,
-and oversize or malformed requests are refused with an error.  Collected
-last so that it also runs after every other GPU test in one session."""
+repeated calls allocate no device memory and return without waiting for the
+stream, and oversize or malformed requests are refused with an error.
+Collected last so that it also runs after every other GPU test in one
+session."""
 import ctypes
 
 import numpy as np
@@ -64,3 +66,40 @@ def test_static_launch_limits():
     nul = sleefcu.BatchItem(0, 0, 10, 0, x.data_ptr(), None, None, None, 8)
     one = (sleefcu.BatchItem * 1)(nul)
     assert L.sleefcu_batch_launch_static(one, 1, st) == -1              # null output with n > 0
+
+
+def test_static_launch_allocates_nothing():
+    """After the first call (which looks up the fixed array's address), more
+    calls leave the device's free memory and the caching allocator's
+    counters unchanged."""
+    import torch
+    names = F64[:4] + F32[:4] + LOWP[:2]
+    items, _ = make_items(names, lengths(len(names), "zb"), "z2")
+    sleefcu.batch_launch_static(items)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        sleefcu.batch_launch_static(items)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    stats1 = torch.cuda.memory_stats()
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
+
+
+def test_static_launch_does_not_wait_for_the_stream():
+    """The descriptors travel as kernel arguments: the call returns while an
+    earlier busy kernel on the same stream is still running."""
+    import torch
+    names = F64[:4] + F32[:2]
+    items, _ = make_items(names, lengths(len(names), "zc"), "z3")
+    sleefcu.batch_launch_static(items)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    torch.cuda._sleep(200_000_000)                 # about 0.1 s of GPU time
+    busy = torch.cuda.Event()
+    busy.record(st)
+    sleefcu.batch_launch_static(items, stream=st)
+    assert not busy.query()
+    torch.cuda.synchronize()
