@@ -92,7 +92,7 @@ __device__ __forceinline__ double ldexp64(double x, int n) {
   if (k >= -1022) return from_bits(sg | (mb + ((uint64_t)(long long)k << 52)));
   int kk = k + 1074;                                        // subnormal: one rounding on the 2^-1074 grid
   if (kk < -1) return from_bits(sg);
-  double r = __dmul_rn(rint(__dmul_rn(from_bits(mb), pow2_64(kk))), 0x1p-1074);
+  double r = dmul(drint(dmul(from_bits(mb), pow2_64(kk))), 0x1p-1074);
   return from_bits(sg | ib(r));
 }
 __device__ __forceinline__ float ldexp32(float x, int n) {
@@ -332,18 +332,18 @@ struct Hypot {
     int e = expo64(ab);
     double as = from_bits(mant64(ab)), b = from_bits(bb), bs;
     if (e >= -1023) {
-      bs = __dmul_rn(b, pow2_64(-e));                          // one rounding at most
+      bs = dmul(b, pow2_64(-e));                          // one rounding at most
     } else {
-      bs = __dmul_rn(__dmul_rn(b, 0x1p64), pow2_64(-e - 64));   // the first product is exact
+      bs = dmul(dmul(b, 0x1p64), pow2_64(-e - 64));   // the first product is exact
     }
     double r;
     if (U05) {
       d2 q = sqrt_d2(add_d2d2_fast(mul_dd(as, as), mul_dd(bs, bs)));
       r = __dadd_rn(q.x, q.y);
     } else {
-      r = __dsqrt_rn(__fma_rn(as, as, __dmul_rn(bs, bs)));
+      r = __dsqrt_rn(__fma_rn(as, as, dmul(bs, bs)));
     }
-    return __dmul_rn(r, pow2_64(e));                           // one rounding at most
+    return dmul(r, pow2_64(e));                           // one rounding at most
   }
   __device__ float operator()(float x, float y) const {
     uint32_t ax = ibf(x) & ABS32, ay = ibf(y) & ABS32;
@@ -400,7 +400,7 @@ struct Sincospi {
     double s = 0.0;
     int o = 0;
     if (ab < 0x4340000000000000ull) {                          // |x| < 2^53: x = q/2 + s exactly
-      double q = rint(__dadd_rn(x, x));
+      double q = drint(__dadd_rn(x, x));
       o = low2_of_int(q);
       s = __fma_rn(-0.5, q, x);
     }
@@ -413,20 +413,20 @@ struct Sincospi {
     double v;
     if (U05) {
       bool tiny = !c && (ib(s) & ABS64) < 0x20B0000000000000ull;   // |s| < 2^-500
-      if (tiny) s = __dmul_rn(s, 0x1p200);
+      if (tiny) s = dmul(s, 0x1p200);
       d2 t = mul_dd(s, s);
       double p = poly(t.x, pc);
-      d2 P = add_dd(k2, __dmul_rn(t.x, p));
+      d2 P = add_dd(k2, dmul(t.x, p));
       P = add_d2d2(c ? D2(CK1, 0.0) : D2(SK1H, SK1L), mul_d2d2(t, P));
       P = add_d2d2(c ? D2(CK0H, CK0L) : D2(SK0H, SK0L), mul_d2d2(t, P));
       d2 r = c ? add_d_d2(1.0, mul_d2d2(t, P)) : mul_d2_d(P, s);
       v = __dadd_rn(r.x, r.y);
-      if (tiny) v = __dmul_rn(v, 0x1p-200);
+      if (tiny) v = dmul(v, 0x1p-200);
     } else {
-      double t = __dmul_rn(s, s);
+      double t = dmul(s, s);
       double p = poly(t, pc);
       double P = __fma_rn(t, __fma_rn(t, __fma_rn(t, p, k2), c ? CK1 : SK1H), c ? CK0H : SK0H);
-      v = c ? __fma_rn(t, P, 1.0) : __dmul_rn(s, P);
+      v = c ? __fma_rn(t, P, 1.0) : dmul(s, P);
     }
     v = neg_if(v, o & 2);
     // zero results: sinpi(n) = +-0 with the sign of n, cospi(n + 1/2) = +0

@@ -56,7 +56,7 @@ __device__ __forceinline__ double copysign_b(double y, uint64_t bx) {
 }
 // e^t - 1 for |t| <= ln2/2, polynomial fitted relative to e^t - 1, one rounding
 __device__ __forceinline__ double em1_r_u35(double t) {
-  return __fma_rn(__dmul_rn(t, t), poly(t, kExpm1U35), t);
+  return __fma_rn(dmul(t, t), poly(t, kExpm1U35), t);
 }
 // 2^k s + (2^k - 1) as a DD (k <= 1000), 2^k - 1 formed exactly by TwoSum
 __device__ __forceinline__ d2 em1_join(d2 s, double k) {
@@ -65,7 +65,7 @@ __device__ __forceinline__ d2 em1_join(d2 s, double k) {
 }
 // k and e^r - 1 in double for the u35 forms
 __device__ __forceinline__ double em1_u35(double xc, double &k) {
-  k = rint(__dmul_rn(xc, R_LN2));
+  k = drint(dmul(xc, R_LN2));
   double r = __fma_rn(k, -L2B, __fma_rn(k, -L2A, xc));
   return em1_r_u35(r);
 }
@@ -74,7 +74,7 @@ __device__ __forceinline__ d2 log_dd(d2 a) {
   int e;
   d2 lm = logm_u10(a, e);
   double ed = dbl_of(e);
-  return add_d2d2(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), lm);
+  return add_d2d2(D2(dmul(ed, L2H), dmul(ed, L2L)), lm);
 }
 
 // ---------------- exp2, exp10 ----------------
@@ -87,7 +87,7 @@ struct Exp2U10 {
     uint64_t b = bits(x);
     bool inr = (b & ABS64) <= B1100;
     double xc = inr ? x : 0.0;
-    double k = rint(xc);
+    double k = drint(xc);
     d2 t = mul_d2_d(D2(L2A, L2B), __dsub_rn(xc, k));
     return exp_out(b, inr, exp_tail_u10(t.x, t.y, int_of(k)));
   }
@@ -97,8 +97,8 @@ struct Exp2U35 {
     uint64_t b = bits(x);
     bool inr = (b & ABS64) <= B1100;
     double xc = inr ? x : 0.0;
-    double k = rint(xc);
-    double t = __dmul_rn(__dsub_rn(xc, k), L2A);
+    double k = drint(xc);
+    double t = dmul(__dsub_rn(xc, k), L2A);
     return exp_out(b, inr, scale2(__dadd_rn(1.0, em1_r_u35(t)), int_of(k)));
   }
 };
@@ -107,7 +107,7 @@ struct Exp10U10 {
     uint64_t b = bits(x);
     bool inr = (b & ABS64) <= B350;
     double xc = inr ? x : 0.0;
-    double k = rint(__dmul_rn(xc, LOG2_10));
+    double k = drint(dmul(xc, LOG2_10));
     double h = __fma_rn(k, -L10A, xc);
     double r = __fma_rn(k, -L10B, h);
     double rl = __fma_rn(k, -L10B, __dsub_rn(h, r));
@@ -120,9 +120,9 @@ struct Exp10U35 {
     uint64_t b = bits(x);
     bool inr = (b & ABS64) <= B350;
     double xc = inr ? x : 0.0;
-    double k = rint(__dmul_rn(xc, LOG2_10));
+    double k = drint(dmul(xc, LOG2_10));
     double r = __fma_rn(k, -L10B, __fma_rn(k, -L10A, xc));
-    return exp_out(b, inr, scale2(__dadd_rn(1.0, em1_r_u35(__dmul_rn(r, LN10H))), int_of(k)));
+    return exp_out(b, inr, scale2(__dadd_rn(1.0, em1_r_u35(dmul(r, LN10H))), int_of(k)));
   }
 };
 
@@ -200,7 +200,7 @@ struct Log10U10 {
     d2 lm = logm_u10(D2(log_arg(b), 0.0), e);
     d2 p = mul_d2d2(lm, D2(RL10H, RL10L));
     double ed = dbl_of(e);
-    d2 r = add_d2d2(D2(__dmul_rn(ed, LG2H), __dmul_rn(ed, LG2L)), p);
+    d2 r = add_d2d2(D2(dmul(ed, LG2H), dmul(ed, LG2L)), p);
     return log_out(b, __dadd_rn(r.x, r.y));
   }
 };
@@ -209,7 +209,7 @@ struct Log10U35 {
     uint64_t b = bits(x);
     int e;
     d2 lm = logm_u10(D2(log_arg(b), 0.0), e);
-    return log_out(b, __fma_rn(dbl_of(e), L10A, __dmul_rn(__dadd_rn(lm.x, lm.y), RL10H)));
+    return log_out(b, __fma_rn(dbl_of(e), L10A, dmul(__dadd_rn(lm.x, lm.y), RL10H)));
   }
 };
 __device__ __forceinline__ double log1p_out(double x, double y) {
@@ -245,28 +245,28 @@ __device__ __forceinline__ double cbrt_core(double x) {
   bool fin = ab - 1 < INF - 1;                     // finite and non-zero
   double a0 = fin ? from_bits(ab) : 1.0;
   int off = 0;
-  if (bits(a0) < 0x0010000000000000ull) { a0 = __dmul_rn(a0, 0x1p54); off = 18; }   // a0 > 0
+  if (bits(a0) < 0x0010000000000000ull) { a0 = dmul(a0, 0x1p54); off = 18; }   // a0 > 0
   uint64_t b0 = bits(a0);
   int e = (int)(b0 >> 52) - 1023;
   int q = e >= 0 ? e / 3 : -((2 - e) / 3);
   int i = e - 3 * q;
   double m = from_bits((b0 & 0x000FFFFFFFFFFFFFull) | ONE);     // [1, 2)
-  double a = __dmul_rn(m, pow2i(i));                             // [1, 8)
+  double a = dmul(m, pow2i(i));                             // [1, 8)
   double c = i == 0 ? 1.0 : (i == 1 ? CBRT_C1 : CBRT_C2);
-  double z = __dmul_rn(poly(__dsub_rn(m, 1.5), kCbrt), c);
-  double z3 = __dmul_rn(__dmul_rn(z, z), z);
-  z = __fma_rn(__dmul_rn(z, __fma_rn(-a, z3, 1.0)), THIRD, z);   // Newton for a^(-1/3)
-  double zz = __dmul_rn(z, z);
-  double y = __dmul_rn(a, zz);
+  double z = dmul(poly(__dsub_rn(m, 1.5), kCbrt), c);
+  double z3 = dmul(dmul(z, z), z);
+  z = __fma_rn(dmul(z, __fma_rn(-a, z3, 1.0)), THIRD, z);   // Newton for a^(-1/3)
+  double zz = dmul(z, z);
+  double y = dmul(a, zz);
   double d;
   if (U10) {
     d2 y3 = mul_d2_d(mul_dd(y, y), y);
     d = __dadd_rn(__dsub_rn(y3.x, a), y3.y);
   } else {
-    d = __fma_rn(__dmul_rn(y, y), y, -a);
+    d = __fma_rn(dmul(y, y), y, -a);
   }
-  y = __fma_rn(-d, __dmul_rn(zz, THIRD), y);                    // Newton for a^(1/3)
-  y = __dmul_rn(y, pow2i(q - off));
+  y = __fma_rn(-d, dmul(zz, THIRD), y);                    // Newton for a^(1/3)
+  y = dmul(y, pow2i(q - off));
   if (!fin) y = __dadd_rn(x, x);
   return canon(copysign_b(y, bx));
 }
@@ -295,7 +295,7 @@ struct SinhU10 {
       d2 em = em1_join(s, k);
       d2 f = div_d2d2(em, add_d_d2(1.0, em));
       d2 h = add_d2d2(em, f);
-      y = __dmul_rn(0.5, __dadd_rn(h.x, h.y));
+      y = dmul(0.5, __dadd_rn(h.x, h.y));
     }
     if (ab < BM28) y = from_bits(ab);
     if (ab > B711) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
@@ -317,7 +317,7 @@ struct CoshU10 {
     } else {
       d2 E = scale_d2(e, pow2i(int_of(k)));
       d2 h = add_d2d2_fast(E, rec_d2(E));
-      y = __dmul_rn(0.5, __dadd_rn(h.x, h.y));
+      y = dmul(0.5, __dadd_rn(h.x, h.y));
     }
     if (ab > B711) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
     return canon(y);
@@ -351,7 +351,7 @@ struct SinhU35 {
     } else {
       double p = pow2i(int_of(k));
       double em = __fma_rn(p, v, __dsub_rn(p, 1.0));
-      y = __dmul_rn(0.5, __dadd_rn(em, __dmul_rn(em, __ddiv_rn(1.0, __dadd_rn(em, 1.0)))));
+      y = dmul(0.5, __dadd_rn(em, dmul(em, __ddiv_rn(1.0, __dadd_rn(em, 1.0)))));
     }
     if (ab < BM28) y = from_bits(ab);
     if (ab > B711) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
@@ -370,8 +370,8 @@ struct CoshU35 {
     if (bits(ac) > 0x4036000000000000ull) {   // ac > 22
       y = scale2(__dadd_rn(1.0, v), int_of(k) - 1);
     } else {
-      double E = __dmul_rn(__dadd_rn(1.0, v), pow2i(int_of(k)));
-      y = __dmul_rn(0.5, __dadd_rn(E, __ddiv_rn(1.0, E)));
+      double E = dmul(__dadd_rn(1.0, v), pow2i(int_of(k)));
+      y = dmul(0.5, __dadd_rn(E, __ddiv_rn(1.0, E)));
     }
     if (ab > B711) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
     return canon(y);
@@ -385,7 +385,7 @@ struct TanhU35 {
     double v = em1_u35(__dadd_rn(ac, ac), k);
     double p = pow2i(int_of(k));
     double em = __fma_rn(p, v, __dsub_rn(p, 1.0));
-    double y = __dmul_rn(em, __ddiv_rn(1.0, __dadd_rn(em, 2.0)));
+    double y = dmul(em, __ddiv_rn(1.0, __dadd_rn(em, 2.0)));
     if (ab < BM28) y = from_bits(ab);
     if (ab > B20) y = is_nan_b(bx) ? from_bits(QNAN64) : 1.0;
     return canon(copysign_b(y, bx));
@@ -444,7 +444,7 @@ struct AtanhU10 {
     double ac = ab < ONE ? from_bits(ab) : 0.5;
     d2 q = div_d2d2(add_dd(1.0, ac), add_dd(1.0, -ac));
     d2 r = log_dd(q);
-    double y = __dmul_rn(0.5, __dadd_rn(r.x, r.y));
+    double y = dmul(0.5, __dadd_rn(r.x, r.y));
     if (ab < BM28) y = from_bits(ab);
     if (ab >= ONE) y = ab == ONE ? from_bits(INF) : from_bits(QNAN64);
     return canon(copysign_b(y, bx));
@@ -506,7 +506,7 @@ __device__ __forceinline__ d2 neg_d2(d2 a) { return D2(-a.x, -a.y); }
 __device__ __forceinline__ d2 erf_s(double a) {
   d2 T = mul_dd(a, a);
   double p = poly_p<10>(T.x, kErfP + 1);
-  d2 in = add_dd(kErfP[0], __dmul_rn(T.x, p));
+  d2 in = add_dd(kErfP[0], dmul(T.x, p));
   in = add_d2d2(D2(kErfH[2], kErfH[3]), mul_d2d2(T, in));
   return add_d2d2(D2(kErfH[0], kErfH[1]), mul_d2d2(T, in));
 }
@@ -521,12 +521,12 @@ __device__ __forceinline__ d2 erfc_F(double a) {
     int i = erfc_iv(a);
     double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
     double p = poly_p<22>(u, kErfcFP[i]);
-    d2 in = add_d2_d(D2(kErfcFH[i][2], kErfcFH[i][3]), __dmul_rn(u, p));
+    d2 in = add_d2_d(D2(kErfcFH[i][2], kErfcFH[i][3]), dmul(u, p));
     return add_d2d2(D2(kErfcFH[i][0], kErfcFH[i][1]), mul_d2_d(in, u));
   }
-  double w = __ddiv_rn(1.0, __dmul_rn(a, a));
+  double w = __ddiv_rn(1.0, dmul(a, a));
   double p = poly_p<9>(w, kErfcGP);
-  d2 in = add_d2_d(D2(kErfcGH[2], kErfcGH[3]), __dmul_rn(w, p));
+  d2 in = add_d2_d(D2(kErfcGH[2], kErfcGH[3]), dmul(w, p));
   d2 g = add_d2d2(D2(kErfcGH[0], kErfcGH[1]), mul_d2_d(in, w));
   return div_d2d2(mul_d2d2(g, D2(RSQPIH, RSQPIL)), D2(a, 0.0));
 }
@@ -539,7 +539,7 @@ __device__ __forceinline__ d2 erfc_core(double a, double &k) {
 // y 2^k by two multiplications with normal powers of two (one rounding)
 __device__ __forceinline__ double scale2_two(double y, int k) {
   int k1 = k / 2, k2 = k - k1;
-  return __dmul_rn(__dmul_rn(y, pow2i(k1)), pow2i(k2));
+  return dmul(dmul(y, pow2i(k1)), pow2i(k2));
 }
 
 struct ErfU10 {
@@ -613,16 +613,16 @@ struct ErfU35 {
     double a = from_bits(bx & ABS64);
     double y;
     if (bits(a) < BE1) {
-      double t = __dmul_rn(a, a);
-      y = __dmul_rn(a, __fma_rn(t, __fma_rn(t, poly(t, kErfP), kErfH[2]), kErfH[0]));
+      double t = dmul(a, a);
+      y = dmul(a, __fma_rn(t, __fma_rn(t, poly(t, kErfP), kErfH[2]), kErfH[0]));
     } else if (bits(a) < BE6) {
       int i = erfc_iv(a);
       double u = __dsub_rn(a, i == 0 ? 1.5 : (i == 1 ? 3.0 : 6.0));
       double F = __fma_rn(u, __fma_rn(u, poly_p<22>(u, kErfcFP[i]), kErfcFH[i][2]), kErfcFH[i][0]);
       d2 Y = mul_dd(a, a);
-      double k = rint(__dmul_rn(-Y.x, R_LN2));
+      double k = drint(dmul(-Y.x, R_LN2));
       double r = __dsub_rn(__fma_rn(k, -L2B, __fma_rn(k, -L2A, -Y.x)), Y.y);
-      double E = __dmul_rn(__dadd_rn(1.0, em1_r_u35(r)), pow2i(int_of(k)));
+      double E = dmul(__dadd_rn(1.0, em1_r_u35(r)), pow2i(int_of(k)));
       y = __fma_rn(-F, E, 1.0);
     } else {
       y = 1.0;

@@ -64,7 +64,7 @@ __device__ __forceinline__ double pow2i(int k) { return from_bits((uint64_t)(k +
 __device__ __forceinline__ double scale2(double y, int k) {
   if (k >= -1021 && k <= 1023) return from_bits(bits(y) + ((uint64_t)(int64_t)k << 52));
   int k1 = k / 2, k2 = k - k1;
-  return __dmul_rn(__dmul_rn(y, pow2i(k1)), pow2i(k2));
+  return dmul(dmul(y, pow2i(k1)), pow2i(k2));
 }
 
 // 2^k for k in [-1074, 1023], normal or subnormal, from the bits
@@ -80,10 +80,10 @@ __device__ __forceinline__ double pow2_any(int k) {
 __device__ __forceinline__ d2 log_mantissa(d2 a, int &ex) {
   ex = (int)(bits(a.x) >> 52) - 1023;
   uint64_t hb = (bits(a.x) & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
-  double t = __dmul_rn(a.y, pow2_any(-ex));
+  double t = dmul(a.y, pow2_any(-ex));
   if (hb >= 0x3FF8000000000000ull) {
     hb -= 0x0010000000000000ull;
-    t = __dmul_rn(t, 0.5);
+    t = dmul(t, 0.5);
     ex++;
   }
   return D2(from_bits(hb), t);
@@ -93,7 +93,7 @@ __device__ __forceinline__ d2 log_mantissa(d2 a, int &ex) {
 // joins the polynomial part and 1 + r is a DD, so the last addition is the
 // only rounding of order one ulp (Section 5.6)
 __device__ __forceinline__ double exp_tail_u10(double r, double rl, int k) {
-  double s = __dmul_rn(r, r);
+  double s = dmul(r, r);
   double w = __fma_rn(s, poly(r, kExpU10), rl);
   d2 o = add_dd_fast(1.0, r);
   return scale2(__dadd_rn(o.x, __dadd_rn(o.y, w)), k);
@@ -103,12 +103,12 @@ __device__ __forceinline__ double exp_tail_u10(double r, double rl, int k) {
 // head Y.x - k L2A is exact (k has at most 11 bits and the result is below
 // 1/2), so the reduced argument is a DD to about 2^-100.
 __device__ __forceinline__ d2 expk_s(d2 Y, double &k) {
-  k = rint(__dmul_rn(Y.x, R_LN2));
+  k = drint(dmul(Y.x, R_LN2));
   double u = __fma_rn(k, -L2A, Y.x);
   d2 r = add_dd(u, __fma_rn(k, -L2B, Y.y));
   d2 q = scale_d2(sqr_d2(r), 0.5);
   double p = poly(r.x, kPowExp);
-  double v = __dmul_rn(__dmul_rn(__dmul_rn(r.x, r.x), r.x), p);
+  double v = dmul(dmul(dmul(r.x, r.x), r.x), p);
   d2 s = add_d2d2(r, q);
   return add_d2_d(s, v);
 }
@@ -137,8 +137,8 @@ __device__ __forceinline__ d2 logm_u10(d2 a, int &e) {
   d2 num = scale_d2(add_dd(__dsub_rn(m.x, 1.0), m.y), 2.0);
   d2 den = add_d_d2(1.0, m);
   d2 z = div_d2d2(num, den);
-  double t = __dmul_rn(z.x, z.x);
-  double corr = __dmul_rn(__dmul_rn(z.x, t), poly(t, kLogU10));
+  double t = dmul(z.x, z.x);
+  double corr = dmul(dmul(z.x, t), poly(t, kLogU10));
   e = ex - off;
   return add_d2_d_fast(z, corr);
 }
@@ -149,11 +149,11 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
   int ex;
   d2 m = log_mantissa(a, ex);
-  double num = __dmul_rn(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
-  double z = __dmul_rn(num, __ddiv_rn(1.0, __dadd_rn(1.0, m.x)));
-  double t = __dmul_rn(z, z);
+  double num = dmul(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
+  double z = dmul(num, __ddiv_rn(1.0, __dadd_rn(1.0, m.x)));
+  double t = dmul(z, z);
   e = ex - off;
-  return __fma_rn(__dmul_rn(z, t), poly(t, kLogU35), z);
+  return __fma_rn(dmul(z, t), poly(t, kLogU35), z);
 }
 
 // log of a DD y > 0 with the 11-term DD polynomial of pow's logarithm
@@ -168,12 +168,12 @@ __device__ __forceinline__ d2 logk_dd(d2 y) {
   d2 z = div_d2d2(num, add_d_d2(1.0, m));
   d2 t = sqr_d2(z);
   double q = poly(t.x, kPowLog);
-  d2 w = add_d2_d_fast(D2(PL_C1H, PL_C1L), __dmul_rn(t.x, q));
+  d2 w = add_d2_d_fast(D2(PL_C1H, PL_C1L), dmul(t.x, q));
   w = mul_d2d2(t, w);
   w = mul_d2d2(z, w);
   d2 lm = add_d2d2_fast(z, w);
   double ed = dbl_of(ex - off);
-  return add_d2d2(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), lm);
+  return add_d2d2(D2(dmul(ed, L2H), dmul(ed, L2L)), lm);
 }
 
 }  // namespace explog64

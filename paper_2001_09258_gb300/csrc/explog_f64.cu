@@ -20,10 +20,10 @@ __device__ __forceinline__ double exp_core(double x, const double (&c)[N]) {
   uint64_t b = bits(x), ab = b & ABS64;
   bool inr = ab <= B746;
   double xc = inr ? x : 0.0;
-  double k = rint(__dmul_rn(xc, R_LN2));
+  double k = drint(dmul(xc, R_LN2));
   double r = __fma_rn(k, -L2A, xc);
   r = __fma_rn(k, -L2B, r);
-  double s = __dmul_rn(r, r);
+  double s = dmul(r, r);
   double v = __fma_rn(s, poly(r, c), r);
   double y = scale2(__dadd_rn(1.0, v), int_of(k));
   if (!inr) y = is_nan_b(b) ? from_bits(QNAN64) : ((b >> 63) ? 0.0 : from_bits(INF));
@@ -34,7 +34,7 @@ __device__ __forceinline__ double exp_core_u10(double x) {
   uint64_t b = bits(x), ab = b & ABS64;
   bool inr = ab <= B746;
   double xc = inr ? x : 0.0;
-  double k = rint(__dmul_rn(xc, R_LN2));
+  double k = drint(dmul(xc, R_LN2));
   double h = __fma_rn(k, -L2A, xc);
   double r = __fma_rn(k, -L2B, h);
   double rl = __fma_rn(k, -L2B, __dsub_rn(h, r));
@@ -49,7 +49,7 @@ struct ExpU35 { __device__ double operator()(double x) const { return exp_core(x
 __device__ __forceinline__ double log_reduce(uint64_t a, int &e) {
   int off = 0;
   if (a < 0x0010000000000000ull) {                // subnormal: scale by 2^64 (exact)
-    a = bits(__dmul_rn(from_bits(a), 0x1p64));
+    a = bits(dmul(from_bits(a), 0x1p64));
     off = 64;
   }
   int ex = (int)(a >> 52) - 1023;
@@ -72,11 +72,11 @@ struct LogU10 {
     int e;
     double m = log_reduce(a, e);
     d2 den = add_dd_fast(1.0, m);
-    d2 z = div_d2d2(D2(__dmul_rn(2.0, __dsub_rn(m, 1.0)), 0.0), den);
-    double t = __dmul_rn(z.x, z.x);
-    double corr = __dmul_rn(__dmul_rn(z.x, t), poly(t, kLogU10));
+    d2 z = div_d2d2(D2(dmul(2.0, __dsub_rn(m, 1.0)), 0.0), den);
+    double t = dmul(z.x, z.x);
+    double corr = dmul(dmul(z.x, t), poly(t, kLogU10));
     double ed = dbl_of(e);
-    d2 r = add_d2d2_fast(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), z);
+    d2 r = add_d2d2_fast(D2(dmul(ed, L2H), dmul(ed, L2L)), z);
     r = add_d2_d_fast(r, corr);
     return canon(log_special(b, __dadd_rn(r.x, r.y)));
   }
@@ -87,9 +87,9 @@ struct LogU35 {
     uint64_t a = (b - 1) < DMAX ? b : 0x3FF0000000000000ull;
     int e;
     double m = log_reduce(a, e);
-    double z = __dmul_rn(__dmul_rn(2.0, __dsub_rn(m, 1.0)), __ddiv_rn(1.0, __dadd_rn(1.0, m)));
-    double t = __dmul_rn(z, z);
-    double lm = __fma_rn(__dmul_rn(z, t), poly(t, kLogU35), z);
+    double z = dmul(dmul(2.0, __dsub_rn(m, 1.0)), __ddiv_rn(1.0, __dadd_rn(1.0, m)));
+    double t = dmul(z, z);
+    double lm = __fma_rn(dmul(z, t), poly(t, kLogU35), z);
     return canon(log_special(b, __fma_rn(dbl_of(e), L2A, lm)));
   }
 };
@@ -99,15 +99,15 @@ __device__ __forceinline__ d2 logk(uint64_t a) {
   int e;
   double m = log_reduce(a, e);
   d2 den = add_dd_fast(1.0, m);
-  d2 z = div_d2d2(D2(__dmul_rn(2.0, __dsub_rn(m, 1.0)), 0.0), den);
+  d2 z = div_d2d2(D2(dmul(2.0, __dsub_rn(m, 1.0)), 0.0), den);
   d2 t = sqr_d2(z);
   double q = poly(t.x, kPowLog);
-  d2 w = add_d2_d_fast(D2(PL_C1H, PL_C1L), __dmul_rn(t.x, q));
+  d2 w = add_d2_d_fast(D2(PL_C1H, PL_C1L), dmul(t.x, q));
   w = mul_d2d2(t, w);
   w = mul_d2d2(z, w);
   d2 lm = add_d2d2_fast(z, w);
   double ed = dbl_of(e);
-  return add_d2d2_fast(D2(__dmul_rn(ed, L2H), __dmul_rn(ed, L2L)), lm);
+  return add_d2d2_fast(D2(dmul(ed, L2H), dmul(ed, L2L)), lm);
 }
 
 struct PowU10 {

@@ -60,14 +60,14 @@ constexpr uint64_t G1015 = 0x7F60000000000000ull, G52 = 0x4330000000000000ull, G
 // lgamma(2 + e), -0.25 <= e < 0.5
 __device__ __forceinline__ d2 lg_r2(d2 e) {
   double p = poly_p<16>(e.x, kLgR2P);
-  d2 in = add_d2_d(D2(kLgR2H[2], kLgR2H[3]), __dmul_rn(e.x, p));
+  d2 in = add_d2_d(D2(kLgR2H[2], kLgR2H[3]), dmul(e.x, p));
   in = add_d2d2(D2(kLgR2H[0], kLgR2H[1]), mul_d2d2(in, e));
   return mul_d2d2(in, e);
 }
 // lgamma(1.5 + u), -0.25 <= u < 0.25
 __device__ __forceinline__ d2 lg_m(d2 u) {
   double p = poly_p<15>(u.x, kLgMP);
-  d2 in = add_d2_d(D2(kLgMH[4], kLgMH[5]), __dmul_rn(u.x, p));
+  d2 in = add_d2_d(D2(kLgMH[4], kLgMH[5]), dmul(u.x, p));
   in = add_d2d2(D2(kLgMH[2], kLgMH[3]), mul_d2d2(in, u));
   return add_d2d2(D2(kLgMH[0], kLgMH[1]), mul_d2d2(in, u));
 }
@@ -81,8 +81,8 @@ __device__ __forceinline__ d2 lg_stirling(d2 y) {
   if (bits(y.x) >= G60) return r;
   r = add_d2d2(r, D2(LOG2PI_H, LOG2PI_L));
   double ry = __ddiv_rn(1.0, y.x);            // one reciprocal: w = 1/y^2 and G(w)/y
-  double w = __dmul_rn(ry, ry);
-  return add_d2_d(r, __dmul_rn(poly(w, kLgSt), ry));
+  double w = dmul(ry, ry);
+  return add_d2_d(r, dmul(poly(w, kLgSt), ry));
 }
 // lgamma of a DD y > 0
 __device__ __forceinline__ d2 lgamma_pos(d2 y) {
@@ -105,11 +105,11 @@ __device__ __forceinline__ d2 lgamma_pos(d2 y) {
 }
 // sin(pi x) as a DD, |x| < 2^52
 __device__ __forceinline__ d2 sinpi_dd(double x) {
-  double r = __dsub_rn(x, __dmul_rn(2.0, rint(__dmul_rn(0.5, x))));
+  double r = __dsub_rn(x, dmul(2.0, drint(dmul(0.5, x))));
   double s = okey(r) > okey(0.5) ? __dsub_rn(1.0, r) : (okey(r) < okey(-0.5) ? __dsub_rn(-1.0, r) : r);
   d2 T = mul_dd(s, s);
   double p = poly_p<11>(T.x, kSpP);
-  d2 in = add_d2_d(D2(kSpH[0], kSpH[1]), __dmul_rn(T.x, p));
+  d2 in = add_d2_d(D2(kSpH[0], kSpH[1]), dmul(T.x, p));
   in = add_d2d2(D2(PI_H, PI_L), mul_d2d2(T, in));
   return mul_d2_d(in, s);
 }
@@ -169,7 +169,7 @@ __device__ __forceinline__ double scale2_any(double y, int k) {
   if (e > 1023) return from_bits(INF);
   if (e >= -1022) return from_bits(bits(y) + ((uint64_t)(int64_t)k << 52));
   const int k1 = k / 2, k2 = k - k1;
-  return __dmul_rn(__dmul_rn(y, pow2i(k1)), pow2i(k2));
+  return dmul(dmul(y, pow2i(k1)), pow2i(k2));
 }
 constexpr uint64_t G2M900 = 0x07B0000000000000ull;   // 2^-900
 
@@ -189,7 +189,7 @@ struct TgammaU10 {
     // |x| < 2^-900 sin(pi x) = pi x is formed from x 2^200 (full precision
     // where pi x would be subnormal) and 2^-200 rejoins 2^k
     const int up = (bx & ABS64) < G2M900 ? 200 : 0;
-    d2 sp = up ? mul_d2_d(D2(PI_H, PI_L), __dmul_rn(x, 0x1p200)) : sinpi_dd(x);
+    d2 sp = up ? mul_d2_d(D2(PI_H, PI_L), dmul(x, 0x1p200)) : sinpi_dd(x);
     const bool negs = lt_0(sp.x);
     d2 d = D2(fabs(sp.x), negs ? -sp.y : sp.y);
     d2 g = lgamma_pos(add_dd(1.0, -x));

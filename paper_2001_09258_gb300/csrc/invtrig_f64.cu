@@ -47,7 +47,7 @@ __device__ __forceinline__ double copysign_b(double v, uint64_t sgn_src) {
 __device__ __forceinline__ d2 sqrt_dd(double t) {
   double h = __dsqrt_rn(t);
   double r = __fma_rn(-h, h, t);
-  double lo = __dmul_rn(r, __ddiv_rn(1.0, __dadd_rn(h, h)));
+  double lo = dmul(r, __ddiv_rn(1.0, __dadd_rn(h, h)));
   return D2(h, (bits(h) & ABS64) != 0 ? lo : 0.0);
 }
 
@@ -56,12 +56,12 @@ __device__ __forceinline__ d2 asin_core_u10(double ax, bool big) {
   double t;
   if (!big) {
     u = D2(ax, 0.0);
-    t = __dmul_rn(ax, ax);
+    t = dmul(ax, ax);
   } else {
-    t = __dmul_rn(__dsub_rn(1.0, ax), 0.5);
+    t = dmul(__dsub_rn(1.0, ax), 0.5);
     u = sqrt_dd(t);
   }
-  double corr = __dmul_rn(__dmul_rn(u.x, t), poly(t, kAsinU10));
+  double corr = dmul(dmul(u.x, t), poly(t, kAsinU10));
   return add_d2_d_fast(u, corr);
 }
 // a square root the compiler cannot hoist out of its branch: inlined, the
@@ -73,12 +73,12 @@ __device__ __forceinline__ double asin_core_u35(double ax, bool big) {
   double u, t;
   if (!big) {
     u = ax;
-    t = __dmul_rn(ax, ax);
+    t = dmul(ax, ax);
   } else {
-    t = __dmul_rn(__dsub_rn(1.0, ax), 0.5);
+    t = dmul(__dsub_rn(1.0, ax), 0.5);
     u = sqrt_branch(t);
   }
-  return __fma_rn(__dmul_rn(u, t), poly(t, kAsinU10), u);
+  return __fma_rn(dmul(u, t), poly(t, kAsinU10), u);
 }
 
 #define ASIN_CLASSES                     \
@@ -132,7 +132,7 @@ struct AcosU35 {
     bool big = ab > HALF, neg = (b >> 63) && ab != 0;
     double r = asin_core_u35(from_bits(ab), big), y;
     if (!big) y = __dadd_rn(__dsub_rn(PIO2H, copysign_b(r, b)), PIO2L);
-    else if (!neg) y = __dmul_rn(2.0, r);
+    else if (!neg) y = dmul(2.0, r);
     else y = __dadd_rn(__fma_rn(-2.0, r, PIH), PIL);
     if (ab > ONE) y = from_bits(QNAN64);
     return canon(y);
@@ -143,14 +143,14 @@ struct AcosU35 {
 __device__ __forceinline__ d2 atan_core_u10(d2 s) {
   d2 t = sqr_d2(s);
   double p = poly(t.x, kAtanU10);
-  d2 w = add_d2_d_fast(D2(AT_C1H, AT_C1L), __dmul_rn(t.x, p));
+  d2 w = add_d2_d_fast(D2(AT_C1H, AT_C1L), dmul(t.x, p));
   w = mul_d2d2(t, w);
   w = mul_d2d2(s, w);
   return add_d2d2_fast(s, w);
 }
 __device__ __forceinline__ double atan_core_u35(double s) {
-  double t = __dmul_rn(s, s);
-  return __fma_rn(__dmul_rn(s, t), poly(t, kAtanU35), s);
+  double t = dmul(s, s);
+  return __fma_rn(dmul(s, t), poly(t, kAtanU35), s);
 }
 
 #define ATAN_CLASSES                     \
@@ -210,8 +210,8 @@ struct Atan2U10 {
     uint64_t num = swap ? ab : aa, den = swap ? aa : ab;
     if (!((den - 1) < DMAX) || !(num <= den)) { num = 0; den = ONE; }
     double fn = from_bits(num), fd = from_bits(den);
-    if (den < 0x0170000000000000ull) { fn = __dmul_rn(fn, 0x1p600); fd = __dmul_rn(fd, 0x1p600); }
-    if (den > 0x7E70000000000000ull) { fn = __dmul_rn(fn, 0x1p-600); fd = __dmul_rn(fd, 0x1p-600); }
+    if (den < 0x0170000000000000ull) { fn = dmul(fn, 0x1p600); fd = dmul(fd, 0x1p600); }
+    if (den > 0x7E70000000000000ull) { fn = dmul(fn, 0x1p-600); fd = dmul(fd, 0x1p-600); }
     d2 s = div_d2d2(D2(fn, 0.0), D2(fd, 0.0));
     d2 r = atan_core_u10(s);
     if (swap) r = add_d2d2_fast(D2(PIO2H, PIO2L), D2(-r.x, -r.y));
@@ -231,9 +231,9 @@ struct Atan2U35 {
     uint64_t num = swap ? ab : aa, den = swap ? aa : ab;
     if (!((den - 1) < DMAX) || !(num <= den)) { num = 0; den = ONE; }
     double fn = from_bits(num), fd = from_bits(den);
-    if (den < 0x0170000000000000ull) { fn = __dmul_rn(fn, 0x1p600); fd = __dmul_rn(fd, 0x1p600); }
-    if (den > 0x7E70000000000000ull) { fn = __dmul_rn(fn, 0x1p-600); fd = __dmul_rn(fd, 0x1p-600); }
-    double r = atan_core_u35(__dmul_rn(fn, __ddiv_rn(1.0, fd)));
+    if (den < 0x0170000000000000ull) { fn = dmul(fn, 0x1p600); fd = dmul(fd, 0x1p600); }
+    if (den > 0x7E70000000000000ull) { fn = dmul(fn, 0x1p-600); fd = dmul(fd, 0x1p-600); }
+    double r = atan_core_u35(dmul(fn, __ddiv_rn(1.0, fd)));
     if (swap) r = __dsub_rn(PIO2H, r);
     bool bneg = (bb >> 63) && ab != 0 && ab <= INF;
     if (bneg) r = __dsub_rn(PIH, r);

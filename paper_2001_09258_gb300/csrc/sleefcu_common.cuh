@@ -143,10 +143,10 @@ template <int N>
 __device__ __forceinline__ double poly(double t, const double (&c)[N]) {
   double pw[5];
   pw[0] = t;
-  if (N > 2) pw[1] = __dmul_rn(t, t);
-  if (N > 4) pw[2] = __dmul_rn(pw[1], pw[1]);
-  if (N > 8) pw[3] = __dmul_rn(pw[2], pw[2]);
-  if (N > 16) pw[4] = __dmul_rn(pw[3], pw[3]);
+  if (N > 2) pw[1] = dmul(t, t);
+  if (N > 4) pw[2] = dmul(pw[1], pw[1]);
+  if (N > 8) pw[3] = dmul(pw[2], pw[2]);
+  if (N > 16) pw[4] = dmul(pw[3], pw[3]);
   return Estrin<N>::d(c, pw);
 }
 // the same for N coefficients starting at c (a row of a table)
@@ -154,10 +154,10 @@ template <int N>
 __device__ __forceinline__ double poly_p(double t, const double *c) {
   double pw[5];
   pw[0] = t;
-  if (N > 2) pw[1] = __dmul_rn(t, t);
-  if (N > 4) pw[2] = __dmul_rn(pw[1], pw[1]);
-  if (N > 8) pw[3] = __dmul_rn(pw[2], pw[2]);
-  if (N > 16) pw[4] = __dmul_rn(pw[3], pw[3]);
+  if (N > 2) pw[1] = dmul(t, t);
+  if (N > 4) pw[2] = dmul(pw[1], pw[1]);
+  if (N > 8) pw[3] = dmul(pw[2], pw[2]);
+  if (N > 16) pw[4] = dmul(pw[3], pw[3]);
   return Estrin<N>::d(c, pw);
 }
 template <int N>
@@ -262,6 +262,12 @@ template <class F, class = void>
 struct sort_ept { static constexpr int value = kSortEPT; };
 template <class F>
 struct sort_ept<F, std::void_t<decltype(F::SORT_EPT)>> { static constexpr int value = F::SORT_EPT; };
+// resident blocks per SM the sorted kernel of F is compiled for (its
+// register budget): F::MIN_BLOCKS if given, else 1
+template <class F, class = void>
+struct sort_minb { static constexpr int value = 1; };
+template <class F>
+struct sort_minb<F, std::void_t<decltype(F::MIN_BLOCKS)>> { static constexpr int value = F::MIN_BLOCKS; };
 
 template <int NC, int EPT>
 __device__ __forceinline__ void sort_scatter(const int (&cl)[EPT], int *cur, unsigned short *sidx, int tid) {
@@ -317,7 +323,7 @@ __device__ __forceinline__ void sort_count(const int (&cl)[EPT], int *cnt, int t
 // evaluated (densely, as the tile's sorted prefix) and stored; the other
 // outputs are left untouched (the masked entry points).
 template <class F, int NOUT, bool MASKED = false>
-__global__ void __launch_bounds__(kBlock) k_sorted64(const double *x, double *o1, double *o2, size_t n,
+__global__ void __launch_bounds__(kBlock, sort_minb<F>::value) k_sorted64(const double *x, double *o1, double *o2, size_t n,
                                                      const uint8_t *mask = nullptr) {
   constexpr int NC = F::NCLS, EPT = sort_ept<F>::value, TILE = kBlock * EPT;
   __shared__ double sx[TILE];

@@ -8,8 +8,34 @@
 // IEEE implementation of the same sequence (Section 4, bit-wise consistency).
 #pragma once
 #include <cuda_runtime.h>
+#include "softfp64.cuh"
+
+// Binary64 multiplication and rounding to an integral value in the kernels:
+// exact software forms on the integer pipe (softfp64.cuh), bit-identical to
+// the FP64 pipe's, so that the FP64 pipe, the bottleneck of the FP64 family
+// on GB300, keeps only the additions and fused multiply-adds.  Compiling
+// with -DSLEEFCU_SOFT_MUL=0 issues them to the FP64 pipe instead (same bits).
+#ifndef SLEEFCU_SOFT_MUL
+#define SLEEFCU_SOFT_MUL 1
+#endif
 
 namespace sleefcu {
+
+__device__ __forceinline__ double dmul(double a, double b) {
+#if SLEEFCU_SOFT_MUL
+  return __longlong_as_double((long long)soft::mul((uint64_t)__double_as_longlong(a),
+                                                   (uint64_t)__double_as_longlong(b)));
+#else
+  return __dmul_rn(a, b);
+#endif
+}
+__device__ __forceinline__ double drint(double a) {
+#if SLEEFCU_SOFT_MUL
+  return __longlong_as_double((long long)soft::rint((uint64_t)__double_as_longlong(a)));
+#else
+  return rint(a);
+#endif
+}
 
 struct d2 { double x, y; };   // value x + y
 struct f2 { float x, y; };
@@ -66,22 +92,22 @@ __device__ __forceinline__ d2 add_d2_d(d2 a, double b) {
 }
 // exact product: RN(ab) and the fma residual
 __device__ __forceinline__ d2 mul_dd(double a, double b) {
-  double s = __dmul_rn(a, b);
+  double s = dmul(a, b);
   return D2(s, __fma_rn(a, b, -s));
 }
 __device__ __forceinline__ d2 mul_d2_d(d2 a, double b) {
-  double s = __dmul_rn(a.x, b);
+  double s = dmul(a.x, b);
   return D2(s, __fma_rn(a.y, b, __fma_rn(a.x, b, -s)));
 }
 __device__ __forceinline__ d2 mul_d2d2(d2 a, d2 b) {
-  double s = __dmul_rn(a.x, b.x);
+  double s = dmul(a.x, b.x);
   return D2(s, __fma_rn(a.x, b.y, __fma_rn(a.y, b.x, __fma_rn(a.x, b.x, -s))));
 }
 __device__ __forceinline__ d2 sqr_d2(d2 a) {
-  double s = __dmul_rn(a.x, a.x);
+  double s = dmul(a.x, a.x);
   return D2(s, __fma_rn(__dadd_rn(a.x, a.x), a.y, __fma_rn(a.x, a.x, -s)));
 }
-__device__ __forceinline__ d2 scale_d2(d2 a, double p2) { return D2(__dmul_rn(a.x, p2), __dmul_rn(a.y, p2)); }
+__device__ __forceinline__ d2 scale_d2(d2 a, double p2) { return D2(dmul(a.x, p2), dmul(a.y, p2)); }
 __device__ __forceinline__ d2 norm_d2(d2 a) {
   double s = __dadd_rn(a.x, a.y);
   return D2(s, __dadd_rn(__dsub_rn(a.x, s), a.y));
@@ -89,25 +115,25 @@ __device__ __forceinline__ d2 norm_d2(d2 a) {
 // n / d with a single division
 __device__ __forceinline__ d2 div_d2d2(d2 n, d2 d) {
   double t = __ddiv_rn(1.0, d.x);
-  double q = __dmul_rn(n.x, t);
+  double q = dmul(n.x, t);
   double r = __fma_rn(-q, d.x, n.x);
   r = __fma_rn(-q, d.y, __dadd_rn(r, n.y));
-  return D2(q, __dmul_rn(r, t));
+  return D2(q, dmul(r, t));
 }
 __device__ __forceinline__ d2 rec_d(double d) {
   double t = __ddiv_rn(1.0, d);
-  return D2(t, __dmul_rn(t, __fma_rn(-t, d, 1.0)));
+  return D2(t, dmul(t, __fma_rn(-t, d, 1.0)));
 }
 __device__ __forceinline__ d2 rec_d2(d2 d) {
   double t = __ddiv_rn(1.0, d.x);
   double r = __fma_rn(-t, d.x, 1.0);
   r = __fma_rn(-t, d.y, r);
-  return D2(t, __dmul_rn(r, t));
+  return D2(t, dmul(r, t));
 }
 __device__ __forceinline__ d2 sqrt_d2(d2 a) {
   double h = __dsqrt_rn(a.x);
   double r = __dadd_rn(__fma_rn(-h, h, a.x), a.y);
-  return D2(h, __dmul_rn(r, __ddiv_rn(1.0, __dadd_rn(h, h))));
+  return D2(h, dmul(r, __ddiv_rn(1.0, __dadd_rn(h, h))));
 }
 
 // ---- FF (binary32) ----

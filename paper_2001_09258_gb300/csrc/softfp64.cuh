@@ -11,8 +11,11 @@
 // Every function here takes and returns the bit patterns of binary64 values
 // (uint64_t) and rounds to nearest, ties to even, with subnormal inputs and
 // results (no flush to zero), signed zeros, infinities and NaN as IEEE 754
-// 2008 Section 6 prescribes.  A NaN result is the quiet NaN kNaN (the
-// pattern the device's FP64 pipe produces, so that even NaN bits agree).
+// 2008 Section 6 prescribes.  NaN results follow the GB300 FP64 pipe bit
+// for bit (measured): a NaN operand is returned quieted (bit 51 set, sign
+// and payload kept), choosing b, then c, then a for fma and the second
+// operand, then the first for add and mul; an invalid operation (inf * 0,
+// inf - inf) returns kDefaultNaN; rint returns its NaN argument quieted.
 // The header compiles as plain C++ as well (host functions), which is how
 // the CPU tests pin it against the host processor's hardware fma.
 #pragma once
@@ -20,8 +23,10 @@
 
 #if defined(__CUDACC__)
 #define SFP_HD __host__ __device__ __forceinline__
+#define SFP_COLD static __host__ __device__ __noinline__   // rare general paths: out of line
 #else
 #define SFP_HD static inline
+#define SFP_COLD static
 #endif
 
 namespace sleefcu {
@@ -32,7 +37,8 @@ constexpr uint64_t kExpMask = 0x7FF0000000000000ull;
 constexpr uint64_t kManMask = 0x000FFFFFFFFFFFFFull;
 constexpr uint64_t kHidden = 0x0010000000000000ull;
 constexpr uint64_t kInf = 0x7FF0000000000000ull;
-constexpr uint64_t kNaN = 0x7FFFFFFFFFFFFFFFull;
+constexpr uint64_t kQuiet = 0x0008000000000000ull;
+constexpr uint64_t kDefaultNaN = 0xFFF8000000000000ull;
 
 // ---- primitives with host and device forms ----
 SFP_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
@@ -86,13 +92,15 @@ SFP_HD u128 shl(u128 x, int s) {   // 0 <= s < 128
 SFP_HD int clz128(u128 x) { return x.hi ? clz64(x.hi) : 64 + clz64(x.lo); }
 
 // The NaN/infinity cases of fma(a, b, c) (some operand has exponent 0x7FF)
-SFP_HD uint64_t fma_special(uint64_t a, uint64_t b, uint64_t c) {
+SFP_COLD uint64_t fma_special(uint64_t a, uint64_t b, uint64_t c) {
   uint64_t aa = a & ~kSign, ab = b & ~kSign, ac = c & ~kSign;
-  if (aa > kInf || ab > kInf || ac > kInf) return kNaN;
+  if (ab > kInf) return b | kQuiet;
+  if (ac > kInf) return c | kQuiet;
+  if (aa > kInf) return a | kQuiet;
   uint64_t sp = (a ^ b) & kSign;
   if (aa == kInf || ab == kInf) {
-    if (aa == 0 || ab == 0) return kNaN;                  // inf * 0
-    if (ac == kInf && (c & kSign) != sp) return kNaN;     // inf - inf
+    if (aa == 0 || ab == 0) return kDefaultNaN;           // inf * 0
+    if (ac == kInf && (c & kSign) != sp) return kDefaultNaN;   // inf - inf
     return sp | kInf;
   }
   return c;                                               // finite a*b + inf
@@ -136,7 +144,7 @@ SFP_HD uint64_t fma(uint64_t a, uint64_t b, uint64_t c) {
   if (ea == 0x7FF || eb == 0x7FF || ec == 0x7FF) return fma_special(a, b, c);
   uint64_t sp = (a ^ b) & kSign, sc = c & kSign;
   uint64_t ma = a & kManMask, mb = b & kManMask, mc = c & kManMask;
-  bool zc = (ea | mc) == 0;
+  bool zc = (ec | mc) == 0;
   if ((ea | ma) == 0 || (eb | mb) == 0) {                 // a b = +-0 exactly
     if (zc) return sp & sc;                               // +0 unless both are -0
     return c;
@@ -183,15 +191,144 @@ SFP_HD uint64_t fma(uint64_t a, uint64_t b, uint64_t c) {
   return round_pack(sign, R, E);
 }
 
-SFP_HD uint64_t mul(uint64_t a, uint64_t b) { return fma(a, b, kSign); }                    // a b + (-0)
-SFP_HD uint64_t add(uint64_t a, uint64_t b) { return fma(a, 0x3FF0000000000000ull, b); }    // a 1 + b
+// ---- add and mul on their own: a 64-bit datapath, far cheaper than fma ----
+
+// x >> s (0 <= s) with the shifted-out bits ORed into bit 0
+SFP_HD uint64_t shr_jam64(uint64_t x, int s) {
+  if (s >= 64) return (uint64_t)(x != 0);
+  return s ? (x >> s) | (uint64_t)((x << (64 - s)) != 0) : x;
+}
+
+// Round-to-nearest-even packing of (sign) m 2^(e - 1085) with m < 2^63 (the
+// 53-bit significand in bits 62..10 once normalized, 10 guard bits):
+// normalizes m (m != 0), rounds, handles subnormal results and overflow.
+SFP_HD uint64_t round_pack64(uint64_t sign, uint64_t m, int e) {
+  int lz = clz64(m) - 1;                 // leading bit to bit 62
+  m <<= lz;
+  e -= lz;                               // value m 2^(e - 1085), m in [2^62, 2^63)
+  if (e >= 0x7FF) return sign | kInf;
+  if (e <= 0) {                          // subnormal: round at 2^-1074
+    m = shr_jam64(m, 1 - e);
+    e = 1;
+  }
+  uint64_t r = m & 0x3FF, q = m >> 10;
+  q += (uint64_t)(r > 0x200 || (r == 0x200 && (q & 1)));
+  return sign | ((((uint64_t)(e - 1)) << 52) + q);
+}
+
+// a + b, every case
+SFP_COLD uint64_t add_any(uint64_t a, uint64_t b) {
+  uint64_t aa = a & ~kSign, ab = b & ~kSign;
+  if (aa >= kInf || ab >= kInf) {                        // NaN or infinity
+    if (ab > kInf) return b | kQuiet;
+    if (aa > kInf) return a | kQuiet;
+    if (aa == kInf && ab == kInf && a != b) return kDefaultNaN;
+    return aa == kInf ? a : b;
+  }
+  if (aa < ab) { uint64_t t = a; a = b; b = t; t = aa; aa = ab; ab = t; }   // |a| >= |b|
+  if (ab == 0) return aa == 0 ? (a & b) : a;             // +0 unless both are -0
+  int ea = (int)(aa >> 52), eb = (int)(ab >> 52);
+  uint64_t ma = (aa & kManMask) | (ea ? kHidden : 0), mb = (ab & kManMask) | (eb ? kHidden : 0);
+  ea += !ea;                                             // subnormal: exponent 1, no hidden bit
+  eb += !eb;
+  ma <<= 10;
+  mb = shr_jam64(mb << 10, ea - eb);
+  uint64_t m;
+  if ((a ^ b) & kSign) {
+    m = ma - mb;                                         // >= 0 since |a| >= |b|
+    if (m == 0) return 0;                                // exact cancellation: +0
+  } else {
+    m = ma + mb;                                         // < 2^64
+    if (m >> 63) { m = (m >> 1) | (m & 1); ea++; }
+  }
+  return round_pack64(a & kSign, m, ea);
+}
+
+// a b, every case
+SFP_COLD uint64_t mul_any(uint64_t a, uint64_t b) {
+  uint64_t aa = a & ~kSign, ab = b & ~kSign, sign = (a ^ b) & kSign;
+  if (aa >= kInf || ab >= kInf) {
+    if (ab > kInf) return b | kQuiet;
+    if (aa > kInf) return a | kQuiet;
+    if (aa == 0 || ab == 0) return kDefaultNaN;           // inf * 0
+    return sign | kInf;
+  }
+  if (aa == 0 || ab == 0) return sign;
+  int ea = (int)(aa >> 52), eb = (int)(ab >> 52);
+  uint64_t ma = aa & kManMask, mb = ab & kManMask;
+  if (ea) ma |= kHidden; else { int s = clz64(ma) - 11; ma <<= s; ea = 1 - s; }
+  if (eb) mb |= kHidden; else { int s = clz64(mb) - 11; mb <<= s; eb = 1 - s; }
+  // (ma 2^10)(mb 2^11) in [2^125, 2^127): its high word in [2^61, 2^63), the
+  // low word folded into bit 0
+  uint64_t xa = ma << 10, xb = mb << 11;
+  uint64_t hi = mulhi64(xa, xb), lo = xa * xb;
+  uint64_t m = hi | (uint64_t)(lo != 0);
+  // a b = (xa xb) 2^(ea + eb - 2171) = hi 2^(ea + eb - 2107) = m 2^(e - 1085), e = ea + eb - 1022
+  return round_pack64(sign, m, ea + eb - 1022);
+}
+
+// ---- the common case on 32-bit words, the rest through add_any / mul_any ----
+
+// a b: normal operands with a normal result take the short path (the product
+// of the 53-bit significands from four 32 x 32 -> 64-bit multiply-adds, the
+// top 53 bits rounded with a round bit and a sticky bit); anything else
+// (zero, subnormal, infinity, NaN, a subnormal or overflowing result) goes
+// through mul_any
+SFP_HD uint64_t mul(uint64_t a, uint64_t b) {
+  uint32_t ah = (uint32_t)(a >> 32), bh = (uint32_t)(b >> 32);
+  int ea = (int)((ah >> 20) & 0x7FF), eb = (int)((bh >> 20) & 0x7FF);
+  int be = ea + eb - 1023;                  // biased exponent when the product is below 2^105
+  if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || (unsigned)(be - 1) >= 2045u)
+    return mul_any(a, b);
+  uint32_t Ah = (ah & 0xFFFFFu) | 0x100000u, Al = (uint32_t)a;
+  uint32_t Bh = (bh & 0xFFFFFu) | 0x100000u, Bl = (uint32_t)b;
+  // P = Ah Bh 2^64 + (Ah Bl + Al Bh) 2^32 + Al Bl = hi 2^64 + mid 2^32 + low, P in [2^104, 2^106)
+  uint64_t p0 = (uint64_t)Al * Bl;
+  uint64_t m1 = (uint64_t)Ah * Bl + (p0 >> 32);
+  uint64_t m2 = (uint64_t)Al * Bh + (uint32_t)m1;
+  uint64_t hi = (uint64_t)Ah * Bh + (m1 >> 32) + (m2 >> 32);
+  uint32_t mid = (uint32_t)m2, low = (uint32_t)p0;
+  int n = (int)(hi >> 41);                  // 1 when P >= 2^105
+  uint64_t M = (hi << (12 - n)) | (mid >> (20 + n));          // P >> (52 + n): 53 bits
+  uint32_t rbit = (mid >> (19 + n)) & 1u;
+  uint32_t sticky = (mid & ((1u << (19 + n)) - 1u)) | low;
+  M += rbit & ((uint32_t)(sticky != 0) | (uint32_t)(M & 1));
+  return ((a ^ b) & kSign) | ((((uint64_t)(be + n - 1)) << 52) + M);
+}
+
+// a + b: normal operands below 2^1022 with a normal result take the short
+// path (align by the exponent difference with a sticky bit, one signed
+// 64-bit addition, one normalizing shift, round); anything else goes
+// through add_any
+SFP_HD uint64_t add(uint64_t a, uint64_t b) {
+  uint64_t aa = a & ~kSign, ab = b & ~kSign;
+  bool sw = aa < ab;
+  uint64_t x = sw ? b : a, y = sw ? a : b;                     // |x| >= |y|
+  uint64_t ax = sw ? ab : aa, ay = sw ? aa : ab;
+  int ex = (int)(ax >> 52), ey = (int)(ay >> 52);
+  if (ey == 0 || ex >= 2046) return add_any(a, b);
+  uint64_t X = ((ax & kManMask) | kHidden) << 10;              // [2^62, 2^63)
+  uint64_t Y = ((ay & kManMask) | kHidden) << 10;
+  int d = ex - ey;
+  Y = d < 64 ? (d ? (Y >> d) | (uint64_t)((Y << (64 - d)) != 0) : Y) : 1;
+  uint64_t S = ((x ^ y) & kSign) ? X - Y : X + Y;
+  if (S == 0) return 0;                                        // exact cancellation: +0
+  int lz = clz64(S);                                           // 0 only after a carry
+  int e = ex + 1 - lz;
+  if (e < 1) return add_any(a, b);                             // subnormal result
+  S = lz ? S << (lz - 1) : (S >> 1) | (S & 1);                 // leading bit to bit 62
+  uint64_t q = S >> 10;
+  uint32_t r = (uint32_t)S & 0x3FFu;
+  q += (uint64_t)(r > 0x200u || (r == 0x200u && (q & 1)));
+  return (x & kSign) | ((((uint64_t)(e - 1)) << 52) + q);
+}
 SFP_HD uint64_t sub(uint64_t a, uint64_t b) { return add(a, b ^ kSign); }
 
 // rint: round to an integral value, ties to even (the sign of a zero result
 // is the sign of the argument)
 SFP_HD uint64_t rint(uint64_t x) {
   int e = (int)((x >> 52) & 0x7FF);
-  if (e == 0x7FF) return (x & ~kSign) > kInf ? kNaN : x;
+  if (e == 0x7FF) return (x & ~kSign) > kInf ? x | kQuiet : x;
   if (e >= 1075) return x;                                // already integral
   uint64_t s = x & kSign;
   if (e < 1022) return s;                                 // |x| < 1/2

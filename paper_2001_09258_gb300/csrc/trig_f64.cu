@@ -60,13 +60,13 @@ static __constant__ double kScSU35[6] = {
 // ---------------- reductions ----------------
 __device__ __forceinline__ d2 cw1(double x, double qd) {
   double u = __fma_rn(qd, -PIO2_A, x);
-  return add_dd_fast(u, __dmul_rn(qd, -PIO2_B));
+  return add_dd_fast(u, dmul(qd, -PIO2_B));
 }
 // cos at |x| < 1 (q = +-1): the fma head is not exact there, so q A is an
 // exact DD product added with TwoSum
 __device__ __forceinline__ d2 cw1_exact(double x, double qd) {
   d2 s = add_d_d2(x, mul_dd(qd, -PIO2_A));
-  return add_d2_d_fast(s, __dmul_rn(qd, -PIO2_B));
+  return add_d2_d_fast(s, dmul(qd, -PIO2_B));
 }
 __device__ __forceinline__ d2 cw2(double x, double qd) {
   double u = __fma_rn(qd, -PIO2_A, x);
@@ -84,7 +84,7 @@ __device__ __forceinline__ double cw2_d(double x, double qd) {
 
 // one rfrac step of Eq. (1): r = rint(4 x.x) quarter turns, kept mod 4 in q
 __device__ __forceinline__ void ph_step(d2 &x, int &q) {
-  double r = rint(__dmul_rn(4.0, x.x));
+  double r = drint(dmul(4.0, x.x));
   q += low2_of_int(r);
   x.x = __fma_rn(r, -0.25, x.x);
   x = norm_d2(x);
@@ -139,11 +139,11 @@ __device__ __forceinline__ d2 reduce_half(double x, uint64_t ab, int &q) {
   if (ab < B1E14) {
     double k, qd;
     if (PARITY == 0) {
-      k = rint(__dmul_rn(x, R_1_PI));
+      k = drint(dmul(x, R_1_PI));
       qd = __dadd_rn(k, k);
       q = (low2_of_int(k) << 1) & 3;
     } else {
-      k = rint(__fma_rn(x, R_1_PI, -0.5));
+      k = drint(__fma_rn(x, R_1_PI, -0.5));
       qd = __fma_rn(2.0, k, 1.0);
       q = ((low2_of_int(k) << 1) + 1) & 3;
       if (ab < B1) return cw1_exact(x, qd);
@@ -159,11 +159,11 @@ __device__ __forceinline__ double reduce_half_d(double x, uint64_t ab, int &q) {
   if (ab < B1E14) {
     double k, qd;
     if (PARITY == 0) {
-      k = rint(__dmul_rn(x, R_1_PI));
+      k = drint(dmul(x, R_1_PI));
       qd = __dadd_rn(k, k);
       q = (low2_of_int(k) << 1) & 3;
     } else {
-      k = rint(__fma_rn(x, R_1_PI, -0.5));
+      k = drint(__fma_rn(x, R_1_PI, -0.5));
       qd = __fma_rn(2.0, k, 1.0);
       q = ((low2_of_int(k) << 1) + 1) & 3;
     }
@@ -176,7 +176,7 @@ __device__ __forceinline__ double reduce_half_d(double x, uint64_t ab, int &q) {
 }
 __device__ __forceinline__ d2 reduce_quarter(double x, uint64_t ab, int &q) {
   if (ab < B1E14) {
-    double qd = rint(__dmul_rn(x, R_2_PI));
+    double qd = drint(dmul(x, R_2_PI));
     q = low2_of_int(qd);
     if (ab < B15) return cw1(x, qd);
     return cw2(x, qd);
@@ -185,7 +185,7 @@ __device__ __forceinline__ d2 reduce_quarter(double x, uint64_t ab, int &q) {
 }
 __device__ __forceinline__ double reduce_quarter_d(double x, uint64_t ab, int &q) {
   if (ab < B1E14) {
-    double qd = rint(__dmul_rn(x, R_2_PI));
+    double qd = drint(dmul(x, R_2_PI));
     q = low2_of_int(qd);
     if (ab < B15) return cw1_d(x, qd);
     return cw2_d(x, qd);
@@ -214,15 +214,15 @@ __device__ __forceinline__ int path_of(double x) {
 __device__ __forceinline__ double sin_poly_u10(d2 s) {
   d2 t = sqr_d2(s);
   double p = poly(t.x, kSinU10);
-  d2 w = add_d2_d_fast(D2(SIN_C1H, SIN_C1L), __dmul_rn(t.x, p));
+  d2 w = add_d2_d_fast(D2(SIN_C1H, SIN_C1L), dmul(t.x, p));
   w = mul_d2d2(t, w);
   w = mul_d2d2(s, w);
   d2 r = add_d2d2_fast(s, w);
   return __dadd_rn(r.x, r.y);
 }
 __device__ __forceinline__ double sin_poly_u35(double s) {
-  double t = __dmul_rn(s, s);
-  return __fma_rn(__dmul_rn(s, t), poly(t, kSinU35), s);
+  double t = dmul(s, s);
+  return __fma_rn(dmul(s, t), poly(t, kSinU35), s);
 }
 
 struct SinU10 {
@@ -297,9 +297,9 @@ struct TanU35 {
     uint64_t ab = bits(d) & ABS64;
     int q;
     double s = reduce_quarter_d(d, ab, q);
-    double y = __dmul_rn(s, 0.5), t = __dmul_rn(y, y);
+    double y = dmul(s, 0.5), t = dmul(y, y);
     double u = __fma_rn(poly(t, kTanC), t, TAN_C3);
-    double tt = __fma_rn(__dmul_rn(y, t), u, y);
+    double tt = __fma_rn(dmul(y, t), u, y);
     double num = __dadd_rn(tt, tt), den = __fma_rn(-tt, tt, 1.0);
     double r = (q & 1) ? __ddiv_rn(-den, num) : __ddiv_rn(num, den);
     if (ab == 0) r = d;
@@ -328,14 +328,14 @@ struct SinCosU10 {
     d2 s = reduce_quarter(d, ab, q);
     d2 t = sqr_d2(s);
     double p = poly(t.x, kScSU10);
-    d2 w = add_d2_d_fast(D2(SC_S1H, SC_S1L), __dmul_rn(t.x, p));
+    d2 w = add_d2_d_fast(D2(SC_S1H, SC_S1L), dmul(t.x, p));
     w = mul_d2d2(t, w);
     w = mul_d2d2(s, w);
     d2 rs = add_d2d2_fast(s, w);
     double sn = __dadd_rn(rs.x, rs.y);
     double pc = poly(t.x, kScC);
     d2 h = add_d_d2_fast(1.0, scale_d2(t, -0.5));
-    h = add_d2_d_fast(h, __dmul_rn(__dmul_rn(t.x, t.x), pc));
+    h = add_d2_d_fast(h, dmul(dmul(t.x, t.x), pc));
     double cs = __dadd_rn(h.x, h.y);
     sc_quadrant(q, sn, cs);
     if (ab == 0) sn = d;
@@ -350,8 +350,8 @@ struct SinCosU35 {
     uint64_t ab = bits(d) & ABS64;
     int q;
     double s = reduce_quarter_d(d, ab, q);
-    double t = __dmul_rn(s, s);
-    double sn = __fma_rn(__dmul_rn(s, t), poly(t, kScSU35), s);
+    double t = dmul(s, s);
+    double sn = __fma_rn(dmul(s, t), poly(t, kScSU35), s);
     double cs = __fma_rn(t, __fma_rn(t, poly(t, kScC), -0.5), 1.0);
     sc_quadrant(q, sn, cs);
     if (ab == 0) sn = d;
