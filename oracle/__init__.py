@@ -38,6 +38,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib.oracle_ph_table_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib.oracle_ph_tablef_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.oracle_fmod_recip.restype = ctypes.c_double
+        _lib.oracle_fmod_recip.argtypes = [ctypes.c_double]
         _lib.oracle_fmod_iters.restype = ctypes.c_int
         _lib.oracle_fmod_iters.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib.oracle_fmod_trace.restype = ctypes.c_int
@@ -100,6 +102,11 @@ def fmod_trace(x, y, maxk=64):
     rs = np.zeros(maxk)
     k = lib().oracle_fmod_trace(float(x), float(y), qs.ctypes.data, rs.ctypes.data, maxk)
     return qs[:k], rs[:k]
+
+
+def fmod_recip(d):
+    """The reciprocal fmod's long division multiplies by (reading R33)."""
+    return lib().oracle_fmod_recip(float(d))
 
 
 def fmod_iters(x, y):

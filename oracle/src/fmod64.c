@@ -6,8 +6,8 @@
  *
  * fmod follows Section 5.9 (Algorithm 1, long division with floating-point
  * "digits": r_{k+1} = r_k - q_k d for any integer q_k in [(r_k/d)/2, r_k/d])
- * and the Appendix B listing: one division, q = trunc(nextafter(r, 0) *
- * nextafter(1/d, 0)), the fix-ups for 1 < r/d < 3 and r == d, r kept exact in
+ * and the Appendix B listing: one reciprocal (reading R33, oracle_fmod_recip),
+ * q = trunc(nextafter(r, 0) * rd), the fix-ups for 1 < r/d < 3 and r == d, r kept exact in
  * DD, the 2^54 rescale of subnormal divisors.  The listing is valid only for
  * x/y < DBL_MAX with at most 21 iterations; here (reading A8) each iteration
  * divides by D = d 2^j with j = max(kmin, ilogb(r) - ilogb(d) - 1000), so r/D
@@ -25,6 +25,35 @@
 #define FMOD_MAXIT 48
 
 static double rdown(double v) { return nextafter(v, 0.0); }
+static double dfrom(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
+static float ffrom(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+
+/* The reciprocal of the divisor (reading R33): Section 5.9 lets q_k be any
+ * integer in [(r_k/d)/2, r_k/d] and says the division need not be correctly
+ * rounded; the listing's nextafter(1/d, 0) is one such choice.  Here: the
+ * binary32 reciprocal of d's significand m (truncated to 24 bits), widened
+ * exactly, two Newton steps y += y (1 - m y) with fma, then two units in the
+ * last place down, scaled by 2^-ilogb(d) through the exponent field.  The
+ * result never exceeds 1/d and is within 2^-50 of it (pinned with exact
+ * rationals), which keeps the proof's factor u above 5/6.  For d >= 2^1021,
+ * where 1/d approaches the subnormal range, the listing's form is kept. */
+double oracle_fmod_recip(double d) {
+  uint64_t b = dbits(d);
+  int e = (int)(b >> 52) - 1023;
+  if (e >= 1021) return rdown(1.0 / d);
+  uint64_t man = b & 0x000FFFFFFFFFFFFFULL;
+  double m = dfrom(0x3FF0000000000000ULL | man);
+  float mf = ffrom(0x3F800000U | (uint32_t)(man >> 29));      /* m truncated to 24 bits */
+  float rf = 1.0f / mf;                                       /* in (1/2, 1] */
+  uint32_t rb = fbits(rf);
+  double y = dfrom(((uint64_t)((rb >> 23) + 896) << 52) | ((uint64_t)(rb & 0x7FFFFF) << 29));  /* exact */
+  double t = fma(-m, y, 1.0);
+  y = fma(y, t, y);
+  t = fma(-m, y, 1.0);
+  y = fma(y, t, y);
+  y = dfrom(dbits(y) - 2);                                    /* two ulps down: y < 1/m */
+  return dfrom(dbits(y) - ((uint64_t)(int64_t)e << 52));      /* y 2^-e, normal */
+}
 
 /* one step of Algorithm 1 with divisor D and rD = nextafter(1/D, 0) */
 static dd_t fmod_step(dd_t r, double D, double rD) {
@@ -40,7 +69,7 @@ static double fmod_abs(double n, double d, int *iters) {
   int sub = d < 0x1p-1022;
   int kmin = sub ? 54 : 0;
   double dmin = ldexp(d, kmin);
-  double rd0 = rdown(1.0 / dmin);
+  double rd0 = oracle_fmod_recip(dmin);
   int ed = ilogb(d);
   dd_t r = dd(n, 0);
   int it = 0;
@@ -107,7 +136,7 @@ double oracle_remainder_u35_f64(double x, double y) { return oracle_remainder_u1
 int oracle_fmod_trace(double x, double y, double *qs, double *rs, int maxk) {
   double n = fabs(x), d = fabs(y);
   if (!(isfinite(n) && d >= 0x1p-1022 && isfinite(d))) return 0;
-  double rd0 = rdown(1.0 / d);
+  double rd0 = oracle_fmod_recip(d);
   int ed = ilogb(d), k = 0;
   dd_t r = dd(n, 0);
   while (k < maxk && k < FMOD_MAXIT && r.x >= d) {

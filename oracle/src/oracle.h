@@ -74,6 +74,7 @@ double oracle_fmod_u35_f64(double, double);
 double oracle_remainder_u10_f64(double, double);
 double oracle_remainder_u35_f64(double, double);
 int oracle_fmod_iters(double, double);
+double oracle_fmod_recip(double);
 int oracle_fmod_trace(double, double, double *, double *, int);
 
 float oracle_sin_u10_f32(float);

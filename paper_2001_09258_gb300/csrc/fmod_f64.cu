@@ -3,9 +3,9 @@
 //
 // Section 5.9 (Algorithm 1) and the Appendix B listing: the remainder is
 // found by long division with floating-point digits, r_{k+1} = r_k - q_k d,
-// q_k = trunc(nextafter(r_k, 0) * nextafter(1/d, 0)) with the fix-ups for
-// 1 < r/d < 3 and r == d, r held exactly as a double-double, one division in
-// total.  Extension for quotients beyond DBL_MAX (the listing's stated
+// q_k = trunc(nextafter(r_k, 0) * rd) with the fix-ups for 1 < r/d < 3 and
+// r == d, r held exactly as a double-double, one reciprocal rd <= 1/d in
+// total (recip_lower).  Extension for quotients beyond DBL_MAX (the listing's stated
 // limit): each step divides by D = d 2^j, j = max(kmin, ilogb(r) - ilogb(d) -
 // 1000), which is the listing itself whenever n/d < 2^1000; a subnormal d
 // (kmin = 54) is rescaled by 2^54 once r < d 2^54, as in the listing.
@@ -24,7 +24,6 @@ namespace fmod64 {
 constexpr int MAXIT = 48;
 constexpr uint64_t DMIN = 0x0010000000000000ull;   // bits of DBL_MIN
 constexpr uint64_t INF = 0x7FF0000000000000ull;
-constexpr uint64_t DMAX = 0x7FEFFFFFFFFFFFFFull;
 
 __device__ __forceinline__ double rdown(double v) {   // nextafter(v, 0) for v > 0 finite
   return from_bits(bits(v) - 1);
@@ -34,13 +33,37 @@ __device__ __forceinline__ double scale_n(double v, int j) {   // v normal, v 2^
   return from_bits(bits(v) + ((uint64_t)(int64_t)j << 52));
 }
 
+// The reciprocal the long division multiplies by: at most 1/d and within
+// 2^-50 of it (Section 5.9 allows any division that keeps q_k in
+// [(r_k/d)/2, r_k/d]): the binary32 reciprocal of d's significand truncated
+// to 24 bits (the FP32 pipe), widened exactly, two Newton steps with fma,
+// two units in the last place down, and 2^-ilogb(d) applied to the exponent
+// field; four FP64-pipe operations instead of a correctly rounded division.
+// From d = 2^1021 on (1/d nears the subnormal range) the listing's
+// nextafter(1/d, 0).
+__device__ __forceinline__ double recip_lower(double d) {
+  uint64_t b = bits(d);
+  int e = (int)(b >> 52) - 1023;
+  if (e >= 1021) return rdown(__ddiv_rn(1.0, d));
+  uint64_t man = b & 0x000FFFFFFFFFFFFFull;
+  double m = from_bits(0x3FF0000000000000ull | man);
+  float rf = __frcp_rn(from_fbits(0x3F800000u | (uint32_t)(man >> 29)));     // in (1/2, 1]
+  uint32_t rb = fbits(rf);
+  double y = from_bits(((uint64_t)((rb >> 23) + 896) << 52) | ((uint64_t)(rb & 0x7FFFFFu) << 29));
+  double t = __fma_rn(-m, y, 1.0);
+  y = __fma_rn(y, t, y);
+  t = __fma_rn(-m, y, 1.0);
+  y = __fma_rn(y, t, y);
+  return from_bits(bits(y) - 2 - ((uint64_t)(int64_t)e << 52));
+}
+
 // one step of Algorithm 1 (listing's fix-ups), r >= 0
 __device__ __forceinline__ d2 step(d2 r, double D, double rD) {
-  double q = trunc(__dmul_rn(rdown(r.x), rD));
+  double q = trunc(dmul(rdown(r.x), rD));
   uint64_t brx = bits(r.x), bD = bits(D);
   bool gt = brx > bD;                                    // r.x > D
-  if (bits(__dmul_rn(3.0, D)) > brx && gt) q = 2.0;
-  if (bits(__dmul_rn(2.0, D)) > brx && gt) q = 1.0;
+  if (bits(dmul(3.0, D)) > brx && gt) q = 2.0;
+  if (bits(dmul(2.0, D)) > brx && gt) q = 1.0;
   if (brx == bD) q = ((bits(r.y) >> 63) == 0 || (bits(r.y) & ABS64) == 0) ? 1.0 : 0.0;
   return norm_d2(add_d2d2(r, mul_dd(q, -D)));
 }
@@ -51,9 +74,8 @@ template <bool COUNT = false>
 __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = nullptr) {
   uint64_t bd = bits(d);
   bool sub = bd < DMIN;
-  int kmin = sub ? 54 : 0;
-  double dmin = sub ? __dmul_rn(d, 0x1p54) : d;          // exact
-  double rd0 = rdown(__ddiv_rn(1.0, dmin));
+  double dmin = sub ? dmul(d, 0x1p54) : d;          // exact
+  double rd0 = recip_lower(dmin);
   int edm = ilogb_n(bits(dmin));                           // ilogb(d) + kmin
   d2 r = D2(n, 0.0);
   uint64_t bdmin = bits(dmin);
@@ -65,12 +87,12 @@ __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = null
   }
   double ret;
   if (sub) {
-    r = D2(__dmul_rn(r.x, 0x1p54), __dmul_rn(r.y, 0x1p54));
+    r = D2(dmul(r.x, 0x1p54), dmul(r.y, 0x1p54));
     for (int k = 0; k < 4 && (int64_t)bits(r.x) >= (int64_t)bdmin; k++) {
       r = step(r, dmin, rd0);
       if (COUNT) ++*steps;
     }
-    ret = __dmul_rn(r.x, 0x1p-54);
+    ret = dmul(r.x, 0x1p-54);
     if (__dadd_rn(r.x, r.y) == dmin) ret = 0.0;
   } else {
     ret = r.x;
@@ -112,7 +134,7 @@ struct RemainderF {
     bool ok = an < INF && ad != 0 && ad < INF;
     double nn = ok ? from_bits(an) : 0.0, d = ok ? from_bits(ad) : 1.0;
     double r2 = nn;
-    if (bits(d) <= 0x7FDFFFFFFFFFFFFFull) r2 = fmod_abs(nn, __dmul_rn(2.0, d));   // 2|y| finite
+    if (bits(d) <= 0x7FDFFFFFFFFFFFFFull) r2 = fmod_abs(nn, dmul(2.0, d));   // 2|y| finite
     if (__dadd_rn(r2, r2) > d) {   // quotient 1, or 2 when r2 >= 3|y|/2
       r2 = __dsub_rn(r2, d);
       if (__dadd_rn(r2, r2) >= d) r2 = __dsub_rn(r2, d);

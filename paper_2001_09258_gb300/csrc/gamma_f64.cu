@@ -11,6 +11,15 @@
 //                    y reduced exactly to [-1/2, 1/2]
 // tgamma = sign * exp(L) with L the DD log-gamma.  Lanes are grouped by path
 // in sorted tiles (the shift path runs a loop of up to seven DD products).
+//
+// Multiplications and roundings to integral stay on the FP64 pipe here
+// (SLEEFCU_SOFT_MUL 0 for this translation unit): measured on GB300, the
+// software forms made these kernels slower (tgamma 2.08 -> 1.44 Gelem/s,
+// 1.53 even with four resident blocks), unlike every other FP64 family.
+// The results are the same bits either way.
+#ifndef SLEEFCU_FUNCTORS_ONLY
+#define SLEEFCU_SOFT_MUL 0
+#endif
 #include "explog64_core.cuh"
 
 namespace sleefcu {

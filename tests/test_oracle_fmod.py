@@ -58,10 +58,11 @@ def test_exact_against_libm(fn, acc):
 def test_worked_example():
     """Section 5.9, the worked-example figure: 1e40 / 0.75;
     first integer quotient about 1.333e40, second dividend about 4.836e24.
-    The printed dividend is n - q d for q = RD53(n/d) - 2 ulp; the listing's
-    quotient formula gives RD53(n/d) - 1 ulp.  Pinned: the quotient to the
-    printed digits, the paper's dividend reproduced from its q, and the
-    listing's q within Algorithm 1's allowed range."""
+    The printed dividend is n - q d for q = RD53(n/d) - 2 ulp, which is what
+    the oracle's reciprocal (reading R33) gives; the listing's formula with a
+    correctly rounded 1/d would give RD53(n/d) - 1 ulp and 3.022e24.  Pinned:
+    the quotient and the second dividend of the oracle's trace to the printed
+    digits, both within Algorithm 1's allowed range."""
     from fractions import Fraction
     gold = dict(l.split() for l in open(os.path.join(ROOT, "tests", "golden", "fmod_example.txt"))
                 if l.strip() and not l.startswith("#"))
@@ -74,8 +75,9 @@ def test_worked_example():
     q_paper = rd - int(gold["q0_ulps_below_rd_paper"]) * ulp
     r_paper = Fraction(n) - q_paper * Fraction(d)
     assert float(f"{float(r_paper):.3e}") == float(gold["r1_approx_paper"])
-    assert s / 2 <= Fraction(qs[0]) <= s and Fraction(qs[0]) == rd - ulp
+    assert s / 2 <= Fraction(qs[0]) <= s and Fraction(qs[0]) == q_paper
     assert Fraction(rs[0]) == Fraction(n) - Fraction(qs[0]) * Fraction(d)
+    assert float(f"{rs[0]:.3e}") == float(gold["r1_approx_paper"])
     assert oracle.apply("fmod_u10_f64", np.array([n]), np.array([d]))[0] == math.fmod(n, d)
 
 
@@ -102,3 +104,25 @@ def test_partial_remainders_stay_exact():
             acc += Fraction(q)
             exact = Fraction(n) - acc * Fraction(d)
             assert abs(Fraction(r) - exact) <= abs(exact) * Fraction(1, 2 ** 52), (n, d)
+
+
+def test_reciprocal_bound():
+    """Reading R33: the reciprocal of the long division never exceeds 1/d and
+    is within 2^-50 of it for d < 2^1021 (exact rationals; from 2^1021 on it
+    is the listing's nextafter(1/d, 0)), so the quotient stays in
+    Algorithm 1's range [(r/d)/2, r/d] (the proof's factor u =
+    (1 - 2^-51)(1 - 2^-50)(1 - 2^-52) is far above the 5/6 it needs)."""
+    from fractions import Fraction
+    mant = (I.raw("recip", 100000) >> np.uint64(12)).astype(np.uint64)
+    ex = (I.raw("recip/e", 100000) % np.uint64(2045)).astype(np.int64) - 1022
+    ds = [math.ldexp(1.0 + int(m) * 2.0 ** -52, int(e)) for m, e in zip(mant, ex)]
+    ds += [1.0, 2.0 - 2.0 ** -52, math.sqrt(2.0), 0.75, 3.0, 2.0 ** -1022, math.ldexp(2.0 - 2.0 ** -52, 1020),
+           2.0 ** 1021, math.ldexp(2.0 - 2.0 ** -52, 1023), 1.5 - 2.0 ** -52, 1e-300, 1e300]
+    worst = Fraction(0)
+    for d in ds:
+        r = Fraction(oracle.fmod_recip(d))
+        e = 1 / Fraction(d)
+        assert r <= e, d
+        if d < 2.0 ** 1021:           # above, 1/d nears the subnormal range: the listing's own form
+            worst = max(worst, (e - r) / e)
+    assert worst < Fraction(1, 2 ** 50), float(worst)
