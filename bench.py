@@ -178,6 +178,16 @@ def csrc_sha():
     return h.hexdigest()[:16]
 
 
+def measured_inst_table(fname):
+    """per-entry-point ncu counts from profiles/<fname> (measure/ncu_table.py),
+    or None once the CUDA sources differ from the captured ones"""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", fname)))
+    except (OSError, ValueError):
+        return None
+    return rec.get("per_entry_point") if csrc_sha() == rec.get("csrc_sha") else None
+
+
 def measured_pipe_counts():
     """FP64 instructions per element measured by ncu for each FP64 entry point
     (profiles/fp64_inst.json), or None when the kernel sources have changed
@@ -241,6 +251,10 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
     import numpy as np
     hbm = peaks.get("hbm_gbs")
     peak_fp32 = pipe_peak(sleefcu, torch, device, "fp32")
+    # issue-slot bound: 4 warp instructions per clock per SM
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    issue_peak = 4.0 * sms * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    inst32 = measured_inst_table("fp32_inst.json") or {}
     f32 = {}
     cache = {}
     for name in [e for e in sleefcu.entry_points() if e.endswith("_f32")]:
@@ -264,6 +278,10 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
                      "ops_per_element": round(ope, 2),
                      "fp32_frac": round(ope * g * 1e9 / peak_fp32, 4),
                      "speedup_vs_f64": round(g / base, 2) if base else None}
+        w = inst32.get(name, {}).get("warp_inst_per_element")
+        if w:
+            f32[name]["warp_inst_per_element"] = w
+            f32[name]["issue_frac"] = round(g * 1e9 * w / issue_peak, 4)
         del outs
     low = {}
     shape = (8192, 28672)
@@ -289,6 +307,10 @@ def extras(sleefcu, torch, device, st, sp, per_fn_f64, peaks, n32):
                             "fp32_frac_note": "algorithmic binary32 ops per element (oracle counting build, "
                                               "mean over the workload) x Gelem/s / measured FFMA peak "
                                               "(measure/probe.cu probe_ffma)",
+                            "issue_frac_note": "executed warp instructions per element (ncu, "
+                                               "profiles/fp32_inst.json) x Gelem/s / (4 warp instructions "
+                                               "per clock per SM x SMs x max SM clock); null when the "
+                                               "kernels changed since the capture",
                             "entry_points": f32},
             "bf16_f16_forms": {"shape": list(shape), "inputs": "N(0,3) rounded to the 16-bit format",
                                "entry_points": low}}
@@ -464,7 +486,7 @@ def c99(sleefcu, torch, device, st, sp, peaks, peak_fp64, n=1 << 26):
             "entry_points": out}
 
 
-def batched(sleefcu, torch, device, st, sp, narrays=4096):
+def batched(sleefcu, torch, device, st, sp, narrays=4096, peak_fp64=None, peak_fp32=None, hbm=None):
     """4096 arrays, lengths log-uniform in [1, 2^20], each assigned an FP64 or
     FP32 entry point uniformly at random: one autotuned persistent launch (plain
     and graph replay) against one launch per array (plain and captured in a
@@ -489,10 +511,32 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
         out2 = torch.empty_like(x) if sleefcu.FUNCS[fn] == "sc" else None
         items.append((name, x, y, out, out2))
     total = int(lens.sum())
+    # algorithmic work of the mix: FP64 operations (per path class, fmod /
+    # remainder with the kernel's own step counts), FP32 operations, bytes
+    from measure import opcounts
+    ops64 = ops32 = 0.0
+    nbytes = 0
+    for name, x, y, out, out2 in items:
+        n = x.numel()
+        nbytes += sum(t.numel() * t.element_size() for t in (x, y, out, out2) if t is not None)
+        if name.endswith("_f64"):
+            fn = name.split("_")[0]
+            stp = None
+            if fn in ("fmod", "remainder"):
+                stp = int(fmod_steps(sleefcu, torch, x, y, fn == "remainder", sp).sum())
+            ops64 += opcounts.ops_per_launch(name, x.cpu().numpy(), None if y is None else y.cpu().numpy(), stp)
+        else:
+            ops32 += opcounts.ops_per_element_f32(name) * n
     b = sleefcu.Batch(items, tune_file=os.path.join(ROOT, "paper_2001_09258_gb300", "_build", "batch_tune.jsonl"))
     cfg = b.config()
     ms_plain = time_calls(torch, st, lambda: b.launch(st), reps=5)
     ms_graph = time_calls(torch, st, lambda: b.launch(st, graph=True), reps=5)
+    # the tuned shape with each vector width (why the tuner picked its width)
+    vec_ms = {}
+    for v in (1, 2):
+        b.set_config(cfg["block"], cfg["tile"], cfg["grid_mult"], v)
+        vec_ms[f"vec{v}"] = round(time_calls(torch, st, lambda: b.launch(st), reps=5), 3)
+    b.set_config(cfg["block"], cfg["tile"], cfg["grid_mult"], cfg["vec"])
 
     def singles():
         for name, x, y, out, out2 in items:
@@ -512,20 +556,34 @@ def batched(sleefcu, torch, device, st, sp, narrays=4096):
     # items, on an idle stream and behind a 50 ms busy kernel (the call must
     # return without waiting for the stream)
     lat = {}
+    arr = sleefcu._items_array(items)                 # descriptors built once: the C call alone is timed
+    fst = sleefcu.lib().sleefcu_batch_launch_static
     for label, busy in (("idle_stream_us", False), ("busy_stream_us", True)):
-        sleefcu.batch_launch_static(items, stream=st)
+        fst(arr, len(items), sp)
         torch.cuda.synchronize()
         ts = []
         for _ in range(5):
             if busy:
                 torch.cuda._sleep(100_000_000)
             t = time.perf_counter()
-            sleefcu.batch_launch_static(items, stream=st)
+            rc = fst(arr, len(items), sp)
             ts.append((time.perf_counter() - t) * 1e6)
             torch.cuda.synchronize()
+            if rc != 0:
+                raise RuntimeError(sleefcu.last_error())
         lat[label] = round(statistics.median(ts), 1)
     gel = lambda ms: round(total / (ms * 1e-3) / 1e9, 3)
+    # roofline of the mixed launch: the slowest of the three bounds at peak
+    t64 = ops64 / peak_fp64 if peak_fp64 else 0.0
+    t32 = ops32 / peak_fp32 if peak_fp32 else 0.0
+    thbm = nbytes / (hbm * 1e9) if hbm else 0.0
+    troof = max(t64, t32, thbm)
+    roof = {"fp64_ops": ops64, "fp32_ops": ops32, "bytes": nbytes,
+            "bound": ["fp64", "fp32", "hbm"][[t64, t32, thbm].index(troof)],
+            "t_fp64_ms": round(t64 * 1e3, 3), "t_fp32_ms": round(t32 * 1e3, 3), "t_hbm_ms": round(thbm * 1e3, 3),
+            "frac": round(troof / (ms_graph * 1e-3), 4) if troof else None}
     return {"arrays": narrays, "elements": total, "entry_points": len(names_all), "config": cfg,
+            "roofline": roof, "vec_width_ms": vec_ms, "fp_frac": roof["frac"],
             "batched_ms": round(ms_plain, 3), "batched_graph_ms": round(ms_graph, 3),
             "single_launches_ms": round(ms_single, 3), "single_launches_graph_ms": round(ms_single_graph, 3),
             "batched_gelem_s": gel(ms_plain), "batched_graph_gelem_s": gel(ms_graph),
@@ -697,9 +755,15 @@ def main():
             st_ = int(fmod_steps(sleefcu, torch, dev[fn][0], dev[fn][1], fn == "remainder", sp).sum())
         o = opcounts.ops_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
         dv, sq = opcounts.div_sqrt_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
+        mu, rn = opcounts.mul_rnd_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
+        # the operations left on the FP64 pipe: multiplications and roundings
+        # run in software on the integer pipe except in the gamma kernels
+        pipe_ops = o if fn in opcounts.HW_MUL_FUNCS else o - mu - rn
         per_roof[name] = {"ops_per_element": round(o / n, 2),
                           "div_per_element": round(dv / n, 3), "sqrt_per_element": round(sq / n, 3),
-                          "fp64_frac": round(o / (avg[name] * 1e-3) / peak_fp64, 4)}
+                          "mul_rnd_per_element": round((mu + rn) / n, 3),
+                          "fp64_frac": round(o / (avg[name] * 1e-3) / peak_fp64, 4),
+                          "fp64_pipe_frac": round(pipe_ops / (avg[name] * 1e-3) / peak_fp64, 4)}
         if pipe_counts and name in pipe_counts:
             per_roof[name]["fp64_inst_per_element"] = pipe_counts[name]["fp64_inst"]
     ext = None
@@ -708,7 +772,9 @@ def main():
         torch.cuda.empty_cache()
         ext = extras(sleefcu, torch, device, st, sp, per_fn, measured_peaks(), args.n32)
         torch.cuda.empty_cache()
-        ext["batched"] = batched(sleefcu, torch, device, st, sp)
+        ext["batched"] = batched(sleefcu, torch, device, st, sp, peak_fp64=peak_fp64,
+                                 peak_fp32=ext["fp32_family"]["fp32_pipe_peak_tops"] * 1e12,
+                                 hbm=measured_peaks().get("hbm_gbs"))
         torch.cuda.empty_cache()
         ext["stress"] = stress(sleefcu, torch, device, st, sp, args.n5, peak_fp64)
         torch.cuda.empty_cache()
@@ -802,9 +868,15 @@ def headline(d, detail_path):
     roof["unit_note"] = "FP64 pipe ops: add, mul, fma, rint, div, sqrt one each (oracle counting build)"
     roof["peak_source"] = "measured DFMA peak, this run (measure/probe.cu)"
     fr = [r["fp64_frac"] for r in d["per_function_roofline"].values()]
+    pf = [r["fp64_pipe_frac"] for r in d["per_function_roofline"].values()]
     summ = {"fp64_entry_points": {"gelem_s": _spread(list(d["per_function_gelem_s"].values())),
                                   "roofline_frac": _spread(fr),
-                                  "at_or_above_0.8": sum(1 for v in fr if v >= 0.8)}}
+                                  "at_or_above_0.8": sum(1 for v in fr if v >= 0.8),
+                                  "pipe_only_frac": _spread(pf),
+                                  "frac_note": "roofline_frac: all algorithmic FP64 operations against the DFMA "
+                                               "peak (can pass 1: multiplications and roundings run on the "
+                                               "integer pipe); pipe_only_frac: the operations left on the FP64 "
+                                               "pipe against the same peak"}}
     ext = d.get("forms") or {}
     if ext:
         f32 = ext["fp32_family"]["entry_points"]

@@ -1,0 +1,67 @@
+"""Turn an ncu CSV of `measure/launch_each.py` (one launch per entry point,
+in its --list order) into the per-entry-point table bench.py reads:
+
+    python measure/ncu_table.py --family f32 --n 4194304 launches.csv > profiles/fp32_inst.json
+
+For each entry point: executed warp instructions per element
+(smsp__inst_executed.sum / n) and, when captured, FP64 thread instructions
+per element (sm__sass_thread_inst_executed_op_fp64_pred_on.sum / n).  The
+table records a hash of the CUDA sources; bench.py ignores it once they
+change."""
+import argparse
+import csv
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "measure"))
+
+
+def csrc_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2001_09258_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        fp = os.path.join(csrc, f)
+        if os.path.isfile(fp):
+            h.update(f.encode())
+            h.update(open(fp, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--family", choices=["f64", "f32"], required=True)
+    p.add_argument("--n", type=int, required=True)
+    p.add_argument("csv")
+    a = p.parse_args()
+    from launch_each import names
+    order = names(a.family)
+    rows = {}
+    with open(a.csv) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        rows.setdefault(int(r["ID"]), {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+        rows[int(r["ID"])]["kernel"] = r["Kernel Name"]
+    if len(rows) != len(order):
+        raise SystemExit(f"{len(rows)} launches in {a.csv}, {len(order)} entry points")
+    out = {}
+    for i, nm in enumerate(order):
+        m = rows[i]
+        e = {"kernel": m["kernel"].split("(")[0], "time_ns": m.get("gpu__time_duration.sum")}
+        if "smsp__inst_executed.sum" in m:
+            e["warp_inst_per_element"] = round(m["smsp__inst_executed.sum"] / a.n, 4)
+        if "sm__sass_thread_inst_executed_op_fp64_pred_on.sum" in m:
+            e["fp64_inst"] = round(m["sm__sass_thread_inst_executed_op_fp64_pred_on.sum"] / a.n, 3)
+        out[nm] = e
+    json.dump({"csrc_sha": csrc_sha(), "n": a.n, "family": a.family,
+               "command": f"python measure/launch_each.py --family {a.family} --n {a.n} under ncu "
+                          "--metrics smsp__inst_executed.sum,gpu__time_duration.sum --clock-control none --csv",
+               "per_entry_point": out}, sys.stdout, indent=1, sort_keys=True)
+    print()
+
+
+if __name__ == "__main__":
+    main()

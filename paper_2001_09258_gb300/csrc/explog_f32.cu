@@ -14,41 +14,60 @@
 
 // ---------------- bf16 / f16 forms ----------------
 // 16-bit input converted exactly to binary32, the FP32 functor, the result
-// rounded to the 16-bit format (round-to-nearest-even, integer arithmetic);
-// NaN results are the canonical 0x7FC0 (bf16) / 0x7E00 (f16).
+// rounded to the 16-bit format with the hardware's round-to-nearest-even
+// conversions (cvt.rn.bf16.f32 / cvt.rn.f16.f32, overflow to infinity,
+// subnormal f16 results included); NaN results are the canonical 0x7FC0
+// (bf16) / 0x7E00 (f16), chosen by a select.
+//
+// A 16-bit format has 65,536 inputs.  For large arrays each block first
+// evaluates the functor on all of them into a 128 KB shared-memory table
+// (the same FP32 body, so every entry is the bit pattern the direct form
+// returns) and the array is then a gather through the table: the kernel is
+// bounded by HBM traffic instead of by FP32 issue.  Small arrays evaluate
+// directly (building a table costs as much as 65,536 elements per block).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <mutex>
 namespace sleefcu {
 namespace lowp {
 
 __device__ __forceinline__ float bf16_in(uint16_t h) { return from_fbits((uint32_t)h << 16); }
 __device__ __forceinline__ uint16_t bf16_out(float f) {
-  uint32_t b = fbits(f);
-  if ((b & ABS32) > EXP32) return 0x7FC0;
-  b += 0x7FFFu + ((b >> 16) & 1u);
-  return (uint16_t)(b >> 16);
+  uint16_t r = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+  return (fbits(f) & ABS32) > EXP32 ? (uint16_t)0x7FC0 : r;
 }
-__device__ __forceinline__ float f16_in(uint16_t h) {
-  uint32_t s = (uint32_t)(h & 0x8000u) << 16, e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
-  if (e == 0x1F) return from_fbits(s | 0x7F800000u | (m << 13));
-  if (e) return from_fbits(s | ((e + 112u) << 23) | (m << 13));
-  float f = __fmul_rn(__uint2float_rn(m), 0x1p-24f);     // exact
-  return s ? -f : f;
-}
+__device__ __forceinline__ float f16_in(uint16_t h) { return __half2float(__ushort_as_half(h)); }
 __device__ __forceinline__ uint16_t f16_out(float f) {
-  uint32_t b = fbits(f), sign = (b >> 16) & 0x8000u, ab = b & ABS32;
-  if (ab > EXP32) return 0x7E00;
-  if (ab >= 0x477FF000u) return (uint16_t)(sign | 0x7C00u);
-  if (ab >= 0x38800000u) {
-    uint32_t r = ab - (112u << 23);
-    r += 0xFFFu + ((r >> 13) & 1u);
-    return (uint16_t)(sign | (r >> 13));
-  }
-  uint32_t t = fbits(__fadd_rn(from_fbits(ab), 0.5f)) - 0x3F000000u;   // RNE to 2^-24 units
-  return (uint16_t)(sign | t);
+  uint16_t r = __half_as_ushort(__float2half_rn(f));
+  return (fbits(f) & ABS32) > EXP32 ? (uint16_t)0x7E00 : r;
 }
 
 template <class F, bool BF>
 __device__ __forceinline__ uint16_t ev(const F &f, uint16_t h) {
   return BF ? bf16_out(f(bf16_in(h))) : f16_out(f(f16_in(h)));
+}
+// a packed pair (low half first), the conversions two at a time
+template <class F, bool BF>
+__device__ __forceinline__ uint32_t ev2(const F &f, uint32_t v) {
+  float a, b;
+  uint32_t r;
+  if (BF) {
+    a = f(bf16_in((uint16_t)(v & 0xFFFFu)));
+    b = f(bf16_in((uint16_t)(v >> 16)));
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    r = *reinterpret_cast<uint32_t *>(&p);
+    if ((fbits(a) & ABS32) > EXP32) r = (r & 0xFFFF0000u) | 0x7FC0u;
+    if ((fbits(b) & ABS32) > EXP32) r = (r & 0x0000FFFFu) | 0x7FC00000u;
+  } else {
+    float2 in = __half22float2(*reinterpret_cast<const __half2 *>(&v));
+    a = f(in.x);
+    b = f(in.y);
+    __half2 p = __floats2half2_rn(a, b);
+    r = *reinterpret_cast<uint32_t *>(&p);
+    if ((fbits(a) & ABS32) > EXP32) r = (r & 0xFFFF0000u) | 0x7E00u;
+    if ((fbits(b) & ABS32) > EXP32) r = (r & 0x0000FFFFu) | 0x7E000000u;
+  }
+  return r;
 }
 
 template <class F, bool BF, bool VEC>
@@ -62,10 +81,10 @@ __global__ void __launch_bounds__(kBlock) k_lowp(const uint16_t *x, uint16_t *ou
     uint4 *o8 = reinterpret_cast<uint4 *>(out);
     for (size_t i = tid; i < n8; i += stride) {
       uint4 v = __ldcs(x8 + i), r;
-      r.x = ev<F, BF>(f, (uint16_t)(v.x & 0xFFFF)) | ((uint32_t)ev<F, BF>(f, (uint16_t)(v.x >> 16)) << 16);
-      r.y = ev<F, BF>(f, (uint16_t)(v.y & 0xFFFF)) | ((uint32_t)ev<F, BF>(f, (uint16_t)(v.y >> 16)) << 16);
-      r.z = ev<F, BF>(f, (uint16_t)(v.z & 0xFFFF)) | ((uint32_t)ev<F, BF>(f, (uint16_t)(v.z >> 16)) << 16);
-      r.w = ev<F, BF>(f, (uint16_t)(v.w & 0xFFFF)) | ((uint32_t)ev<F, BF>(f, (uint16_t)(v.w >> 16)) << 16);
+      r.x = ev2<F, BF>(f, v.x);
+      r.y = ev2<F, BF>(f, v.y);
+      r.z = ev2<F, BF>(f, v.z);
+      r.w = ev2<F, BF>(f, v.w);
       __stcs(o8 + i, r);
     }
     size_t rem = n & 7;
@@ -73,6 +92,33 @@ __global__ void __launch_bounds__(kBlock) k_lowp(const uint16_t *x, uint16_t *ou
   } else {
     for (size_t i = tid; i < n; i += stride) out[i] = ev<F, BF>(f, x[i]);
   }
+}
+
+// the table form: one block per SM, 1024 threads
+constexpr int kTabBlock = 1024;
+constexpr size_t kTabMinN = (size_t)1 << 24;   // below this, direct evaluation
+template <class F, bool BF>
+__global__ void __launch_bounds__(kTabBlock, 1) k_lowp_table(const uint16_t *x, uint16_t *out, size_t n) {
+  extern __shared__ uint32_t tab2[];           // 65,536 results as 32,768 packed pairs
+  F f;
+  for (uint32_t i = threadIdx.x; i < 32768u; i += kTabBlock) tab2[i] = ev2<F, BF>(f, (2u * i) | ((2u * i + 1u) << 16));
+  __syncthreads();
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(tab2);
+  size_t stride = (size_t)gridDim.x * kTabBlock;
+  size_t tid = (size_t)blockIdx.x * kTabBlock + threadIdx.x;
+  size_t n8 = n >> 3;
+  const uint4 *x8 = reinterpret_cast<const uint4 *>(x);
+  uint4 *o8 = reinterpret_cast<uint4 *>(out);
+  for (size_t i = tid; i < n8; i += stride) {
+    uint4 v = __ldcs(x8 + i), r;
+    r.x = tab[v.x & 0xFFFFu] | ((uint32_t)tab[v.x >> 16] << 16);
+    r.y = tab[v.y & 0xFFFFu] | ((uint32_t)tab[v.y >> 16] << 16);
+    r.z = tab[v.z & 0xFFFFu] | ((uint32_t)tab[v.z >> 16] << 16);
+    r.w = tab[v.w & 0xFFFFu] | ((uint32_t)tab[v.w >> 16] << 16);
+    __stcs(o8 + i, r);
+  }
+  size_t rem = n & 7;
+  if (tid < rem) out[n - rem + tid] = tab[x[n - rem + tid]];
 }
 
 template <class F, bool BF>
@@ -83,6 +129,27 @@ sleefcu_status launch_lowp(const char *name, const void *x, void *out, size_t n,
   uint16_t *oi = (uint16_t *)out;
   if (sleefcu_status rc_ = check_args(name, n, xi, oi)) return rc_;
   cudaStream_t st = (cudaStream_t)s;
+  if (aligned16(x) && aligned16(out) && n >= kTabMinN) {
+    auto k = k_lowp_table<F, BF>;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    static std::mutex mu;                      // 128 KB of dynamic shared memory is opt-in, per device
+    static signed char attr[64];               // 0 not set yet, 1 set, -1 refused
+    signed char a = -1;
+    if (dev >= 0 && dev < 64) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (attr[dev] == 0)
+        attr[dev] = cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 131072) ==
+                            cudaSuccess ? 1 : -1;
+      a = attr[dev];
+    }
+    cudaGetLastError();
+    if (a == 1) {
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      k<<<sms, kTabBlock, 131072, st>>>(xi, oi, n);
+      return check_launch(name);
+    }
+  }
   if (aligned16(x) && aligned16(out)) {
     auto k = k_lowp<F, BF, true>;
     k<<<grid_for((const void *)k, (n + 7) / 8), kBlock, 0, st>>>(xi, oi, n);

@@ -59,7 +59,7 @@ __device__ __forceinline__ double recip_lower(double d) {
 
 // one step of Algorithm 1 (listing's fix-ups), r >= 0
 __device__ __forceinline__ d2 step(d2 r, double D, double rD) {
-  double q = trunc(dmul(rdown(r.x), rD));
+  double q = dtrunc(dmul(rdown(r.x), rD));
   uint64_t brx = bits(r.x), bD = bits(D);
   bool gt = brx > bD;                                    // r.x > D
   if (bits(dmul(3.0, D)) > brx && gt) q = 2.0;

@@ -10,7 +10,7 @@
 #include <cuda_runtime.h>
 #include "softfp64.cuh"
 
-// Binary64 multiplication and rounding to an integral value in the kernels:
+// Binary64 multiplication and rounding to an integral value (rint, trunc) in the kernels:
 // exact software forms on the integer pipe (softfp64.cuh), bit-identical to
 // the FP64 pipe's, so that the FP64 pipe, the bottleneck of the FP64 family
 // on GB300, keeps only the additions and fused multiply-adds.  Compiling
@@ -34,6 +34,13 @@ __device__ __forceinline__ double drint(double a) {
   return __longlong_as_double((long long)soft::rint((uint64_t)__double_as_longlong(a)));
 #else
   return rint(a);
+#endif
+}
+__device__ __forceinline__ double dtrunc(double a) {
+#if SLEEFCU_SOFT_MUL
+  return __longlong_as_double((long long)soft::trunc((uint64_t)__double_as_longlong(a)));
+#else
+  return trunc(a);
 #endif
 }
 

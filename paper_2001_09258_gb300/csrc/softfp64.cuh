@@ -15,7 +15,8 @@
 // for bit (measured): a NaN operand is returned quieted (bit 51 set, sign
 // and payload kept), choosing b, then c, then a for fma and the second
 // operand, then the first for add and mul; an invalid operation (inf * 0,
-// inf - inf) returns kDefaultNaN; rint returns its NaN argument quieted.
+// inf - inf) returns kDefaultNaN; rint and trunc return a NaN argument
+// quieted.
 // The header compiles as plain C++ as well (host functions), which is how
 // the CPU tests pin it against the host processor's hardware fma.
 #pragma once
@@ -339,6 +340,15 @@ SFP_HD uint64_t rint(uint64_t x) {
   if (q == 0) return s;
   // q 2^sh has the exponent of x, or one more after a carry to 2^53
   return s | ((((uint64_t)(e - 1)) << 52) + (q << sh));
+}
+
+// trunc: round toward zero to an integral value (NaN quieted, as the pipe does)
+SFP_HD uint64_t trunc(uint64_t x) {
+  int e = (int)((x >> 52) & 0x7FF);
+  if (e == 0x7FF) return (x & ~kSign) > kInf ? x | kQuiet : x;
+  if (e >= 1075) return x;                                // already integral
+  if (e < 1023) return x & kSign;                         // |x| < 1
+  return x & ~((1ull << (1075 - e)) - 1);                 // clear the fraction bits
 }
 
 }  // namespace soft

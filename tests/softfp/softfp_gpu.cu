@@ -1,5 +1,5 @@
 // Device-side checks of the software binary64 arithmetic (softfp64.cuh)
-// against the FP64 pipe of the GPU (__fma_rn, __dadd_rn, __dmul_rn, rint),
+// against the FP64 pipe of the GPU (__fma_rn, __dadd_rn, __dmul_rn, rint, trunc),
 // bit for bit including the NaN pattern, and a throughput probe of the two.
 // Test infrastructure, built by tests/test_softfp.py with nvcc.
 #include <cuda_runtime.h>
@@ -15,10 +15,10 @@ __global__ void k_check(uint64_t seed, long long per_thread, int mode_mask, unsi
     for (long long i = 0; i < per_thread; i++) {
       uint64_t a, b, c;
       gen(r, mode, a, b, c);
-      uint64_t got[4] = {S::fma(a, b, c), S::add(a, c), S::mul(a, b), S::rint(a)};
-      uint64_t want[4] = {b_of(__fma_rn(d_of(a), d_of(b), d_of(c))), b_of(__dadd_rn(d_of(a), d_of(c))),
-                          b_of(__dmul_rn(d_of(a), d_of(b))), b_of(rint(d_of(a)))};
-      for (int op = 0; op < 4; op++) {
+      uint64_t got[5] = {S::fma(a, b, c), S::add(a, c), S::mul(a, b), S::rint(a), S::trunc(b)};
+      uint64_t want[5] = {b_of(__fma_rn(d_of(a), d_of(b), d_of(c))), b_of(__dadd_rn(d_of(a), d_of(c))),
+                          b_of(__dmul_rn(d_of(a), d_of(b))), b_of(rint(d_of(a))), b_of(trunc(d_of(b)))};
+      for (int op = 0; op < 5; op++) {
         if (got[op] != want[op]) {
           // err[0]: any difference; err[1]: a difference that is not between two NaNs
           bool both_nan = is_nan(got[op]) && is_nan(want[op]);

@@ -49,3 +49,17 @@ def test_activation_tensor_8192x28672(name):
     h = I.activations("c3/act", (8192, 28672), fmt).reshape(-1)
     got, want = run(name, h), oracle.apply(name, h)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_table_form_every_input(name):
+    """Arrays of 2^24 elements and more take the shared-memory table form:
+    every 16-bit pattern, in a scrambled order and with a ragged tail, gives
+    the oracle's bits."""
+    n = (1 << 24) + 11
+    perm = (I.raw(f"tab/{name}", n) & np.uint64(0xFFFF)).astype(np.uint16)
+    perm[:65536] = np.arange(65536, dtype=np.uint16)
+    table = oracle.apply(name, np.arange(65536, dtype=np.uint16))
+    got = run(name, perm)
+    bad = np.nonzero(got != table[perm])[0]
+    assert bad.size == 0, (name, bad.size, hex(perm[bad[0]]), hex(got[bad[0]]), hex(table[perm[bad[0]]]))

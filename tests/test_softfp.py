@@ -1,7 +1,7 @@
 """Exact binary64 arithmetic on the integer pipe (csrc/softfp64.cuh).
 
 Correctly rounded IEEE operations are unique (the bit-consistency argument of
-Section 4), so the software fma, add, mul and rint must equal the host
+Section 4), so the software fma, add, mul, rint and trunc must equal the host
 processor's hardware operations bit for bit (NaN results: NaN-ness on the
 host, whose NaN payload rules differ) and the GPU's FP64 pipe bit for bit
 (NaN bits included).  Pinned on:
@@ -9,13 +9,13 @@ host, whose NaN payload rules differ) and the GPU's FP64 pipe bit for bit
     patterns, cancellation against RN(a b), subnormal and near-overflow
     ranges, few-bit significands that produce exact ties, specials mixed with
     finite values, additions with close exponents, products with a zero
-    addend -- 2^29 triples x 4 operations on the host cores
+    addend -- 2^29 triples x 5 operations on the host cores
     (SOFTFP_CASES=<per mode per thread> for larger runs);
   * directed cases: ties to even in the normal and subnormal range, exact
     cancellation to +0, signed zeros, overflow to infinity at the tie above
     DBL_MAX, underflow ties around 2^-1075, invalid operations;
   * on the GPU, 1.3e9 structured triples against __fma_rn, __dadd_rn,
-    __dmul_rn and rint."""
+    __dmul_rn, rint and trunc."""
 import ctypes
 import concurrent.futures as cf
 import os
