@@ -121,6 +121,18 @@ def ops_per_launch(name, x, y=None, steps=None):
     return _per_launch(name, x, y, steps, "ops")
 
 
+def mul_rnd_per_launch(name, x, y=None, steps=None):
+    """(multiplications, roundings to integral) of one launch of a binary64
+    entry point: the operations the kernels run in software on the integer
+    pipe (all FP64 families but tgamma / lgamma)"""
+    return _per_launch(name, x, y, steps, "mul"), _per_launch(name, x, y, steps, "rnd")
+
+
+# entry points whose multiplications stay on the FP64 pipe (their translation
+# unit is compiled with SLEEFCU_SOFT_MUL 0)
+HW_MUL_FUNCS = ("tgamma", "lgamma")
+
+
 def div_sqrt_per_launch(name, x, y=None, steps=None):
     """(divisions, square roots) of one launch of a binary64 entry point"""
     return _per_launch(name, x, y, steps, "div"), _per_launch(name, x, y, steps, "sqrt")

@@ -102,7 +102,8 @@ def _entry(t, n, prec=None):
         prec = "f64" if t["f64"]["add"] + t["f64"]["mul"] + t["f64"]["fma"] else "f32"
     f = t[prec]
     ops = sum(f[c] for c in oracle.ALGO_CATS)
-    return {"ops": round(ops / n, 4), "div": round(f["div"] / n, 4), "sqrt": round(f["sqrt"] / n, 4), "n": n}
+    return {"ops": round(ops / n, 4), "div": round(f["div"] / n, 4), "sqrt": round(f["sqrt"] / n, 4),
+            "mul": round(f["mul"] / n, 4), "rnd": round(f["rnd"] / n, 4), "n": n}
 
 
 def _count_f64(name, fn):
@@ -117,7 +118,7 @@ def _count_f64(name, fn):
     for cls, mask in classes(fn, x, y).items():
         idx = np.flatnonzero(mask)[:SAMPLE_PER_CLASS]
         if idx.size == 0:
-            out[cls] = {"ops": 0.0, "div": 0.0, "sqrt": 0.0, "n": 0}
+            out[cls] = {"ops": 0.0, "div": 0.0, "sqrt": 0.0, "mul": 0.0, "rnd": 0.0, "n": 0}
             continue
         _, t = oracle.count(name, x[idx], None if y is None else y[idx])
         out[cls] = _entry(t, idx.size)
@@ -139,7 +140,7 @@ def _count_fmod(name, fn):
         d = abs(b)
         if fn == "remainder" and np.isfinite(2 * d):
             d = 2 * d
-        rows.append((oracle.fmod_iters(abs(a), d), ops, t["f64"]["div"]))
+        rows.append((oracle.fmod_iters(abs(a), d), ops, t["f64"]["div"], t["f64"]["mul"], t["f64"]["rnd"]))
     rows = np.array(rows, dtype=np.float64)
     fin = np.isfinite(xs) & np.isfinite(ys) & (ys != 0)
     it, ops = rows[fin, 0], rows[fin, 1]
@@ -150,16 +151,23 @@ def _count_fmod(name, fn):
         a = 1.5 * 2.0 ** (40 * k)
         _, t = oracle.count(name, np.array([a]), np.array([1.0]))
         pts.append((oracle.fmod_iters(a, 2.0 if fn == "remainder" else 1.0),
-                    sum(t["f64"][c] for c in oracle.ALGO_CATS)))
+                    sum(t["f64"][c] for c in oracle.ALGO_CATS), t["f64"]["mul"], t["f64"]["rnd"]))
     pts = np.array(sorted(set(pts)), dtype=np.float64)
-    slopes = np.diff(pts[:, 1]) / np.diff(pts[:, 0])
-    step = float(slopes[0])
-    if not np.all(slopes == step) or step != int(step):
-        raise RuntimeError(f"{name}: long-division steps do not cost a fixed count ({slopes})")
+    per = []
+    for col in (1, 2, 3):                      # ops, mul, rnd per step
+        slopes = np.diff(pts[:, col]) / np.diff(pts[:, 0])
+        v = float(slopes[0])
+        if not np.all(slopes == v) or v != int(v):
+            raise RuntimeError(f"{name}: long-division steps do not cost a fixed count ({slopes})")
+        per.append(v)
+    step, step_mul, step_rnd = per
     setup = ops - step * it
+    smul = rows[fin, 3] - step_mul * it
+    srnd = rows[fin, 4] - step_rnd * it
     return {"setup": {"ops": round(float(setup.mean()), 4), "div": round(float(rows[fin, 2].mean()), 4),
-                      "sqrt": 0.0, "n": int(fin.sum()), "min": float(setup.min()), "max": float(setup.max())},
-            "step": {"ops": step, "div": 0.0, "sqrt": 0.0, "n": int(fin.sum())}}
+                      "sqrt": 0.0, "mul": round(float(smul.mean()), 4), "rnd": round(float(srnd.mean()), 4),
+                      "n": int(fin.sum()), "min": float(setup.min()), "max": float(setup.max())},
+            "step": {"ops": step, "div": 0.0, "sqrt": 0.0, "mul": step_mul, "rnd": step_rnd, "n": int(fin.sum())}}
 
 
 def table():

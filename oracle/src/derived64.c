@@ -29,7 +29,8 @@
  *        cosh = (E + 1/E)/2, tanh = e2/(e2 + 2) with e2 = e^(2|x|) - 1);
  *        for large |x| e^|x|/2 directly.
  * asinh, acosh, atanh   log of the DD argument |x| + sqrt(x^2 + 1),
- *        x + sqrt((x-1)(x+1)), (1+|x|)/(1-|x|).
+ *        x + sqrt((x-1)(x+1)), (1+|x|)/(1-|x|): the DD logarithm (u10), or
+ *        the logarithm in double with its z corrected once (u35).
  */
 #include "common.h"
 #include "coeffs64.h"
@@ -399,12 +400,56 @@ double oracle_atanh_u10_f64(double x) {
   return canon(copysign(y, x));
 }
 
-/* No cheaper form holds 3.5 ULP without giving up the DD argument (the
- * cancellation in x^2 + 1 - 1 and 1 - |x| is the whole difficulty), so the
- * 3.5-ULP entry points are the 1-ULP algorithms. */
-double oracle_asinh_u35_f64(double x) { return oracle_asinh_u10_f64(x); }
-double oracle_acosh_u35_f64(double x) { return oracle_acosh_u10_f64(x); }
-double oracle_atanh_u35_f64(double x) { return oracle_atanh_u10_f64(x); }
+/* 3.5-ULP forms: the same DD arguments as the 1-ULP forms (they carry the
+ * cancellation in x^2 + 1 - 1, x^2 - 1 and 1 - |x|), whose logarithm is
+ * taken in double with z corrected once (oracle_logm_u20) and e ln 2 added by
+ * one fma, instead of the DD logarithm (the plain 3.5-ULP core, z rounded
+ * three times, reached 4.0 ULP on asinh near 0.24).
+ * Above 2^500, log(2x) = (e + 1) ln 2 + log m. */
+double oracle_asinh_u35_f64(double x) {
+  double a = fabs(x);
+  double ac = a <= 0x1.fffffffffffffp1023 ? a : 1.0;
+  int e;
+  double lm;
+  if (ac > 0x1p500) {
+    lm = oracle_logm_u20(dd(ac, 0.0), &e);
+    e += 1;
+  } else {
+    dd_t w = ddsqrt_d2_d2(ddadd2_d2_d2_d(ddmul_d2_d_d(ac, ac), 1.0));
+    lm = oracle_logm_u20(ddadd2_d2_d2_d(w, ac), &e);
+  }
+  double y = fma((double)e, L2A, lm);
+  if (a < TWO_M28) y = a;
+  if (!(a <= 0x1.fffffffffffffp1023)) y = isnan(x) ? NAN : INFINITY;
+  return canon(copysign(y, x));
+}
+double oracle_acosh_u35_f64(double x) {
+  double xc = (x >= 1 && x <= 0x1.fffffffffffffp1023) ? x : 1.0;
+  int e;
+  double lm;
+  if (xc > 0x1p500) {
+    lm = oracle_logm_u20(dd(xc, 0.0), &e);
+    e += 1;
+  } else {
+    dd_t d = ddmul_d2_d2_d2(ddadd2_d2_d_d(xc, -1.0), ddadd2_d2_d_d(xc, 1.0));
+    lm = oracle_logm_u20(ddadd2_d2_d2_d(ddsqrt_d2_d2(d), xc), &e);
+  }
+  double y = fma((double)e, L2A, lm);
+  if (xc == 1) y = 0.0;                         /* the DD square root of 0 is not defined */
+  if (!(x >= 1 && x <= 0x1.fffffffffffffp1023)) y = x == INFINITY ? INFINITY : NAN;
+  return canon(y);
+}
+double oracle_atanh_u35_f64(double x) {
+  double a = fabs(x);
+  double ac = a < 1 ? a : 0.5;
+  dd_t q = dddiv_d2_d2_d2(ddadd2_d2_d_d(1.0, ac), ddadd2_d2_d_d(1.0, -ac));
+  int e;
+  double lm = oracle_logm_u20(q, &e);
+  double y = 0.5 * fma((double)e, L2A, lm);
+  if (a < TWO_M28) y = a;
+  if (!(a < 1)) y = a == 1 ? INFINITY : NAN;
+  return canon(copysign(y, x));
+}
 
 /* ---------------- erf, erfc ----------------
  * erf   |x| < 1: x (C0 + t (C1 + t (c2 + t P(t)))), t = x^2 exact as a DD and

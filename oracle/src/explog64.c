@@ -158,6 +158,28 @@ double oracle_logm_u35(dd_t a, int *ep) {
   return fma(z * t, poly_d(t, LOG_U35, 7), z);
 }
 
+/* log m in double with z = 2(m-1)/(m+1) corrected once: the reciprocal
+ * quotient's residual num - z (1 + m) taken by fma (with the DD tail of m)
+ * and added back through the reciprocal, then the 3.5-ULP polynomial; for
+ * the 3.5-ULP forms whose logarithm is small against its argument's
+ * rounding (asinh, acosh, atanh near 0 and 1) */
+double oracle_logm_u20(dd_t a, int *ep) {
+  int off = 0;
+  if (a.x < 0x1p-1022) { a = ddscale_d2_d2_d(a, 0x1p64); off = 64; }
+  int ex = ilogb(a.x);
+  dd_t m = ddscale_d2_d2_d(a, ldexp(1.0, -ex));
+  if (m.x >= 1.5) { m = ddscale_d2_d2_d(m, 0.5); ex++; }
+  double num = 2.0 * ((m.x - 1.0) + m.y);
+  double den = 1.0 + m.x;
+  double rd = 1.0 / den;
+  double z = num * rd;
+  double r = fma(-z, den, num) - z * (((1.0 - den) + m.x) + m.y);   /* num - z (1 + m), the rounding of den included */
+  z = fma(r, rd, z);
+  double t = z * z;
+  *ep = ex - off;
+  return fma(z * t, poly_d(t, LOG_U35, 7), z);
+}
+
 /* ---------------- pow ---------------- */
 static const double PL_C1H = POWLOG_C1H, PL_C1L = POWLOG_C1L;
 static const double POWLOG[9] = { POWLOG_COEFFS };

@@ -20,6 +20,7 @@ dd_t oracle_expk_s(dd_t Y, double *k);
 dd_t oracle_logm_u10(dd_t a, int *e);
 /* the same in double for the 3.5-ULP forms */
 double oracle_logm_u35(dd_t a, int *e);
+double oracle_logm_u20(dd_t a, int *e);
 
 /* log of a DD y > 0 with the 11-term DD polynomial of pow (about 2^-66) */
 dd_t oracle_logk_dd(dd_t y);

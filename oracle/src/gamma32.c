@@ -18,6 +18,9 @@
 #define LOGPI_LF 0x1.1cf438p-25f
 #define PI_HF 0x1.921fb6p+1f
 #define PI_LF (-0x1.777a5cp-24f)
+/* 64 ln 2 as an FF: 64 times the 15-bit head of ln 2 and 64 times its tail (both exact) */
+#define LN2X64_HF 0x1.62e4p+5f
+#define LN2X64_LF 0x1.7f7d1cp-14f
 
 static const float LGR_H[4] = { LGF_R2_HEAD };
 static const float LGR_P[8] = { LGF_R2_COEFFS };
@@ -79,9 +82,14 @@ static ff_t sinpif_ff(float x) {
 static ff_t lgammaf_ff(float x, int *sign) {
   *sign = 1;
   if (x > 0) return lgammaf_pos(ff(x, 0.0f));
-  ff_t sp = sinpif_ff(x);
+  /* |x| < 2^-100: sin(pi x) is pi x to far below an ulp and pi x would lose
+   * its precision in the subnormal range; formed from x 2^64 (exact), with
+   * 64 ln 2 taken off its logarithm */
+  int up = fabsf(x) < 0x1p-100f;
+  ff_t sp = up ? ffmul_f2_f2_f(ff(PI_HF, PI_LF), ldexpf(x, 64)) : sinpif_ff(x);
   *sign = sp.x < 0 ? -1 : 1;
   ff_t l = oracle_logkf(ff(fabsf(sp.x), sp.x < 0 ? -sp.y : sp.y));
+  if (up) l = ffadd2_f2_f2_f2(l, ff(-LN2X64_HF, -LN2X64_LF));
   ff_t r = ffadd2_f2_f2_f2(ff(LOGPI_HF, LOGPI_LF), fneg(l));
   return ffadd2_f2_f2_f2(r, fneg(lgammaf_pos(ffadd2_f2_f_f(1.0f, -x))));
 }

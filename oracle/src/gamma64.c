@@ -36,6 +36,9 @@
 #define LOGPI_L 0x1.7abf2ad8d5088p-57
 #define PI_H 0x1.921fb54442d18p+1
 #define PI_L 0x1.1a62633145c07p-53
+/* 200 ln 2 as a DD: 200 times the 42-bit head of ln 2 (exact) and RN(200 times its tail) */
+#define LN2X200_H 0x1.1542457337bc0p+7
+#define LN2X200_L 0x1.82e1c6b73c89ep-37
 
 static const double LG_RH[4] = { LGAMMA_R2_HEAD };
 static const double LG_RP[16] = { LGAMMA_R2_COEFFS };
@@ -112,9 +115,14 @@ static dd_t sinpi_dd(double x) {
 static dd_t lgamma_dd(double x, int *sign) {
   *sign = 1;
   if (x > 0) return lgamma_pos(dd(x, 0.0));
-  dd_t sp = sinpi_dd(x);
+  /* |x| < 2^-900: sin(pi x) is pi x to far below an ulp, and pi x itself
+   * would lose its precision in the subnormal range; it is formed from
+   * x 2^200 (exact) and 200 ln 2 is taken off its logarithm */
+  int up = fabs(x) < 0x1p-900;
+  dd_t sp = up ? ddmul_d2_d2_d(dd(PI_H, PI_L), ldexp(x, 200)) : sinpi_dd(x);
   *sign = sp.x < 0 ? -1 : 1;
   dd_t l = oracle_logk_dd(dd(fabs(sp.x), sp.x < 0 ? -sp.y : sp.y));
+  if (up) l = ddadd2_d2_d2_d2(l, dd(-LN2X200_H, -LN2X200_L));
   dd_t r = ddadd2_d2_d2_d2(dd(LOGPI_H, LOGPI_L), dd(-l.x, -l.y));
   dd_t g = lgamma_pos(ddadd2_d2_d_d(1.0, -x));
   return ddadd2_d2_d2_d2(r, dd(-g.x, -g.y));

@@ -114,11 +114,11 @@ enum Kind { U64, B64, SC64, U32, B32, SC32, BF, HF };
   X(74, "tanh_u10_f64", U64, derived64::TanhU10) \
   X(75, "tanh_u35_f64", U64, derived64::TanhU35) \
   X(76, "asinh_u10_f64", U64, derived64::AsinhU10) \
-  X(77, "asinh_u35_f64", U64, derived64::AsinhU10) \
+  X(77, "asinh_u35_f64", U64, derived64::AsinhU35) \
   X(78, "acosh_u10_f64", U64, derived64::AcoshU10) \
-  X(79, "acosh_u35_f64", U64, derived64::AcoshU10) \
+  X(79, "acosh_u35_f64", U64, derived64::AcoshU35) \
   X(80, "atanh_u10_f64", U64, derived64::AtanhU10) \
-  X(81, "atanh_u35_f64", U64, derived64::AtanhU10) \
+  X(81, "atanh_u35_f64", U64, derived64::AtanhU35) \
   X(82, "erf_u10_f64", U64, derived64::ErfU10) \
   X(83, "erf_u35_f64", U64, derived64::ErfU35) \
   X(84, "erfc_u10_f64", U64, derived64::ErfcU10) \

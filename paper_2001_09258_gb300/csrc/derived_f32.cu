@@ -36,6 +36,7 @@ constexpr float PIO4F = 0x1.921fb6p-1f, P3O4F = 0x1.2d97c8p+1f;
 constexpr float R_2_PIF = 0x1.45f306p-1f;
 constexpr float LOG2PI_HF = 0x1.d67f1cp-1f, LOG2PI_LF = 0x1.0c97d6p-26f;
 constexpr float LOGPI_HF = 0x1.250d04p+0f, LOGPI_LF = 0x1.1cf438p-25f;
+constexpr float PI_HF = 0x1.921fb6p+1f, PI_LF = -0x1.777a5cp-24f;
 constexpr uint32_t SIGN32 = 0x80000000u, B2P20 = 0x49800000u, B125 = 0x42fa0000u;
 
 constexpr float POWLOG_C1H = 0x1.5555560000000p-4f, POWLOG_C1L = -0x1.556c1c0000000p-29f;
@@ -866,10 +867,15 @@ __device__ __forceinline__ f2 sinpif_ff(float x) {
 __device__ __forceinline__ f2 lgammaf_ff(float x, int &sign) {
   sign = 1;
   if (x > 0.0f) return lgammaf_pos(F2(x, 0.0f));
-  f2 sp = sinpif_ff(x);
+  // |x| < 2^-100: sin(pi x) is pi x to far below an ulp and pi x would lose
+  // its precision in the subnormal range; formed from x 2^64 (exact), with
+  // 64 ln 2 taken off its logarithm
+  bool up = fabsf(x) < 0x1p-100f;
+  f2 sp = up ? mul_f2_f(F2(PI_HF, PI_LF), __fmul_rn(x, 0x1p64f)) : sinpif_ff(x);
   bool negs = sp.x < 0.0f;
   sign = negs ? -1 : 1;
   f2 l = logk_ff(F2(fabsf(sp.x), negs ? -sp.y : sp.y));
+  if (up) l = add_f2f2(l, F2(-0x1.62e4p+5f, -0x1.7f7d1cp-14f));   // - 64 ln 2 (both parts exact)
   f2 r = add_f2f2(F2(LOGPI_HF, LOGPI_LF), fneg(l));
   return add_f2f2(r, fneg(lgammaf_pos(add_ff(1.0f, -x))));
 }

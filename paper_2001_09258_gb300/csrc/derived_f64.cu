@@ -451,6 +451,67 @@ struct AtanhU10 {
   }
 };
 
+// the 3.5-ULP forms: the same DD arguments, their logarithm in double with z
+// corrected once (logm_u20) and e ln 2 added by one fma
+struct AsinhU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_500(x); }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x), ab = bx & ABS64;
+    double ac = ab <= DMAX ? from_bits(ab) : 1.0;
+    bool big = bits(ac) > 0x5F30000000000000ull;   // ac > 2^500
+    d2 arg;
+    if (big) {
+      arg = D2(ac, 0.0);
+    } else {
+      d2 w = sqrt_d2(add_d2_d(mul_dd(ac, ac), 1.0));
+      arg = add_d2_d(w, ac);
+    }
+    int e;
+    double lm = logm_u20(arg, e);
+    double y = __fma_rn(dbl_of(big ? e + 1 : e), L2A, lm);   // log(2 ac) above 2^500
+    if (ab < BM28) y = from_bits(ab);
+    if (ab > DMAX) y = is_nan_b(bx) ? from_bits(QNAN64) : from_bits(INF);
+    return canon(copysign_b(y, bx));
+  }
+};
+struct AcoshU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(double x) { return cls_500(x); }
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x);
+    bool inr = bx >= ONE && bx <= DMAX;              // 1 <= x < inf
+    double xc = inr ? x : 1.0;
+    bool big = bits(xc) > 0x5F30000000000000ull;   // xc > 2^500
+    d2 arg;
+    if (big) {
+      arg = D2(xc, 0.0);
+    } else {
+      d2 d = mul_d2d2(add_dd(xc, -1.0), add_dd(xc, 1.0));
+      arg = add_d2_d(sqrt_d2(d), xc);
+    }
+    int e;
+    double lm = logm_u20(arg, e);
+    double y = __fma_rn(dbl_of(big ? e + 1 : e), L2A, lm);
+    if (bits(xc) == ONE) y = 0.0;
+    if (!inr) y = bx == INF ? from_bits(INF) : from_bits(QNAN64);
+    return canon(y);
+  }
+};
+struct AtanhU35 {
+  __device__ double operator()(double x) const {
+    uint64_t bx = bits(x), ab = bx & ABS64;
+    double ac = ab < ONE ? from_bits(ab) : 0.5;
+    d2 q = div_d2d2(add_dd(1.0, ac), add_dd(1.0, -ac));
+    int e;
+    double lm = logm_u20(q, e);
+    double y = dmul(0.5, __fma_rn(dbl_of(e), L2A, lm));
+    if (ab < BM28) y = from_bits(ab);
+    if (ab >= ONE) y = ab == ONE ? from_bits(INF) : from_bits(QNAN64);
+    return canon(copysign_b(y, bx));
+  }
+};
+
 
 // ---------------- erf, erfc ----------------
 // erf: |x| < 1: x (C0 + T (C1 + T (c2 + t P(t)))), T = x^2 exact, the three
@@ -700,12 +761,12 @@ UNARY64(tanh_u35_f64, TanhU35)
 UNARY64_MASKED(tanh_u35_f64, TanhU35)
 SORTED64(asinh_u10_f64, AsinhU10)
 SORTED64_MASKED(asinh_u10_f64, AsinhU10)
-SORTED64(asinh_u35_f64, AsinhU10)
-SORTED64_MASKED(asinh_u35_f64, AsinhU10)
+SORTED64(asinh_u35_f64, AsinhU35)
+SORTED64_MASKED(asinh_u35_f64, AsinhU35)
 SORTED64(acosh_u10_f64, AcoshU10)
 SORTED64_MASKED(acosh_u10_f64, AcoshU10)
-SORTED64(acosh_u35_f64, AcoshU10)
-SORTED64_MASKED(acosh_u35_f64, AcoshU10)
+SORTED64(acosh_u35_f64, AcoshU35)
+SORTED64_MASKED(acosh_u35_f64, AcoshU35)
 SORTED64(erf_u10_f64, ErfU10)
 SORTED64_MASKED(erf_u10_f64, ErfU10)
 SORTED64(erf_u35_f64, ErfU35)
@@ -716,8 +777,8 @@ SORTED64(erfc_u35_f64, ErfcU10)
 SORTED64_MASKED(erfc_u35_f64, ErfcU10)
 UNARY64(atanh_u10_f64, AtanhU10)
 UNARY64_MASKED(atanh_u10_f64, AtanhU10)
-UNARY64(atanh_u35_f64, AtanhU10)
-UNARY64_MASKED(atanh_u35_f64, AtanhU10)
+UNARY64(atanh_u35_f64, AtanhU35)
+UNARY64_MASKED(atanh_u35_f64, AtanhU35)
 #undef UNARY64
 #undef UNARY64_MASKED
 #undef SORTED64

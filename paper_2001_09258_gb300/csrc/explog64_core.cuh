@@ -156,6 +156,27 @@ __device__ __forceinline__ double logm_u35(d2 a, int &e) {
   return __fma_rn(dmul(z, t), poly(t, kLogU35), z);
 }
 
+// log m in double with z = 2(m-1)/(m+1) corrected once: the residual
+// num - z (1 + m) (the rounding of 1 + m and the DD tail of m included) goes
+// back through the reciprocal, then the 3.5-ULP polynomial; for the 3.5-ULP
+// forms whose logarithm is small against the rounding of its argument
+// (asinh, acosh, atanh)
+__device__ __forceinline__ double logm_u20(d2 a, int &e) {
+  int off = 0;
+  if (lt_c(a.x, 0x1p-1022)) { a = scale_d2(a, 0x1p64); off = 64; }
+  int ex;
+  d2 m = log_mantissa(a, ex);
+  double num = dmul(2.0, __dadd_rn(__dsub_rn(m.x, 1.0), m.y));
+  double den = __dadd_rn(1.0, m.x);
+  double rd = __ddiv_rn(1.0, den);
+  double z = dmul(num, rd);
+  double r = __dsub_rn(__fma_rn(-z, den, num), dmul(z, __dadd_rn(__dadd_rn(__dsub_rn(1.0, den), m.x), m.y)));
+  z = __fma_rn(r, rd, z);
+  double t = dmul(z, z);
+  e = ex - off;
+  return __fma_rn(dmul(z, t), poly(t, kLogU35), z);
+}
+
 // log of a DD y > 0 with the 11-term DD polynomial of pow's logarithm
 // (about 2^-66 relative): m in [0.75, 1.5) from the head, z = 2(m-1)/(m+1)
 // in DD

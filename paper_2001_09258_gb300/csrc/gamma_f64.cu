@@ -29,6 +29,8 @@ using namespace explog64;
 constexpr double LOG2PI_H = 0x1.d67f1c864beb5p-1, LOG2PI_L = -0x1.65b5a1b7ff5dfp-55;   // log(2 pi)/2
 constexpr double LOGPI_H = 0x1.250d048e7a1bdp+0, LOGPI_L = 0x1.7abf2ad8d5088p-57;      // log(pi)
 constexpr double PI_H = 0x1.921fb54442d18p+1, PI_L = 0x1.1a62633145c07p-53;
+// 200 ln 2 as a DD: 200 times the 42-bit head of ln 2 (exact) and RN(200 times its tail)
+constexpr double LN2X200_H = 0x1.1542457337bc0p+7, LN2X200_L = 0x1.82e1c6b73c89ep-37;
 constexpr uint64_t SIGN = 0x8000000000000000ull;
 
 static __constant__ double kLgR2H[4] = {0x1.b0ee6072093cep-2, 0x1.6c58518ef209cp-58, 0x1.4a34cc4a60fa6p-2, 0x1.1b98b7d24eb82p-56};
@@ -126,10 +128,15 @@ __device__ __forceinline__ d2 sinpi_dd(double x) {
 __device__ __forceinline__ d2 lgamma_dd(double x, int &sign) {
   sign = 1;
   if (gt_0(x)) return lgamma_pos(D2(x, 0.0));
-  d2 sp = sinpi_dd(x);
+  // |x| < 2^-900: sin(pi x) is pi x to far below an ulp, and pi x itself
+  // would lose its precision in the subnormal range; it is formed from
+  // x 2^200 (exact) and 200 ln 2 is taken off its logarithm
+  bool up = (bits(x) & ABS64) < 0x07B0000000000000ull;          // |x| < 2^-900
+  d2 sp = up ? mul_d2_d(D2(PI_H, PI_L), dmul(x, 0x1p200)) : sinpi_dd(x);
   bool negs = lt_0(sp.x);
   sign = negs ? -1 : 1;
   d2 l = logk_dd(D2(fabs(sp.x), negs ? -sp.y : sp.y));
+  if (up) l = add_d2d2(l, D2(-LN2X200_H, -LN2X200_L));
   d2 r = add_d2d2(D2(LOGPI_H, LOGPI_L), neg(l));
   d2 g = lgamma_pos(add_dd(1.0, -x));
   return add_d2d2(r, neg(g));

@@ -198,7 +198,9 @@ def test_lgamma_negative_axis():
     |error| <= 2^-51 max(1, |lgamma x|); away from them (|lgamma x| >= 1) it
     is the 1-ULP bound."""
     x = np.concatenate([U("n1", N, -1000, 0), U("n2", N, -5, 0), U("n3", N, -2.5, -2.4),
-                        L("n4", N, 1e-300, 1e-3, signed=False) * -1])
+                        L("n4", N, 1e-300, 1e-3, signed=False) * -1,
+                        L("n5", N, 5e-324, 1e-260, signed=False) * -1,      # pi x subnormal: the 2^200 path
+                        -np.array([5e-324, 1e-320, 2.0 ** -1022, 2.0 ** -900, 2.0 ** -901])])
     x = x[x != np.rint(x)]
     y = oracle.apply("lgamma_u10_f64", x)
     ref = quadref.ref("lgamma", x)

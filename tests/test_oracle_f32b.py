@@ -38,7 +38,8 @@ SETS = {
     "atanh": lambda: [U("a", N, -1, 1), U("b", N, 0.99, 1), L("c", N, 1e-30, 1e-3)],
     "erfc": lambda: [U("a", N, -5, 10.1), U("b", N, -1, 1), U("c", N, 9, 10.1), U("d", N, 0.9, 1.1),
                      U("e", N, 3.8, 4.1)],
-    "tgamma": lambda: [U("a", N, -40, 35.9), U("b", N, 0, 3), L("c", N, 1e-30, 1e-3), U("d", N, -5, 0)],
+    "tgamma": lambda: [U("a", N, -40, 35.9), U("b", N, 0, 3), L("c", N, 1e-30, 1e-3), U("d", N, -5, 0),
+                       L("s", N, 1.4e-45, 1e-30)],
     "lgamma": lambda: [U("a", N, 0, 1000), U("b", N, 0, 3), L("c", N, 1e-30, 4e36, signed=False),
                        U("d", N, 0.99, 1.01), U("e", N, 1.99, 2.01)],
 }
@@ -154,3 +155,21 @@ def test_f32_identities():
             assert np.max(np.abs(a + b - 2)) <= 2.0 ** -22
         else:
             assert np.array_equal(a, -b), fn
+
+
+@needs_quad
+@pytest.mark.parametrize("acc", ["u10", "u35"])
+def test_f32_lgamma_negative_axis(acc):
+    """x < 0 in binary32, tiny negative subnormals included (pi x formed
+    from x 2^64 there): near the zeros of lgamma the absolute bound
+    2^-22 max(1, |lgamma x|) (reading A16), the ULP bound where |lgamma x| >= 1."""
+    x = np.concatenate([U("n1", N, -40, 0), U("n2", N, -5, 0), U("n3", N, -2.5, -2.4),
+                        -L("n4", N, 1e-30, 1e-3, signed=False), -L("n5", N, 1.4e-45, 1e-30, signed=False),
+                        -np.array([1.4e-45, 1e-40, 2.0 ** -126, 2.0 ** -100, 2.0 ** -101])]).astype(F)
+    x = x[x != np.rint(x)]
+    y = oracle.apply(f"lgamma_{acc}_f32", x)
+    ref = quadref.ref("lgamma", x.astype(np.float64))
+    assert np.max(np.abs(y - ref) / np.maximum(1, np.abs(ref))) <= 2.0 ** -22
+    far = np.abs(ref) >= 1
+    err = quadref.ulp_err("lgamma", x[far], y[far])
+    assert err.max() <= BOUND[acc], (x[far][np.argmax(err)], err.max())
