@@ -164,15 +164,16 @@ def launch(sleefcu, name, ins, outs, stream_ptr):
 E2E_CHUNK = 1 << 24          # elements per host-pipeline chunk of the end-to-end step
 
 
-def csrc_sha():
-    """hash of the CUDA sources (every file of csrc/): a stored ncu figure is
-    used only while the kernels it was taken on are unchanged"""
+def csrc_sha(sources=None):
+    """hash of the CUDA sources a stored ncu figure was taken on: the given
+    .cu files and every shared header of csrc/ (all of csrc/ when sources is
+    None); the figure is used only while they are unchanged"""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2001_09258_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         fp = os.path.join(csrc, f)
-        if os.path.isfile(fp):
+        if os.path.isfile(fp) and (sources is None or f in sources or not f.endswith(".cu")):
             h.update(f.encode())
             h.update(open(fp, "rb").read())
     return h.hexdigest()[:16]
@@ -185,7 +186,7 @@ def measured_inst_table(fname):
         rec = json.load(open(os.path.join(ROOT, "profiles", fname)))
     except (OSError, ValueError):
         return None
-    return rec.get("per_entry_point") if csrc_sha() == rec.get("csrc_sha") else None
+    return rec.get("per_entry_point") if csrc_sha(rec.get("sources")) == rec.get("csrc_sha") else None
 
 
 def measured_pipe_counts():
@@ -197,7 +198,7 @@ def measured_pipe_counts():
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    return rec.get("per_entry_point") if csrc_sha() == rec.get("csrc_sha") else None
+    return rec.get("per_entry_point") if csrc_sha(rec.get("sources")) == rec.get("csrc_sha") else None
 
 
 def pipe_peak(sleefcu, torch, device, pipe="fp64"):
@@ -811,7 +812,7 @@ def main():
     if os.path.exists(prof):
         try:
             tr = json.load(open(prof)).get(dom)
-            if tr and tr.get("csrc_sha") == csrc_sha():        # null once any kernel source changed
+            if tr and tr.get("csrc_sha") == csrc_sha([tr["source"]]):   # null once its sources changed
                 roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
         except (OSError, ValueError, KeyError):
             pass

@@ -535,7 +535,7 @@ void sleefcu_batch_destroy(sleefcu_batch *plan);
  * same rules as sleefcu_batch_create; items with n == 0 are skipped).
  * count > 4096 returns SLEEFCU_EINVAL with a message; an unsupported
  * combination SLEEFCU_EUNSUPPORTED; every item is checked before anything
- * is enqueued.  The call enqueues ceil(items with n > 0 / 256) small staging
+ * is enqueued.  The call enqueues ceil(items with n > 0 / 512) small staging
  * kernels, which carry the descriptors as kernel arguments and also zero
  * the tile counter, then the batched kernel, in that order on `stream`, and
  * returns without waiting for the stream (there is no copy from host

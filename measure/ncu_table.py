@@ -6,8 +6,8 @@ in its --list order) into the per-entry-point table bench.py reads:
 For each entry point: executed warp instructions per element
 (smsp__inst_executed.sum / n) and, when captured, FP64 thread instructions
 per element (sm__sass_thread_inst_executed_op_fp64_pred_on.sum / n).  The
-table records a hash of the CUDA sources; bench.py ignores it once they
-change."""
+table records a hash of the family's CUDA sources and the shared headers;
+bench.py ignores it once they change."""
 import argparse
 import csv
 import json
@@ -19,13 +19,19 @@ sys.path.insert(0, ROOT)
 sys.path.insert(0, os.path.join(ROOT, "measure"))
 
 
-def csrc_sha():
+SOURCES = {"f32": ["trig_f32.cu", "explog_f32.cu", "derived_f32.cu"],
+           "f64": ["trig_f64.cu", "explog_f64.cu", "invtrig_f64.cu", "fmod_f64.cu", "derived_f64.cu",
+                   "gamma_f64.cu"]}
+
+
+def csrc_sha(sources):
+    """the hash bench.py checks: the family's .cu files and every shared header"""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2001_09258_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         fp = os.path.join(csrc, f)
-        if os.path.isfile(fp):
+        if os.path.isfile(fp) and (f in sources or not f.endswith(".cu")):
             h.update(f.encode())
             h.update(open(fp, "rb").read())
     return h.hexdigest()[:16]
@@ -56,7 +62,7 @@ def main():
         if "sm__sass_thread_inst_executed_op_fp64_pred_on.sum" in m:
             e["fp64_inst"] = round(m["sm__sass_thread_inst_executed_op_fp64_pred_on.sum"] / a.n, 3)
         out[nm] = e
-    json.dump({"csrc_sha": csrc_sha(), "n": a.n, "family": a.family,
+    json.dump({"csrc_sha": csrc_sha(SOURCES[a.family]), "sources": SOURCES[a.family], "n": a.n, "family": a.family,
                "command": f"python measure/launch_each.py --family {a.family} --n {a.n} under ncu "
                           "--metrics smsp__inst_executed.sum,gpu__time_duration.sum --clock-control none --csv",
                "per_entry_point": out}, sys.stdout, indent=1, sort_keys=True)

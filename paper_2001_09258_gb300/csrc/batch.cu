@@ -472,17 +472,38 @@ const char *kFnNames[SLEEFCU_FN_COUNT] = {"sin",   "cos",   "tan",   "sincos", "
                                           "erfc",  "tgamma", "lgamma"};
 const char *kTypeNames[4] = {"f64", "f32", "bf16", "f16"};
 
+// (fn, dtype, ulp) -> entry point code, and the operands each code needs:
+// tables built once from the entry point names, so that a lookup is one load
+struct CodeTables {
+  short code[SLEEFCU_FN_COUNT][4][2];
+  bool y[kCodes], out2[kCodes];
+  CodeTables() {
+    for (int f = 0; f < SLEEFCU_FN_COUNT; f++)
+      for (int t = 0; t < 4; t++)
+        for (int u = 0; u < 2; u++) {
+          char name[64];
+          snprintf(name, sizeof name, "%s_u%d_%s", kFnNames[f], u ? 35 : 10, kTypeNames[t]);
+          code[f][t][u] = -1;
+          for (int c = 0; c < kCodes; c++)
+            if (!strcmp(kNames[c], name)) code[f][t][u] = (short)c;
+        }
+    for (int c = 0; c < kCodes; c++) {
+      y[c] = strstr(kNames[c], "atan2_") || strstr(kNames[c], "pow_") || strstr(kNames[c], "fmod_") ||
+             strstr(kNames[c], "remainder_");
+      out2[c] = strstr(kNames[c], "sincos_") != nullptr;
+    }
+  }
+};
+const CodeTables &code_tables() {
+  static const CodeTables t;           // thread-safe one-time initialization
+  return t;
+}
 int code_of(const sleefcu_batch_item &it) {
   if (it.fn >= SLEEFCU_FN_COUNT || it.dtype > 3 || (it.ulp != 10 && it.ulp != 35)) return -1;
-  char name[64];
-  snprintf(name, sizeof name, "%s_u%d_%s", kFnNames[it.fn], it.ulp, kTypeNames[it.dtype]);
-  for (int c = 0; c < kCodes; c++)
-    if (!strcmp(kNames[c], name)) return c;
-  return -1;
+  return code_tables().code[it.fn][it.dtype][it.ulp == 35];
 }
-bool needs_y(int code) { return strstr(kNames[code], "atan2_") || strstr(kNames[code], "pow_") ||
-                                strstr(kNames[code], "fmod_") || strstr(kNames[code], "remainder_"); }
-bool needs_out2(int code) { return strstr(kNames[code], "sincos_") != nullptr; }
+bool needs_y(int code) { return code_tables().y[code]; }
+bool needs_out2(int code) { return code_tables().out2[code]; }
 }  // namespace
 
 struct sleefcu_batch {
@@ -760,7 +781,7 @@ void *g_static_dev[kStaticMaxDevices];                     // scratch address pe
 
 namespace sleefcu {
 namespace batch {
-constexpr int kStageItems = 256;
+constexpr int kStageItems = 512;
 // one staging launch: descriptors first .. first+count-1 and their prefix sums
 struct StageChunk {
   Desc desc[kStageItems];
