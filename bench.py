@@ -180,25 +180,21 @@ def csrc_sha(sources=None):
 
 
 def measured_inst_table(fname):
-    """per-entry-point ncu counts from profiles/<fname> (measure/ncu_table.py),
-    or None once the CUDA sources differ from the captured ones"""
+    """per-entry-point ncu counts from profiles/<fname> (measure/ncu_table.py):
+    the entries whose kernel sources are unchanged since the capture"""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", fname)))
     except (OSError, ValueError):
         return None
-    return rec.get("per_entry_point") if csrc_sha(rec.get("sources")) == rec.get("csrc_sha") else None
+    return {k: v for k, v in rec.get("per_entry_point", {}).items()
+            if v.get("csrc_sha") == csrc_sha([v.get("source")])}
 
 
 def measured_pipe_counts():
     """FP64 instructions per element measured by ncu for each FP64 entry point
     (profiles/fp64_inst.json), or None when the kernel sources have changed
     since the capture (the file records a hash of the CUDA sources)."""
-    path = os.path.join(ROOT, "profiles", "fp64_inst.json")
-    try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
-        return None
-    return rec.get("per_entry_point") if csrc_sha(rec.get("sources")) == rec.get("csrc_sha") else None
+    return measured_inst_table("fp64_inst.json")
 
 
 def pipe_peak(sleefcu, torch, device, pipe="fp64"):

@@ -2,12 +2,13 @@
 in its --list order) into the per-entry-point table bench.py reads:
 
     python measure/ncu_table.py --family f32 --n 4194304 launches.csv > profiles/fp32_inst.json
+    python measure/ncu_table.py --family f64 --n 33554432 captures_dir > profiles/fp64_inst.json
 
 For each entry point: executed warp instructions per element
 (smsp__inst_executed.sum / n) and, when captured, FP64 thread instructions
 per element (sm__sass_thread_inst_executed_op_fp64_pred_on.sum / n).  The
-table records a hash of the family's CUDA sources and the shared headers;
-bench.py ignores it once they change."""
+table records, per entry point, a hash of the kernel's .cu file and the
+shared headers; bench.py ignores an entry once they change."""
 import argparse
 import csv
 import json
@@ -22,6 +23,28 @@ sys.path.insert(0, os.path.join(ROOT, "measure"))
 SOURCES = {"f32": ["trig_f32.cu", "explog_f32.cu", "derived_f32.cu"],
            "f64": ["trig_f64.cu", "explog_f64.cu", "invtrig_f64.cu", "fmod_f64.cu", "derived_f64.cu",
                    "gamma_f64.cu"]}
+
+
+def source_of(name):
+    """the .cu file that holds an entry point's kernel"""
+    fn, prec = name.split("_")[0], name.split("_")[-1]
+    if prec == "f64":
+        if fn in ("sin", "cos", "tan", "sincos"):
+            return "trig_f64.cu"
+        if fn in ("asin", "acos", "atan", "atan2"):
+            return "invtrig_f64.cu"
+        if fn in ("exp", "log", "pow"):
+            return "explog_f64.cu"
+        if fn in ("fmod", "remainder"):
+            return "fmod_f64.cu"
+        if fn in ("tgamma", "lgamma"):
+            return "gamma_f64.cu"
+        return "derived_f64.cu"
+    if fn in ("sin", "cos", "tan", "sincos"):
+        return "trig_f32.cu"
+    if fn in ("exp", "log", "log1p", "tanh", "erf"):
+        return "explog_f32.cu"
+    return "derived_f32.cu"
 
 
 def csrc_sha(sources):
@@ -41,16 +64,25 @@ def main():
     p = argparse.ArgumentParser()
     p.add_argument("--family", choices=["f64", "f32"], required=True)
     p.add_argument("--n", type=int, required=True)
-    p.add_argument("csv")
+    p.add_argument("csv", help="one CSV of every launch in --list order, or a directory of <entry point>.csv "
+                                "files with one launch each")
     a = p.parse_args()
     from launch_each import names
     order = names(a.family)
-    rows = {}
-    with open(a.csv) as f:
-        lines = [l for l in f if l.startswith('"')]
-    for r in csv.DictReader(lines):
-        rows.setdefault(int(r["ID"]), {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
-        rows[int(r["ID"])]["kernel"] = r["Kernel Name"]
+
+    def read(path):
+        out = {}
+        with open(path) as f:
+            lines = [l for l in f if l.startswith('"')]
+        for r in csv.DictReader(lines):
+            out.setdefault(int(r["ID"]), {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+            out[int(r["ID"])]["kernel"] = r["Kernel Name"]
+        return out
+
+    if os.path.isdir(a.csv):
+        rows = {i: read(os.path.join(a.csv, nm + ".csv"))[0] for i, nm in enumerate(order)}
+    else:
+        rows = read(a.csv)
     if len(rows) != len(order):
         raise SystemExit(f"{len(rows)} launches in {a.csv}, {len(order)} entry points")
     out = {}
@@ -61,10 +93,12 @@ def main():
             e["warp_inst_per_element"] = round(m["smsp__inst_executed.sum"] / a.n, 4)
         if "sm__sass_thread_inst_executed_op_fp64_pred_on.sum" in m:
             e["fp64_inst"] = round(m["sm__sass_thread_inst_executed_op_fp64_pred_on.sum"] / a.n, 3)
+        e["source"] = source_of(nm)
+        e["csrc_sha"] = csrc_sha([e["source"]])
         out[nm] = e
     json.dump({"csrc_sha": csrc_sha(SOURCES[a.family]), "sources": SOURCES[a.family], "n": a.n, "family": a.family,
-               "command": f"python measure/launch_each.py --family {a.family} --n {a.n} under ncu "
-                          "--metrics smsp__inst_executed.sum,gpu__time_duration.sum --clock-control none --csv",
+               "command": f"python measure/launch_each.py --family {a.family} --n {a.n} [--only NAME] under "
+                          "ncu --metrics <the metrics above>,gpu__time_duration.sum --clock-control none --csv",
                "per_entry_point": out}, sys.stdout, indent=1, sort_keys=True)
     print()
 

@@ -123,8 +123,8 @@ def ops_per_launch(name, x, y=None, steps=None):
 
 def mul_rnd_per_launch(name, x, y=None, steps=None):
     """(multiplications, roundings to integral) of one launch of a binary64
-    entry point: the operations the kernels run in software on the integer
-    pipe (all FP64 families but tgamma / lgamma)"""
+    entry point: the operations the single-array kernels run in software on
+    the integer pipe (all FP64 families but tgamma / lgamma)"""
     return _per_launch(name, x, y, steps, "mul"), _per_launch(name, x, y, steps, "rnd")
 
 

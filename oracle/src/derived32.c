@@ -217,9 +217,53 @@ float oracle_atanh_u10_f32(float x) {
   if (!(a < 1.0f)) y = a == 1.0f ? INFINITY : NAN;
   return canonf(copysignf(y, x));
 }
-float oracle_asinh_u35_f32(float x) { return oracle_asinh_u10_f32(x); }
-float oracle_acosh_u35_f32(float x) { return oracle_acosh_u10_f32(x); }
-float oracle_atanh_u35_f32(float x) { return oracle_atanh_u10_f32(x); }
+/* 3.5-ULP forms: the same FF arguments, their logarithm in binary32 with z
+ * corrected once (oracle_logmf_u20) and e ln 2 added by one fma; above 2^60
+ * log(2x) = (e + 1) ln 2 + log m */
+float oracle_asinh_u35_f32(float x) {
+  float a = fabsf(x);
+  float ac = a <= FLT_MAXF ? a : 1.0f;
+  int e;
+  float lm;
+  if (ac > 0x1p60f) {
+    lm = oracle_logmf_u20(ff(ac, 0.0f), &e);
+    e += 1;
+  } else {
+    ff_t w = ffsqrt_f2_f2(ffadd2_f2_f2_f(ffmul_f2_f_f(ac, ac), 1.0f));
+    lm = oracle_logmf_u20(ffadd2_f2_f2_f(w, ac), &e);
+  }
+  float y = fmaf((float)e, L2AF, lm);
+  if (a < 0x1p-12f) y = a;
+  if (!(a <= FLT_MAXF)) y = isnan(x) ? NAN : INFINITY;
+  return canonf(copysignf(y, x));
+}
+float oracle_acosh_u35_f32(float x) {
+  float xc = (x >= 1.0f && x <= FLT_MAXF) ? x : 1.0f;
+  int e;
+  float lm;
+  if (xc > 0x1p60f) {
+    lm = oracle_logmf_u20(ff(xc, 0.0f), &e);
+    e += 1;
+  } else {
+    ff_t d = ffmul_f2_f2_f2(ffadd2_f2_f_f(xc, -1.0f), ffadd2_f2_f_f(xc, 1.0f));
+    lm = oracle_logmf_u20(ffadd2_f2_f2_f(ffsqrt_f2_f2(d), xc), &e);
+  }
+  float y = fmaf((float)e, L2AF, lm);
+  if (xc == 1.0f) y = 0.0f;
+  if (!(x >= 1.0f && x <= FLT_MAXF)) y = x == INFINITY ? INFINITY : NAN;
+  return canonf(y);
+}
+float oracle_atanh_u35_f32(float x) {
+  float a = fabsf(x);
+  float ac = a < 1.0f ? a : 0.5f;
+  ff_t q = ffdiv_f2_f2_f2(ffadd2_f2_f_f(1.0f, ac), ffadd2_f2_f_f(1.0f, -ac));
+  int e;
+  float lm = oracle_logmf_u20(q, &e);
+  float y = 0.5f * fmaf((float)e, L2AF, lm);
+  if (a < 0x1p-12f) y = a;
+  if (!(a < 1.0f)) y = a == 1.0f ? INFINITY : NAN;
+  return canonf(copysignf(y, x));
+}
 
 /* ---------------- pow ---------------- */
 /* e^Y for an FF Y: overflow to +inf, underflow with subnormals rounded once */

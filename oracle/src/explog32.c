@@ -289,6 +289,25 @@ ff_t oracle_logmf_u10(ff_t a, int *ep) {
   return ffadd_f2_f2_f(z, corr);
 }
 
+/* log m in binary32 with z = 2(m-1)/(m+1) corrected once: the residual
+ * num - z (1 + m) (the rounding of 1 + m and the FF tail included) goes back
+ * through the reciprocal, then the 3.5-ULP polynomial (the 3.5-ULP forms of
+ * asinh, acosh, atanh) */
+float oracle_logmf_u20(ff_t a, int *ep) {
+  int e;
+  float m = logf_reduce(a.x, &e);
+  float ml = ldexpf(a.y, -e);
+  float num = 2.0f * ((m - 1.0f) + ml);
+  float den = 1.0f + m;
+  float rd = 1.0f / den;
+  float z = num * rd;
+  float r = fmaf(-z, den, num) - z * (((1.0f - den) + m) + ml);
+  z = fmaf(r, rd, z);
+  float t = z * z;
+  *ep = e;
+  return fmaf(z * t, poly_f(t, LOGF_U35, 3), z);
+}
+
 /* log of an FF a > 0 as an FF pair: e ln2 + log m with the FF core */
 ff_t oracle_logf_ff(ff_t a) {
   int e;

@@ -14,6 +14,7 @@ float oracle_expf_tail_u10(float r, float rl, float k);
 ff_t oracle_expf_parts(ff_t a, float *k);
 ff_t oracle_expm1f_s(float a, float *k);
 ff_t oracle_logmf_u10(ff_t a, int *e);
+float oracle_logmf_u20(ff_t a, int *e);
 ff_t oracle_logf_ff(ff_t a);
 ff_t oracle_logkf(ff_t a);
 ff_t oracle_erfcf_L(float x);

@@ -237,6 +237,40 @@ double oracle_tan_u10_f64(double d) {
   return canon(r);
 }
 
+/* a / b within about a unit of the correctly rounded quotient (reading
+ * R35): the reciprocal of b's significand from its binary32 reciprocal
+ * (significand truncated to 24 bits, exact widening) and two Newton steps
+ * with fma, scaled by 2^-ilogb|b|, the quotient a r and one fma correction
+ * q + (a - q b) r; b outside [2^-1000, 2^1000] (zero, subnormal, huge, not
+ * finite) takes the IEEE division */
+static double div_u35(double a, double b) {
+  double ab = fabs(b);
+  if (!(ab >= 0x1p-1000 && ab <= 0x1p1000)) return a / b;
+  uint64_t bb = dbits(ab), man = bb & 0x000FFFFFFFFFFFFFULL;
+  int e = (int)(bb >> 52) - 1023;
+  uint64_t mb = 0x3FF0000000000000ULL | man;
+  uint32_t fb = 0x3F800000U | (uint32_t)(man >> 29);
+  double m;
+  float mf;
+  memcpy(&m, &mb, 8);
+  memcpy(&mf, &fb, 4);
+  float rf = 1.0f / mf;
+  uint32_t rb = fbits(rf);
+  uint64_t yb = ((uint64_t)((rb >> 23) + 896) << 52) | ((uint64_t)(rb & 0x7FFFFF) << 29);
+  double y;
+  memcpy(&y, &yb, 8);
+  double t = fma(-m, y, 1.0);
+  y = fma(y, t, y);
+  t = fma(-m, y, 1.0);
+  y = fma(y, t, y);                                         /* 1/m to about an ulp */
+  uint64_t rbits = dbits(y) - ((uint64_t)(int64_t)e << 52);
+  double r;
+  memcpy(&r, &rbits, 8);
+  if (b < 0) r = -r;
+  double q = a * r;
+  return fma(fma(-q, b, a), r, q);
+}
+
 /* u35: the same polynomial in double, one division for the reconstruction */
 double oracle_tan_u35_f64(double d) {
   int q;
@@ -245,7 +279,7 @@ double oracle_tan_u35_f64(double d) {
   double u = fma(poly_d(t, TAN_C, 8), t, TAN_C3);
   double tt = fma(y * t, u, y);
   double num = tt + tt, den = fma(-tt, tt, 1.0);
-  double r = (q & 1) ? -den / num : num / den;
+  double r = (q & 1) ? div_u35(-den, num) : div_u35(num, den);
   if (d == 0) r = d;
   return canon(r);
 }

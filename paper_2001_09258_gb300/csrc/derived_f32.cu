@@ -408,6 +408,86 @@ struct AtanhU10 {
     return canonf(csign(y, bx));
   }
 };
+// log m in binary32 with z = 2(m-1)/(m+1) corrected once (the residual
+// num - z (1 + m), the rounding of 1 + m and the FF tail included, back
+// through the reciprocal), then the 3.5-ULP polynomial
+__device__ __forceinline__ float logm_u20(f2 a, int &e) {
+  float m = log_reduce(fbits(a.x), e);
+  float ml = ldexp_small(a.y, e);
+  float num = __fmul_rn(2.0f, __fadd_rn(__fsub_rn(m, 1.0f), ml));
+  float den = __fadd_rn(1.0f, m);
+  float rd = __frcp_rn(den);
+  float z = __fmul_rn(num, rd);
+  float r = __fsub_rn(__fmaf_rn(-z, den, num), __fmul_rn(z, __fadd_rn(__fadd_rn(__fsub_rn(1.0f, den), m), ml)));
+  z = __fmaf_rn(r, rd, z);
+  float t = __fmul_rn(z, z);
+  return __fmaf_rn(__fmul_rn(z, t), polyf(t, kLogU35), z);
+}
+// the 3.5-ULP forms: the same FF arguments, their logarithm with logm_u20
+// and e ln 2 added by one fma (log(2x) = (e + 1) ln 2 + log m above 2^60)
+struct AsinhU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 0x1p60f; }
+  static constexpr bool DEFER = true;
+  static constexpr float kStandIn = 0x1p61f;
+  __device__ static bool defer(float x) { return !((fbits(x) & ABS32) > 0x5D800000u && (fbits(x) & ABS32) <= FMAX); }
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    float a = fabsf(x);
+    float ac = (fbits(a) <= FMAX) ? a : 1.0f;
+    int e;
+    float lm;
+    bool big = ac > 0x1p60f;
+    if (big) {
+      lm = logm_u20(F2(ac, 0.0f), e);
+    } else {
+      f2 w = sqrt_f2(add_f2_f(mul_ff(ac, ac), 1.0f));
+      lm = logm_u20(add_f2_f(w, ac), e);
+    }
+    float y = __fmaf_rn(fl_of(big ? e + 1 : e), L2AF, lm);
+    if (a < 0x1p-12f) y = a;
+    if (!(fbits(a) <= FMAX)) y = isnan_f(x) ? from_fbits(QNAN32) : from_fbits(INF);
+    return canonf(csign(y, bx));
+  }
+};
+struct AcoshU35 {
+  static constexpr int NCLS = 2;
+  __device__ static int cls(float x) { return fabsf(x) > 0x1p60f; }
+  static constexpr bool DEFER = true;
+  static constexpr float kStandIn = 0x1p61f;
+  __device__ static bool defer(float x) { return !(fbits(x) > 0x5D800000u && fbits(x) <= FMAX); }
+  __device__ float operator()(float x) const {
+    bool inr = x >= 1.0f && fbits(x) <= FMAX;
+    float xc = inr ? x : 1.0f;
+    int e;
+    float lm;
+    bool big = xc > 0x1p60f;
+    if (big) {
+      lm = logm_u20(F2(xc, 0.0f), e);
+    } else {
+      f2 d = mul_f2f2(add_ff(xc, -1.0f), add_ff(xc, 1.0f));
+      lm = logm_u20(add_f2_f(sqrt_f2(d), xc), e);
+    }
+    float y = __fmaf_rn(fl_of(big ? e + 1 : e), L2AF, lm);
+    if (xc == 1.0f) y = 0.0f;
+    if (!inr) y = fbits(x) == INF ? from_fbits(INF) : from_fbits(QNAN32);
+    return canonf(y);
+  }
+};
+struct AtanhU35 {
+  __device__ float operator()(float x) const {
+    uint32_t bx = fbits(x);
+    float a = fabsf(x);
+    float ac = a < 1.0f ? a : 0.5f;
+    f2 q = div_f2f2(add_ff(1.0f, ac), add_ff(1.0f, -ac));
+    int e;
+    float lm = logm_u20(q, e);
+    float y = __fmul_rn(0.5f, __fmaf_rn(fl_of(e), L2AF, lm));
+    if (a < 0x1p-12f) y = a;
+    if (!(a < 1.0f)) y = a == 1.0f ? from_fbits(INF) : from_fbits(QNAN32);
+    return canonf(csign(y, bx));
+  }
+};
 
 // ---------------- pow ----------------
 __device__ __forceinline__ float expkf(f2 Y) {
@@ -985,11 +1065,11 @@ UNARY32(sinh_u35_f32, SinhU10)
 UNARY32(cosh_u10_f32, CoshU10)
 UNARY32(cosh_u35_f32, CoshU10)
 UNARY32(asinh_u10_f32, AsinhU10)
-UNARY32(asinh_u35_f32, AsinhU10)
+UNARY32(asinh_u35_f32, AsinhU35)
 UNARY32(acosh_u10_f32, AcoshU10)
-UNARY32(acosh_u35_f32, AcoshU10)
+UNARY32(acosh_u35_f32, AcoshU35)
 UNARY32(atanh_u10_f32, AtanhU10)
-UNARY32(atanh_u35_f32, AtanhU10)
+UNARY32(atanh_u35_f32, AtanhU35)
 UNARY32(erfc_u10_f32, ErfcU10)
 UNARY32(erfc_u35_f32, ErfcU10)
 BINARY32(fmod_u10_f32, FmodF)

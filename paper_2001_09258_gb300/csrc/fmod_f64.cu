@@ -9,7 +9,7 @@
 // limit): each step divides by D = d 2^j, j = max(kmin, ilogb(r) - ilogb(d) -
 // 1000), which is the listing itself whenever n/d < 2^1000; a subnormal d
 // (kmin = 54) is rescaled by 2^54 once r < d 2^54, as in the listing.
-// Elements are grouped in divergence-sorted tiles by their expected trip
+// Elements are grouped in divergence-sorted 2048-element tiles by their expected trip
 // count ceil((ilogb n - ilogb d) / 52) (48 classes), so the lanes of a warp leave the loop
 // together (the listing's "terminate once every element of the vector is
 // done").  Comparisons of the non-negative operands run on the integer pipe.
@@ -112,6 +112,10 @@ __device__ __forceinline__ int trip_class(double x, double y) {
 
 struct FmodF {
   static constexpr int NCLS = kTripClasses;
+  // 2048-element tiles: the long-division tail spreads over some twenty trip
+  // classes, and a larger tile puts more lanes of one class in a warp
+  // (measured on the full-FP64-set mix: 12.3 -> 14.0 Gelem/s against 1024)
+  static constexpr int SORT_EPT = 8;
   __device__ static int cls(double x, double y) { return trip_class(x, y); }
   __device__ double operator()(double x, double y) const {
     uint64_t bx = bits(x), by = bits(y);
@@ -127,6 +131,7 @@ struct FmodF {
 
 struct RemainderF {
   static constexpr int NCLS = kTripClasses;
+  static constexpr int SORT_EPT = 8;                 // as FmodF (13.8 -> 15.2 Gelem/s)
   __device__ static int cls(double x, double y) { return trip_class(x, y); }
   __device__ double operator()(double x, double y) const {
     uint64_t bx = bits(x), by = bits(y);

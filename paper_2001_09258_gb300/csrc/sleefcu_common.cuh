@@ -389,22 +389,22 @@ __global__ void __launch_bounds__(kBlock, sort_minb<F>::value) k_sorted64(const 
 template <class F, bool MASKED = false>
 __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const double *y, double *o, size_t n,
                                                       const uint8_t *mask = nullptr) {
-  constexpr int NC = F::NCLS;
-  __shared__ double sx[kSortTile];
-  __shared__ double sy[kSortTile];
-  __shared__ unsigned short sidx[kSortTile];
+  constexpr int NC = F::NCLS, EPT = sort_ept<F>::value, TILE = kBlock * EPT;
+  __shared__ double sx[TILE];
+  __shared__ double sy[TILE];
+  __shared__ unsigned short sidx[TILE];
   __shared__ int cnt[NC], cur[NC], tot;
   F f;
   const int tid = threadIdx.x;
-  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const size_t ntiles = (n + TILE - 1) / TILE;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const size_t base = tile * kSortTile;
-    const int valid = (int)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+    const size_t base = tile * TILE;
+    const int valid = (int)((n - base) < (size_t)TILE ? (n - base) : (size_t)TILE);
     if (tid < NC) cnt[tid] = 0;
     __syncthreads();
-    int cl[kSortEPT];
+    int cl[EPT];
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
       double a = 0.0, b = 0.0;
       if (e < valid && (!MASKED || mask[base + e])) {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
       sx[e] = a;
       sy[e] = b;
     }
-    sort_count<NC, kSortEPT>(cl, cnt, tid);
+    sort_count<NC, EPT>(cl, cnt, tid);
     __syncthreads();
     if (tid == 0) {
       int acc = 0;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
       tot = acc;
     }
     __syncthreads();
-    sort_scatter<NC, kSortEPT>(cl, cur, sidx, tid);
+    sort_scatter<NC, EPT>(cl, cur, sidx, tid);
     __syncthreads();
     const int m = MASKED ? tot : valid;
     for (int k = tid; k < m; k += kBlock) {
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kBlock) k_sorted64b(const double *x, const dou
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortEPT; j++) {
+    for (int j = 0; j < EPT; j++) {
       int e = j * kBlock + tid;
       if (e < valid && (!MASKED || mask[base + e])) __stcs(o + base + e, sx[e]);
     }
@@ -545,7 +545,8 @@ sleefcu_status launch_sorted64b(const char *name, const double *x, const double 
   if (!x || !y || !out) { set_error("%s: null pointer with n = %zu", name, n); return SLEEFCU_EINVAL; }
   if (sleefcu_status rc_ = check_args(name, n, x, y, out)) return rc_;
   auto k = k_sorted64b<F>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, nullptr);
+  constexpr int EPT = sort_ept<F>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, nullptr);
   return check_launch(name);
 }
 
@@ -597,7 +598,8 @@ sleefcu_status launch_masked64b(const char *name, const double *x, const double 
   if (sleefcu_status rc_ = check_args(name, n, x, y, mask, out)) return rc_;
   using G = sortable_t<F>;
   auto k = k_sorted64b<G, true>;
-  k<<<grid_for((const void *)k, (n + kSortEPT - 1) / kSortEPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, mask);
+  constexpr int EPT = sort_ept<G>::value;
+  k<<<grid_for((const void *)k, (n + EPT - 1) / EPT), kBlock, 0, (cudaStream_t)s>>>(x, y, out, n, mask);
   return check_launch(name);
 }
 

@@ -291,6 +291,29 @@ struct TanU10 {
     return canon(r);
   }
 };
+// a / b within about a unit of the correctly rounded quotient: the
+// reciprocal of b's significand from the binary32 reciprocal (significand
+// truncated to 24 bits, widened exactly) and two Newton steps with fma,
+// scaled by 2^-ilogb|b|, then q = a r and one fma correction q + (a - q b) r:
+// six FP64-pipe operations and a software multiply instead of a correctly
+// rounded division; b outside [2^-1000, 2^1000] takes the IEEE division
+__device__ __forceinline__ double div_u35(double a, double b) {
+  const uint64_t bb = bits(b) & ABS64;
+  if (!(bb >= 0x0170000000000000ull && bb <= 0x7E70000000000000ull)) return __ddiv_rn(a, b);
+  const uint64_t man = bb & 0x000FFFFFFFFFFFFFull;
+  const int e = (int)(bb >> 52) - 1023;
+  const double m = from_bits(0x3FF0000000000000ull | man);
+  const uint32_t rb = fbits(__frcp_rn(from_fbits(0x3F800000u | (uint32_t)(man >> 29))));
+  double y = from_bits(((uint64_t)((rb >> 23) + 896) << 52) | ((uint64_t)(rb & 0x7FFFFFu) << 29));
+  double t = __fma_rn(-m, y, 1.0);
+  y = __fma_rn(y, t, y);
+  t = __fma_rn(-m, y, 1.0);
+  y = __fma_rn(y, t, y);                                       // 1/m to about an ulp
+  const double r = neg_if(from_bits(bits(y) - ((uint64_t)(int64_t)e << 52)), (bits(b) >> 63) != 0);
+  const double q = dmul(a, r);
+  return __fma_rn(__fma_rn(-q, b, a), r, q);
+}
+
 struct TanU35 {
   TRIG_PATHS
   __device__ double operator()(double d) const {
@@ -301,7 +324,7 @@ struct TanU35 {
     double u = __fma_rn(poly(t, kTanC), t, TAN_C3);
     double tt = __fma_rn(dmul(y, t), u, y);
     double num = __dadd_rn(tt, tt), den = __fma_rn(-tt, tt, 1.0);
-    double r = (q & 1) ? __ddiv_rn(-den, num) : __ddiv_rn(num, den);
+    double r = (q & 1) ? div_u35(-den, num) : div_u35(num, den);
     if (ab == 0) r = d;
     return canon(r);
   }
