@@ -754,7 +754,8 @@ def main():
         dv, sq = opcounts.div_sqrt_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
         mu, rn = opcounts.mul_rnd_per_launch(name, hx[0], hx[1] if len(hx) > 1 else None, st_)
         # the operations left on the FP64 pipe: multiplications and roundings
-        # run in software on the integer pipe except in the gamma kernels
+        # run in software on the integer pipe (except where a translation
+        # unit keeps them on the FP64 pipe, opcounts.HW_MUL_FUNCS)
         pipe_ops = o if fn in opcounts.HW_MUL_FUNCS else o - mu - rn
         per_roof[name] = {"ops_per_element": round(o / n, 2),
                           "div_per_element": round(dv / n, 3), "sqrt_per_element": round(sq / n, 3),

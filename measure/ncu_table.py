@@ -8,7 +8,15 @@ For each entry point: executed warp instructions per element
 (smsp__inst_executed.sum / n) and, when captured, FP64 thread instructions
 per element (sm__sass_thread_inst_executed_op_fp64_pred_on.sum / n).  The
 table records, per entry point, a hash of the kernel's .cu file and the
-shared headers; bench.py ignores an entry once they change."""
+shared headers; bench.py ignores an entry once they change.  The hashes are
+those of the sources the captures ran: write them beside the captures, on
+the machine that runs them, before capturing,
+
+    python measure/ncu_table.py --stamp captures_dir
+
+and the table takes them from captures_dir/csrc_sha.json (or from the
+csrc_sha.json beside a single CSV); --assume-local-sources takes the local
+sources' hashes instead, for captures made from the local tree unchanged."""
 import argparse
 import csv
 import json
@@ -22,7 +30,7 @@ sys.path.insert(0, os.path.join(ROOT, "measure"))
 
 SOURCES = {"f32": ["trig_f32.cu", "explog_f32.cu", "derived_f32.cu"],
            "f64": ["trig_f64.cu", "explog_f64.cu", "invtrig_f64.cu", "fmod_f64.cu", "derived_f64.cu",
-                   "gamma_f64.cu"]}
+                   "gamma_f64.cu", "pow_f64.cu"]}
 
 
 def source_of(name):
@@ -33,8 +41,10 @@ def source_of(name):
             return "trig_f64.cu"
         if fn in ("asin", "acos", "atan", "atan2"):
             return "invtrig_f64.cu"
-        if fn in ("exp", "log", "pow"):
+        if fn in ("exp", "log"):
             return "explog_f64.cu"
+        if fn == "pow":
+            return "pow_f64.cu"
         if fn in ("fmod", "remainder"):
             return "fmod_f64.cu"
         if fn in ("tgamma", "lgamma"):
@@ -60,13 +70,41 @@ def csrc_sha(sources):
     return h.hexdigest()[:16]
 
 
+def stamp(path):
+    """record the hashes of the sources as they are now (before a capture)"""
+    os.makedirs(path, exist_ok=True)
+    srcs = sorted(set(SOURCES["f32"]) | set(SOURCES["f64"]))
+    out = {src: csrc_sha([src]) for src in srcs}
+    out.update({f"family:{k}": csrc_sha(v) for k, v in SOURCES.items()})
+    with open(os.path.join(path, "csrc_sha.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+
+
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--stamp":
+        stamp(sys.argv[2])
+        return
     p = argparse.ArgumentParser()
     p.add_argument("--family", choices=["f64", "f32"], required=True)
     p.add_argument("--n", type=int, required=True)
+    p.add_argument("--assume-local-sources", action="store_true",
+                   help="hash the local sources (no csrc_sha.json was written at capture time)")
     p.add_argument("csv", help="one CSV of every launch in --list order, or a directory of <entry point>.csv "
                                 "files with one launch each")
     a = p.parse_args()
+    sdir = a.csv if os.path.isdir(a.csv) else os.path.dirname(os.path.abspath(a.csv))
+    spath = os.path.join(sdir, "csrc_sha.json")
+    if os.path.exists(spath):
+        with open(spath) as f:
+            stamped = json.load(f)
+        sha_of = lambda src: stamped[src]
+        family_sha = stamped[f"family:{a.family}"]
+    elif a.assume_local_sources:
+        sha_of = lambda src: csrc_sha([src])
+        family_sha = csrc_sha(SOURCES[a.family])
+    else:
+        raise SystemExit(f"{spath} missing: run `ncu_table.py --stamp` where the captures run, "
+                         "or pass --assume-local-sources")
     from launch_each import names
     order = names(a.family)
 
@@ -94,9 +132,9 @@ def main():
         if "sm__sass_thread_inst_executed_op_fp64_pred_on.sum" in m:
             e["fp64_inst"] = round(m["sm__sass_thread_inst_executed_op_fp64_pred_on.sum"] / a.n, 3)
         e["source"] = source_of(nm)
-        e["csrc_sha"] = csrc_sha([e["source"]])
+        e["csrc_sha"] = sha_of(e["source"])
         out[nm] = e
-    json.dump({"csrc_sha": csrc_sha(SOURCES[a.family]), "sources": SOURCES[a.family], "n": a.n, "family": a.family,
+    json.dump({"csrc_sha": family_sha, "sources": SOURCES[a.family], "n": a.n, "family": a.family,
                "command": f"python measure/launch_each.py --family {a.family} --n {a.n} [--only NAME] under "
                           "ncu --metrics <the metrics above>,gpu__time_duration.sum --clock-control none --csv",
                "per_entry_point": out}, sys.stdout, indent=1, sort_keys=True)

@@ -129,8 +129,8 @@ def mul_rnd_per_launch(name, x, y=None, steps=None):
 
 
 # entry points whose multiplications stay on the FP64 pipe (their translation
-# unit is compiled with SLEEFCU_SOFT_MUL 0)
-HW_MUL_FUNCS = ("tgamma", "lgamma")
+# unit is compiled with SLEEFCU_SOFT_MUL 0): none of the single-array kernels
+HW_MUL_FUNCS = ()
 
 
 def div_sqrt_per_launch(name, x, y=None, steps=None):

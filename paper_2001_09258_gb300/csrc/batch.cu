@@ -20,6 +20,7 @@
 #define SLEEFCU_FUNCTORS_ONLY
 #include "trig_f64.cu"
 #include "explog_f64.cu"
+#include "pow_f64.cu"
 #include "invtrig_f64.cu"
 #include "fmod_f64.cu"
 #include "trig_f32.cu"

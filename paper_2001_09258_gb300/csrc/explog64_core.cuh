@@ -126,6 +126,20 @@ __device__ __forceinline__ double expk(d2 Y) {
   return y;
 }
 
+// a = bits of a finite positive double: m in [0.75, 1.5) and e with a = m 2^e
+__device__ __forceinline__ double log_reduce(uint64_t a, int &e) {
+  int off = 0;
+  if (a < 0x0010000000000000ull) {                // subnormal: scale by 2^64 (exact)
+    a = bits(dmul(from_bits(a), 0x1p64));
+    off = 64;
+  }
+  int ex = (int)(a >> 52) - 1023;
+  uint64_t mb = (a & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;   // significand in [1, 2)
+  if (mb & 0x0008000000000000ull) { mb -= 0x0010000000000000ull; ex++; } // >= 1.5: halve
+  e = ex - off;
+  return from_bits(mb);
+}
+
 // log of a DD a > 0 with a finite head: a = m 2^e, m in [0.75, 1.5) (heads
 // below DBL_MIN scaled by 2^64 first); returns log m = z + z^3 P(z^2) as a DD
 // with z = 2(m-1)/(m+1) in DD (Section 5.5 on a DD argument)

@@ -12,13 +12,15 @@
 // tgamma = sign * exp(L) with L the DD log-gamma.  Lanes are grouped by path
 // in sorted tiles (the shift path runs a loop of up to seven DD products).
 //
-// Multiplications and roundings to integral stay on the FP64 pipe here
-// (SLEEFCU_SOFT_MUL 0 for this translation unit): measured on GB300, the
-// software forms made these kernels slower (tgamma 2.08 -> 1.44 Gelem/s,
-// 1.53 even with four resident blocks), unlike every other FP64 family.
-// The results are the same bits either way.
+// Multiplications run in software on the integer pipe through one
+// out-of-line copy of the exact multiply (SLEEFCU_SOFT_MUL 2 for this
+// translation unit), with four resident blocks per SM.  Measured on GB300
+// on 2^25 elements of the full-set workload: tgamma 2.09 Gelem/s with the
+// FP64 pipe's multiply, 1.45 with the software multiply inlined at its many
+// call sites (the paths of eight classes in one kernel), 2.42 out of line;
+// lgamma 4.46, 3.74, 5.37.  The results are the same bits in all three.
 #ifndef SLEEFCU_FUNCTORS_ONLY
-#define SLEEFCU_SOFT_MUL 0
+#define SLEEFCU_SOFT_MUL 2
 #endif
 #include "explog64_core.cuh"
 
@@ -160,6 +162,7 @@ __device__ __forceinline__ bool neg_int(double x) {   // x < 0 and an integer (-
 struct LgammaU10 {
   static constexpr int NCLS = 9;
   static constexpr int SORT_EPT = 16;   // 4096-element tiles: nine classes, several of them small
+  static constexpr int MIN_BLOCKS = 4;  // 64 registers: four 256-thread blocks per SM
   // class 8: x >= 2^60, Stirling's form without its two smallest terms
   __device__ static int cls(double x) {
     const int c = gamma_cls(x);
@@ -192,6 +195,7 @@ constexpr uint64_t G2M900 = 0x07B0000000000000ull;   // 2^-900
 struct TgammaU10 {
   static constexpr int NCLS = 8;
   static constexpr int SORT_EPT = 16;   // 4096-element tiles: eight classes, several of them small
+  static constexpr int MIN_BLOCKS = 4;  // 64 registers: four 256-thread blocks per SM
   __device__ static int cls(double x) { return gamma_cls(x); }
   __device__ double operator()(double x) const {
     uint64_t bx = bits(x);

@@ -13,16 +13,29 @@
 // Binary64 multiplication and rounding to an integral value (rint, trunc) in the kernels:
 // exact software forms on the integer pipe (softfp64.cuh), bit-identical to
 // the FP64 pipe's, so that the FP64 pipe, the bottleneck of the FP64 family
-// on GB300, keeps only the additions and fused multiply-adds.  Compiling
-// with -DSLEEFCU_SOFT_MUL=0 issues them to the FP64 pipe instead (same bits).
+// on GB300, keeps only the additions and fused multiply-adds.  A translation
+// unit chooses by defining SLEEFCU_SOFT_MUL before this header:
+//   1 (default)  the software multiply inlined at each call site
+//   2            one out-of-line copy of it, called from every site (large
+//                kernels with many multiplications: the inlined copies cost
+//                more instruction fetch than the call)
+//   0            multiplications and roundings on the FP64 pipe
+// All three give the same bits.
 #ifndef SLEEFCU_SOFT_MUL
 #define SLEEFCU_SOFT_MUL 1
 #endif
 
 namespace sleefcu {
 
+#if SLEEFCU_SOFT_MUL == 2
+static __device__ __noinline__ uint64_t dmul_call(uint64_t a, uint64_t b) { return soft::mul(a, b); }
+#endif
+
 __device__ __forceinline__ double dmul(double a, double b) {
-#if SLEEFCU_SOFT_MUL
+#if SLEEFCU_SOFT_MUL == 2
+  return __longlong_as_double((long long)dmul_call((uint64_t)__double_as_longlong(a),
+                                                   (uint64_t)__double_as_longlong(b)));
+#elif SLEEFCU_SOFT_MUL
   return __longlong_as_double((long long)soft::mul((uint64_t)__double_as_longlong(a),
                                                    (uint64_t)__double_as_longlong(b)));
 #else
