@@ -10,7 +10,7 @@
 // 1000), which is the listing itself whenever n/d < 2^1000; a subnormal d
 // (kmin = 54) is rescaled by 2^54 once r < d 2^54, as in the listing.
 // Elements are grouped in divergence-sorted 2048-element tiles by their expected trip
-// count ceil((ilogb n - ilogb d) / 52) (48 classes), so the lanes of a warp leave the loop
+// count (48 classes, trip_class), so the lanes of a warp leave the loop
 // together (the listing's "terminate once every element of the vector is
 // done").  Comparisons of the non-negative operands run on the integer pipe.
 //
@@ -101,13 +101,31 @@ __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = null
   return ret;
 }
 
-// expected trip-count class of |x| mod |y| (for the tile sort): one class
-// per step count up to the 44-step maximum
+// expected trip count of n mod d (bits of n >= 0 and of the divisor d > 0;
+// for the tile sort only, the results do not depend on it): none when
+// n < d or the operands are not a division; otherwise 1 + floor(2 (ilogb n
+// - ilogb d) / 101).  Each step of the loop removes about 50.5 bits of the
+// exponent difference (53 bits of quotient less what the truncated quotient
+// of a reciprocal at most 1/d and nextafter(r, 0) gives up), and n >= d
+// with equal exponents takes one step: on the full-set workload this
+// estimate equals the oracle's step count for 99 % of the elements, against
+// 85 % for ceil((ilogb n - ilogb d) / 52), which put equal-exponent
+// operands (a quarter of the array, half of them needing a step) with the
+// elements that need none.
 constexpr int kTripClasses = 48;
+__device__ __forceinline__ int trip_class_b(uint64_t an, uint64_t ad) {
+  if (an >= INF || ad == 0 || ad >= INF || an < ad) return 0;
+  int t = 1 + 2 * (ilogb_n(an) - ilogb_n(ad)) / 101;
+  return t > kTripClasses - 1 ? kTripClasses - 1 : t;
+}
 __device__ __forceinline__ int trip_class(double x, double y) {
-  int en = ilogb_n(bits(x) & ABS64), ed = ilogb_n(bits(y) & ABS64);
-  int t = (en - ed + 51) / 52;
-  return t < 0 ? 0 : (t > kTripClasses - 1 ? kTripClasses - 1 : t);
+  return trip_class_b(bits(x) & ABS64, bits(y) & ABS64);
+}
+// remainder divides by 2|y| (no step when y is zero or 2|y| overflows)
+__device__ __forceinline__ int trip_class_rem(double x, double y) {
+  uint64_t ad = bits(y) & ABS64;
+  if (ad == 0 || ad > 0x7FDFFFFFFFFFFFFFull) return 0;
+  return trip_class_b(bits(x) & ABS64, ad + 0x0010000000000000ull);
 }
 
 struct FmodF {
@@ -132,7 +150,7 @@ struct FmodF {
 struct RemainderF {
   static constexpr int NCLS = kTripClasses;
   static constexpr int SORT_EPT = 8;                 // as FmodF (13.8 -> 15.2 Gelem/s)
-  __device__ static int cls(double x, double y) { return trip_class(x, y); }
+  __device__ static int cls(double x, double y) { return trip_class_rem(x, y); }
   __device__ double operator()(double x, double y) const {
     uint64_t bx = bits(x), by = bits(y);
     uint64_t an = bx & ABS64, ad = by & ABS64;
