@@ -11,12 +11,13 @@
 // size), vector width and grid multiplier are runtime parameters chosen by
 // sleefcu_batch_autotune, which times candidate configurations on the plan
 // itself and can cache the choice in a JSON file keyed by device name.
-// The batched kernel keeps multiplications and roundings on the FP64 pipe
-// (SLEEFCU_SOFT_MUL 0): measured on the 4096-array mix it was no faster with
-// the software forms (15.1 against 15.4 Gelem/s; its one kernel holds every
-// functor and is bound by their largest register budget), and they nearly
-// double this translation unit's compile time.  The results are the same bits.
-#define SLEEFCU_SOFT_MUL 0
+// The batched kernel runs multiplications and roundings in software through
+// one out-of-line copy of the exact multiply (SLEEFCU_SOFT_MUL 2): measured
+// on the 4096-array mix, 17.9 Gelem/s against 15.8 with the FP64 pipe's
+// multiply and 15.1 with the software multiply inlined (its one kernel holds
+// every functor, and the inlined copies cost more instruction fetch than
+// they save).  The results are the same bits.
+#define SLEEFCU_SOFT_MUL 2
 #define SLEEFCU_FUNCTORS_ONLY
 #include "trig_f64.cu"
 #include "explog_f64.cu"

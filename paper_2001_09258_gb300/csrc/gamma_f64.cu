@@ -97,8 +97,10 @@ __device__ __forceinline__ d2 lg_stirling(d2 y) {
   double w = dmul(ry, ry);
   return add_d2_d(r, dmul(poly(w, kLgSt), ry));
 }
-// lgamma of a DD y > 0
-__device__ __forceinline__ d2 lgamma_pos(d2 y) {
+// lgamma of a DD y > 0; out of line (its four paths are called from the
+// positive and the reflected arguments of both functions: one copy of the
+// code instead of three, tgamma 2.41 -> 2.48 Gelem/s on GB300, same bits)
+static __device__ __noinline__ d2 lgamma_pos(d2 y) {
   const uint64_t b = bits(y.x);                       // y.x > 0 and finite
   if (b >= G8) return lg_stirling(y);
   if (b >= G175 && b < G25) return lg_r2(norm_d2(add_d2_d(y, -2.0)));
