@@ -29,6 +29,13 @@ __device__ __forceinline__ double rdown(double v) {   // nextafter(v, 0) for v >
   return from_bits(bits(v) - 1);
 }
 __device__ __forceinline__ int ilogb_n(uint64_t b) { return (int)((b >> 52) & 0x7FF) - 1023; }
+// bits of 2v for the bits b of a non-negative finite v: the exponent field
+// plus one for a normal v (beyond the largest finite v this gives a pattern
+// above +inf, which compares above every finite value as 2v = +inf does), a
+// one-bit shift for a subnormal v (into the normal range where it carries)
+__device__ __forceinline__ uint64_t twice_b(uint64_t b) {
+  return b < 0x0010000000000000ull ? b << 1 : b + 0x0010000000000000ull;
+}
 __device__ __forceinline__ double scale_n(double v, int j) {   // v normal, v 2^j normal
   return from_bits(bits(v) + ((uint64_t)(int64_t)j << 52));
 }
@@ -156,11 +163,16 @@ struct RemainderF {
     uint64_t an = bx & ABS64, ad = by & ABS64;
     bool ok = an < INF && ad != 0 && ad < INF;
     double nn = ok ? from_bits(an) : 0.0, d = ok ? from_bits(ad) : 1.0;
+    const uint64_t bd = bits(d);
     double r2 = nn;
-    if (bits(d) <= 0x7FDFFFFFFFFFFFFFull) r2 = fmod_abs(nn, dmul(2.0, d));   // 2|y| finite
-    if (__dadd_rn(r2, r2) > d) {   // quotient 1, or 2 when r2 >= 3|y|/2
+    if (bd <= 0x7FDFFFFFFFFFFFFFull) r2 = fmod_abs(nn, from_bits(twice_b(bd)));   // 2|y| finite
+    // 2 r2 > |y| (quotient 1, or 2 when r2 >= 3|y|/2), compared on the bits
+    // of the non-negative operands: the same outcome as the FP64 comparison
+    // of the exact 2 r2 (an overflowing 2 r2 compares above every finite |y|
+    // either way), without FP64-pipe additions or comparisons
+    if (twice_b(bits(r2)) > bd) {
       r2 = __dsub_rn(r2, d);
-      if (__dadd_rn(r2, r2) >= d) r2 = __dsub_rn(r2, d);
+      if (!(bits(r2) >> 63) && twice_b(bits(r2)) >= bd) r2 = __dsub_rn(r2, d);
     }
     double ret = neg_if(r2, (bx >> 63) != 0);
     if (ad == INF && an < INF) ret = x;
