@@ -92,6 +92,9 @@ __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = null
     r = step(r, j ? scale_n(dmin, j) : dmin, j ? scale_n(rd0, -j) : rd0);
     if (COUNT) ++*steps;
   }
+  // the remainder equal to the divisor reads as 0; the divisor is positive
+  // and finite, a value with one bit pattern, so comparing the bits is
+  // comparing the values (on the integer pipe instead of the FP64 pipe)
   double ret;
   if (sub) {
     r = D2(dmul(r.x, 0x1p54), dmul(r.y, 0x1p54));
@@ -100,10 +103,10 @@ __device__ __forceinline__ double fmod_abs(double n, double d, int *steps = null
       if (COUNT) ++*steps;
     }
     ret = dmul(r.x, 0x1p-54);
-    if (__dadd_rn(r.x, r.y) == dmin) ret = 0.0;
+    if (bits(__dadd_rn(r.x, r.y)) == bdmin) ret = 0.0;
   } else {
     ret = r.x;
-    if (__dadd_rn(r.x, r.y) == d) ret = 0.0;
+    if (bits(__dadd_rn(r.x, r.y)) == bd) ret = 0.0;
   }
   return ret;
 }
