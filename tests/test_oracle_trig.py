@@ -163,6 +163,41 @@ def test_payne_hanek_bruteforce():
         assert abs(hi) <= math.pi / 4 + 1e-9
 
 
+def test_payne_hanek_bruteforce_million():
+    """The same exact check on 10^6 log-uniform huge arguments (1e14 to
+    DBL_MAX), in integers scaled by 2^1500: the reduction x - k pi/2 with
+    pi/2 to 1500 bits, the oracle's DD remainder hi + lo (every double down
+    to 2^-1074 is an integer multiple of 2^-1500), same quadrant mod 4 (a
+    neighbouring one only where |r| is near pi/4), relative error < 2^-95."""
+    import ctypes
+    B = 1500
+    P = I._pi_half_int(B)
+    near_quarter = 780 * (1 << B)          # 0.780 in units of 2^-1500, times 1000
+
+    def scaled(v):                          # v * 2^B as an exact integer
+        if v == 0.0:
+            return 0
+        m, e = math.frexp(v)
+        return int(m * 2 ** 53) << (e - 53 + B)
+
+    f = oracle.lib().oracle_ph_reduce
+    q, hi, lo = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    xs = I.loguniform("ph/bf1m", 10 ** 6, 1e14, 1.79e308)
+    for x in xs.tolist():
+        f(x, ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo))
+        m, e = math.frexp(abs(x))
+        X = int(m * 2 ** 53) << (e - 53 + B)
+        k = (2 * X + P) // (2 * P)
+        r = X - k * P
+        if x < 0:
+            k, r = -k, -r
+        d = (q.value - k) % 4
+        if d:
+            assert d in (1, 3) and abs(r) * 1000 > near_quarter, x
+            r -= (1 if d == 1 else -1) * P
+        assert abs(scaled(hi.value) + scaled(lo.value) - r) << 95 < abs(r), x
+
+
 def test_payne_hanek_table_definition():
     """the Payne-Hanek table-generation figure: 1024 x 4 doubles (32 KB), each the
     RN double of the remaining fraction with its lowest bit cleared, E > 700
